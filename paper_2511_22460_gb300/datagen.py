@@ -1,0 +1,243 @@
+"""Seeded synthetic inputs for the embedding-based ad retrieval hot path.
+
+This module only draws random inputs: ad embeddings, per-ad field values, user
+field values, cross pairs, cross-weight tables, targeting bitmaps and request
+arrival times.  It holds none of the scoring arithmetic (no dot products, no
+weight hashing, no index construction); the CUDA library and the CPU oracle
+both consume the arrays it returns.
+
+Shapes follow the paper's workload description: millions of ads (Sec. 4.4),
+64-d tower outputs (Sec. 4.1), and heavy-tailed categorical ad features such as
+categories and advertiser ids (Sec. 4.1, "Features").  The paper's own data is
+private, so every array here is synthetic.
+
+Random streams: ``numpy.random.PCG64`` seeded from ``SeedSequence(seed)``,
+one spawned child stream per array, in the fixed order of ``_STREAMS``.
+
+Distributions:
+  * embeddings and user vectors: iid N(0, 1/d) float32 (the second parameter of
+    N(.,.) is a variance);
+  * vocabularies: fixed, or log-uniform integers in [10, 100000];
+  * field values: finite Zipf, P(rank r) proportional to r^-s for r = 1..V,
+    drawn by inverse CDF, rank mapped to a value id through a seeded
+    permutation per field;
+  * cross weights: iid N(0, var) float32, either one dense table per cross pair
+    (shape V_user_i x V_ad_j, row-major [u][v]) or one shared table of 2^24
+    entries addressed through a hash of (pair, u, v);
+  * targeting bitmaps: bit a set iid with probability f, f ~ U[0.01, 1] per
+    request, packed little-endian into uint64 words (bit a of word a >> 6).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+from typing import Optional
+
+import numpy as np
+
+HASH_BITS = 24
+
+_STREAMS = (
+    "vocab_u", "vocab_a", "perm_u", "perm_a", "ad_vals", "user_vals", "pairs",
+    "weights", "emb", "h_u", "filter", "shuffle", "k_choice", "arrivals",
+)
+
+
+@dataclass(frozen=True)
+class Recipe:
+    """Parameters of one synthetic workload."""
+    name: str
+    n_ads: int
+    d: int
+    f_u: int
+    f_a: int
+    vocab: object            # int (fixed) or "loguniform"
+    zipf_ad: float
+    zipf_user: float
+    n_pairs: Optional[int]   # None = all F_u x F_a pairs
+    weights: str             # "dense" | "hashed"
+    w_var: float
+    k: int
+    batch: int = 1
+    emb_dtype: str = "f32"   # "f32" | "bf16" | "fp8e4m3"
+    rescore_mult: int = 0    # R: rescoring keeps R*K candidates (0 = no rescoring)
+    k_choices: tuple = ()    # per-request K drawn uniformly from this set
+    filter_frac: Optional[tuple] = None  # (lo, hi) for per-request filter density
+    vocab_lo: int = 10
+    vocab_hi: int = 100_000
+
+
+RECIPES = {
+    # Plain method, single request, small enough for the FP64 oracle.
+    "single_fp32_10k": Recipe("single_fp32_10k", 10_000, 32, 4, 4, 50, 1.1, 1.1, None,
+                              "dense", 0.1, 100),
+    # Plain FP32 single request at inventory scale.
+    "single_fp32_2m": Recipe("single_fp32_2m", 2_000_000, 64, 16, 16, "loguniform", 1.05,
+                             1.05, 64, "hashed", 0.05, 500),
+    # 256 users against 5M ads, BF16 embeddings, rescoring of the top 4K.
+    "batch256_bf16_5m": Recipe("batch256_bf16_5m", 5_000_000, 128, 24, 24, "loguniform",
+                               1.05, 1.05, 96, "hashed", 0.05, 1000, batch=256,
+                               emb_dtype="bf16", rescore_mult=4),
+    # FP8-e4m3 with per-row scale, 10M ads, posting lists Zipf(1.0) over V=15.
+    "fp8_10m": Recipe("fp8_10m", 10_000_000, 64, 32, 32, 15, 1.0, 1.0, 128, "hashed",
+                      0.05, 2000, batch=1, emb_dtype="fp8e4m3", rescore_mult=4),
+    # Serving: 5M BF16 ads, per-request K and targeting bitmap.
+    "serve_bf16_5m": Recipe("serve_bf16_5m", 5_000_000, 64, 32, 32, "loguniform", 1.05,
+                            1.05, 128, "hashed", 0.05, 1000, batch=64, emb_dtype="bf16",
+                            rescore_mult=4, k_choices=(100, 500, 1000),
+                            filter_frac=(0.01, 1.0)),
+}
+
+
+@dataclass
+class Workload:
+    """All synthetic arrays of one workload (host numpy arrays)."""
+    recipe: Recipe
+    vocab_u: np.ndarray          # uint32 [F_u]
+    vocab_a: np.ndarray          # uint32 [F_a]
+    key_off: np.ndarray          # uint32 [F_a + 1]: key(j, v) = key_off[j] + v
+    ad_vals: np.ndarray          # uint32 [N, F_a]
+    pairs: np.ndarray            # uint32 [P, 2]: (user field i, ad field j)
+    w_table: np.ndarray          # float32: hashed table [2^24] or concatenated dense tables
+    w_off: np.ndarray            # uint64 [P]: start of pair p's dense table (dense only)
+    emb: np.ndarray              # float32 [N, d]
+    users: np.ndarray            # uint32 [B, F_u]
+    h_u: np.ndarray              # float32 [B, d]
+    ks: np.ndarray               # uint32 [B]
+    filters: Optional[np.ndarray] = None   # uint64 [B, ceil(N/64)] or None
+    seed: int = 0
+    _rngs: dict = field(default_factory=dict, repr=False)
+
+    @property
+    def n_ads(self) -> int:
+        return self.recipe.n_ads
+
+    @property
+    def n_keys(self) -> int:
+        return int(self.key_off[-1])
+
+    @property
+    def nnz(self) -> int:
+        return int(self.ad_vals.size)
+
+    def postings(self, shuffle: bool = False):
+        """Uncompressed feature->ad map L as (key, ad) pairs, ad-major order.
+
+        The pairs are the raw input of index construction: ad ``a`` is in the
+        posting list of key(j, v) iff ad field j of ``a`` has value v.
+        """
+        n, f_a = self.ad_vals.shape
+        keys = (self.ad_vals + self.key_off[:f_a][None, :]).astype(np.uint32).reshape(-1)
+        ads = np.repeat(np.arange(n, dtype=np.uint32), f_a)
+        if shuffle:
+            perm = self._rngs["shuffle"].permutation(keys.size)
+            keys, ads = keys[perm], ads[perm]
+        return keys, ads
+
+
+def _zipf_sample(rng, V: int, s: float, size: int, perm: np.ndarray) -> np.ndarray:
+    w = np.arange(1, V + 1, dtype=np.float64) ** (-s)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    u = rng.random(size)
+    r = np.searchsorted(cdf, u, side="right")
+    np.minimum(r, V - 1, out=r)
+    return perm[r].astype(np.uint32)
+
+
+def _vocab(rng, recipe: Recipe, n: int) -> np.ndarray:
+    if recipe.vocab == "loguniform":
+        lo, hi = np.log(recipe.vocab_lo), np.log(recipe.vocab_hi)
+        return np.rint(np.exp(rng.uniform(lo, hi, size=n))).astype(np.uint32)
+    return np.full(n, int(recipe.vocab), dtype=np.uint32)
+
+
+def make_workload(name_or_recipe, seed: int = 0, **overrides) -> Workload:
+    """Draw one workload.  ``overrides`` replace Recipe fields (e.g. n_ads, batch)."""
+    recipe = RECIPES[name_or_recipe] if isinstance(name_or_recipe, str) else name_or_recipe
+    if overrides:
+        recipe = replace(recipe, **overrides)
+    children = np.random.SeedSequence(seed).spawn(len(_STREAMS))
+    rngs = {k: np.random.Generator(np.random.PCG64(c)) for k, c in zip(_STREAMS, children)}
+
+    n, d, f_u, f_a, B = recipe.n_ads, recipe.d, recipe.f_u, recipe.f_a, recipe.batch
+    vocab_u = _vocab(rngs["vocab_u"], recipe, f_u)
+    vocab_a = _vocab(rngs["vocab_a"], recipe, f_a)
+    key_off = np.zeros(f_a + 1, dtype=np.uint64)
+    key_off[1:] = np.cumsum(vocab_a.astype(np.uint64))
+    assert key_off[-1] < 2**32
+    key_off = key_off.astype(np.uint32)
+
+    perm_u = [rngs["perm_u"].permutation(int(v)) for v in vocab_u]
+    perm_a = [rngs["perm_a"].permutation(int(v)) for v in vocab_a]
+
+    ad_vals = np.empty((n, f_a), dtype=np.uint32)
+    for j in range(f_a):
+        ad_vals[:, j] = _zipf_sample(rngs["ad_vals"], int(vocab_a[j]), recipe.zipf_ad, n,
+                                     perm_a[j])
+    users = np.empty((B, f_u), dtype=np.uint32)
+    for i in range(f_u):
+        users[:, i] = _zipf_sample(rngs["user_vals"], int(vocab_u[i]), recipe.zipf_user, B,
+                                   perm_u[i])
+
+    all_pairs = np.array([(i, j) for i in range(f_u) for j in range(f_a)], dtype=np.uint32)
+    if recipe.n_pairs is None or recipe.n_pairs >= len(all_pairs):
+        pairs = all_pairs
+    else:
+        idx = np.sort(rngs["pairs"].choice(len(all_pairs), size=recipe.n_pairs, replace=False))
+        pairs = all_pairs[idx]
+
+    std = np.float32(np.sqrt(recipe.w_var))
+    if recipe.weights == "dense":
+        sizes = [int(vocab_u[i]) * int(vocab_a[j]) for i, j in pairs]
+        w_off = np.zeros(len(pairs), dtype=np.uint64)
+        w_off[1:] = np.cumsum(np.array(sizes[:-1], dtype=np.uint64))
+        w_table = (rngs["weights"].standard_normal(sum(sizes), dtype=np.float32) * std)
+    elif recipe.weights == "hashed":
+        w_off = np.zeros(len(pairs), dtype=np.uint64)
+        w_table = rngs["weights"].standard_normal(1 << HASH_BITS, dtype=np.float32) * std
+    else:
+        raise ValueError(recipe.weights)
+
+    estd = np.float32(np.sqrt(1.0 / d))
+    emb = rngs["emb"].standard_normal((n, d), dtype=np.float32)
+    emb *= estd
+    h_u = rngs["h_u"].standard_normal((B, d), dtype=np.float32) * estd
+
+    if recipe.k_choices:
+        ks = rngs["k_choice"].choice(np.array(recipe.k_choices, dtype=np.uint32), size=B)
+    else:
+        ks = np.full(B, recipe.k, dtype=np.uint32)
+    ks = np.minimum(ks, n).astype(np.uint32)
+
+    filters = None
+    if recipe.filter_frac is not None:
+        filters = make_filters(rngs["filter"], n, B, recipe.filter_frac)
+
+    return Workload(recipe, vocab_u, vocab_a, key_off, ad_vals, pairs,
+                    w_table.astype(np.float32), w_off, emb, users, h_u, ks, filters, seed,
+                    rngs)
+
+
+def make_filters(rng, n: int, B: int, frac) -> np.ndarray:
+    """Per-request targeting bitmaps: bit a set iid with probability f ~ U[lo, hi]."""
+    words = (n + 63) // 64
+    out = np.zeros((B, words), dtype=np.uint64)
+    for b in range(B):
+        f = rng.uniform(frac[0], frac[1])
+        bits = rng.random(n) < f
+        padded = np.zeros(words * 64, dtype=bool)
+        padded[:n] = bits
+        out[b] = np.packbits(padded.reshape(-1, 8), axis=1, bitorder="little").view(
+            np.uint64).reshape(-1)
+    return out
+
+
+def poisson_arrivals(rate_per_s: float, duration_s: float, seed: int = 0) -> np.ndarray:
+    """Open-loop request arrival times (seconds), exponential inter-arrivals."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 7])))
+    n_est = int(rate_per_s * duration_s * 1.2) + 16
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=n_est))
+    while t[-1] < duration_s:
+        t = np.concatenate([t, t[-1] + np.cumsum(rng.exponential(1.0 / rate_per_s,
+                                                                 size=n_est))])
+    return t[t < duration_s]
