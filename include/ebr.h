@@ -1,0 +1,246 @@
+/*
+ * ebr.h -- C ABI of the GB300 embedding-based ad retrieval library.
+ *
+ * The library scores one request (or a batch) against every ad of an
+ * inventory with the Wide & Deep retrieval score of the paper
+ * "An Efficient Embedding Based Ad Retrieval with GPU-Powered Feature
+ * Interaction" (arXiv 2511.22460):
+ *
+ *     s(u, a) = <h~_u, h~_a> + sum_m w_m x_m L[a, m]        (HitMatch eq., Sec. 3.3)
+ *
+ * and returns the K best ads.  The deep term is the dual-tower inner product
+ * (Eq. 1, Sec. 3.1; IPNN dimensions are concatenated into h~, Sec. 3.2).  The
+ * wide term is evaluated by walking the compressed inverted list of
+ * Sec. 3.4 (Algorithm 1 builds it, Algorithm 2 queries it).
+ *
+ * Conventions for every entry point:
+ *  - Return value: EBR_OK (0) or a negative EBR_E* code.  Nothing aborts or
+ *    throws across this boundary.  After an error, ebr_last_error() returns a
+ *    message for the calling thread.
+ *  - Plain pointers only.  "device" means memory of the index's CUDA device;
+ *    "host" means ordinary or pinned host memory.  Each argument says which
+ *    it accepts.
+ *  - Ownership: the caller owns every pointer it passes in and may free it
+ *    once the call returns (stream-ordered calls: once the stream has
+ *    drained).  The library owns the objects it creates (ebr_index,
+ *    ebr_cross, ebr_server) and their device memory until the matching
+ *    *_free / *_destroy.
+ *  - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Calls that use one index's scratch memory (ebr_score_topk,
+ *    ebr_score_all) must not overlap on the GPU: issue them on one stream, or
+ *    synchronise between streams.
+ */
+#ifndef EBR_H
+#define EBR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define EBR_OK 0
+#define EBR_EINVAL (-1)    /* bad argument: shape, id >= N, key >= n_keys, K > limits ... */
+#define EBR_ENOMEM (-2)    /* device allocation failed, or admission refused */
+#define EBR_ECUDA (-3)     /* CUDA runtime error; see ebr_last_error() */
+#define EBR_EAGAIN (-4)    /* ebr_poll: request still in flight */
+#define EBR_ETIMEDOUT (-5) /* a bounded device or host wait ran out */
+#define EBR_EDATA (-6)     /* a device-side check rejected input data (e.g. a query key >= n_keys) */
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *ebr_last_error(void);
+/* ABI version: 0xMMmmpp. */
+int ebr_version(void);
+
+typedef enum { EBR_F32 = 0, EBR_BF16 = 1, EBR_FP8E4M3 = 2 } ebr_dtype;
+
+/* --------------------------------------------------------------- index */
+typedef struct ebr_index ebr_index;
+
+/*
+ * Index description.  The feature->ad matrix L of Sec. 3.3 is given as its
+ * non-zeros: (post_key[e], post_ad[e]) means ad post_ad[e] is in the posting
+ * list of key post_key[e] (keys are feature indices, values are ad indices,
+ * Sec. 3.4 and Algorithm 1's input).  Pairs may come in any order and may
+ * repeat (a repeated pair counts once: a posting list is a set).
+ */
+typedef struct {
+  uint32_t n_ads;            /* N, ad ids are 0 .. N-1 (N >= 1) */
+  uint32_t n_keys;           /* number of feature keys, keys are 0 .. n_keys-1 (>= 1) */
+  uint64_t nnz;              /* number of (key, ad) pairs, < 2^31 */
+  const uint32_t *post_key;  /* [nnz] host or device */
+  const uint32_t *post_ad;   /* [nnz] host or device */
+  uint32_t d;                /* embedding dimension: 4, 8, 16, 32, 64 or 128 */
+  ebr_dtype emb_dtype;       /* dtype the scan streams; BF16/FP8 keep an FP32 copy for rescoring */
+  const float *emb_f32;      /* [N][d] row-major FP32 ad vectors h~_a, host or device */
+  uint32_t rescore_mult;     /* R: BF16/FP8 scans keep R*K candidates for FP32 rescoring (0 -> 4) */
+  int device;                /* CUDA device ordinal */
+  void *stream;              /* stream for the build */
+} ebr_index_desc;
+
+/*
+ * Build the compressed inverted list of Algorithm 1 (Block Grouping by
+ * ad >> 8, Logarithmic Categorization into groups g = ceil(log2 n) = 0..8,
+ * Block Compression to one 24-bit header per block plus one byte per ad,
+ * struct-of-arrays storage with a per-key offset array; Sec. 3.4) on the GPU,
+ * and upload (and, for BF16/FP8, quantise) the ad embeddings.
+ * Returns EBR_EINVAL for bad sizes and EBR_EDATA if a key >= n_keys or an
+ * ad >= n_ads is found.  Synchronous: returns after the build completes.
+ */
+int ebr_build_index(const ebr_index_desc *desc, ebr_index **out);
+void ebr_index_free(ebr_index *ix);
+
+typedef struct {
+  uint32_t n_ads, n_keys, d;
+  ebr_dtype emb_dtype;
+  uint32_t rescore_mult;
+  uint64_t nnz_unique;          /* distinct (key, ad) pairs */
+  uint64_t n_blocks[9];         /* blocks per size group g */
+  uint64_t index_bytes;         /* sum_g 4*(n_keys+1) + 4*n_blocks[g] + 2^g*n_blocks[g] */
+  uint64_t emb_bytes;           /* bytes of the scanned embedding table (+ FP8 row scales) */
+  float build_ms;               /* device time of the index build (Algorithm 1 only) */
+} ebr_index_info;
+int ebr_index_get_info(const ebr_index *ix, ebr_index_info *out);
+
+/*
+ * Copy group g of the index to host buffers: keys[n_keys+1] (per-key block
+ * offsets), header[n_blocks[g]] (ad >> 8 of each block), values[n_blocks[g] << g]
+ * (ad & 255 of each slot; within a block ascending, padding slots are 0 and
+ * only slot 0 may hold a real 0).  Any of the three may be NULL to skip it.
+ */
+int ebr_index_export(const ebr_index *ix, uint32_t g, uint32_t *keys, uint32_t *header,
+                     uint8_t *values);
+
+/*
+ * Copy the scanned embedding table to host: codes[N*d] of the index dtype
+ * (float, bfloat16 bits as uint16, or E4M3 bytes) and, for FP8, scale[N].
+ */
+int ebr_index_export_emb(const ebr_index *ix, void *codes, float *scale);
+
+/* ------------------------------------------------- cross model / expansion */
+typedef struct ebr_cross ebr_cross;
+typedef enum { EBR_W_DENSE = 0, EBR_W_HASHED = 1 } ebr_wkind;
+
+/*
+ * Cross-feature model.  Feature key of ad field j with value v is
+ * key_off[j] + v, key_off[j] = vocab_a[0] + ... + vocab_a[j-1].  A cross
+ * pair p = (i, j) pairs user field i with ad field j; its weight for user
+ * value u and ad value v is
+ *   dense:  w_table[w_off[p] + u * vocab_a[j] + v]
+ *   hashed: w_table[splitmix64((p << 40) | (u << 20) | v) & (2^hash_bits - 1)]
+ * where splitmix64(x) is the first output of the SplitMix64 generator seeded
+ * with x.  Hashed tables need vocabularies < 2^20 and n_pairs < 2^24.
+ */
+typedef struct {
+  uint32_t f_u, f_a;
+  const uint32_t *vocab_u;   /* host [f_u] */
+  const uint32_t *vocab_a;   /* host [f_a] */
+  uint32_t n_pairs;
+  const uint32_t *pairs;     /* host [n_pairs][2] = (user field i, ad field j) */
+  ebr_wkind kind;
+  const float *w_table;      /* host or device, w_len floats; copied */
+  uint64_t w_len;
+  const uint64_t *w_off;     /* host [n_pairs], dense tables only (else NULL) */
+  uint32_t hash_bits;        /* hashed tables: 1 .. 30 */
+  int device;
+  void *stream;
+} ebr_cross_desc;
+int ebr_cross_create(const ebr_cross_desc *desc, ebr_cross **out);
+void ebr_cross_free(ebr_cross *c);
+uint32_t ebr_cross_n_keys(const ebr_cross *c);
+
+/*
+ * Query expansion: the non-zero (k, w^) of a request (Algorithm 2's input,
+ * w^ = w x of Sec. 3.4 with x = 1).  Cross features sharing an ad-field key
+ * fold into one weight:  w_hat[b][key_off[j] + v] = sum over pairs (i, j) of
+ * w_ij(user_vals[b][i], v).  Output is dense over all n_keys keys (0 for ad
+ * fields in no pair).  user_vals: device [batch][f_u]; w_hat: device
+ * [batch][n_keys].  A user value >= its vocabulary gives EBR_EDATA (checked on
+ * device, reported after the stream drains) and a zero row.
+ */
+int ebr_expand_query(const ebr_cross *c, const uint32_t *user_vals, uint32_t batch,
+                     float *w_hat, void *stream);
+
+/* ------------------------------------------------------------- queries */
+/*
+ * One request.  The wide term's query is either
+ *   - raw user features: user_vals[f_u], expanded with the call's cross model;
+ *   - a dense weight vector: q_key == NULL, q_w[n_keys] indexed by key;
+ *   - a sparse list: q_key[n_q], q_w[n_q] (duplicates add, keys must be < n_keys).
+ * filter: targeting bitmap, bit a of word a >> 6 keeps ad a (NULL keeps all).
+ * k: 1 .. 8192 (with BF16/FP8 scans, R*k <= 8192).
+ */
+typedef struct {
+  const float *h_u;            /* [d] */
+  const uint32_t *user_vals;   /* [f_u] or NULL */
+  uint32_t n_q;
+  const uint32_t *q_key;       /* [n_q] or NULL */
+  const float *q_w;            /* [n_q] or [n_keys] */
+  const uint64_t *filter;      /* [ceil(N / 64)] or NULL */
+  uint32_t k;
+} ebr_query;
+
+#define EBR_IO_DEVICE 0   /* all query arrays and outputs are device pointers; stream-ordered */
+#define EBR_IO_HOST 1     /* all query arrays and outputs are host pointers; the call copies them
+                             in and out on `stream` and returns after the stream drained */
+
+/*
+ * Score every ad for each of `batch` requests and return its top K
+ * (Eq. 1 + HitMatch equation; the top-K retrieval of Sec. 2/4.4).  Row b of
+ * out_ids/out_scores ([batch][kmax], kmax = max_b q[b].k) holds request b's
+ * best ads by score descending then id ascending; positions past the number
+ * of eligible ads hold id 0xFFFFFFFF and score -inf.  The full score vector
+ * is never written to device memory.  `cross` may be NULL when no request
+ * uses user_vals.  `q` is a host array of `batch` structs.
+ */
+int ebr_score_topk(const ebr_index *ix, const ebr_cross *cross, const ebr_query *q,
+                   uint32_t batch, uint32_t *out_ids, float *out_scores, int io,
+                   void *stream);
+
+/*
+ * Diagnostic: the full score vector of one request, out_scores[N] (device),
+ * computed by the same kernels as ebr_score_topk's scan (with the index's
+ * scan dtype) but written out instead of selected.  The filter is ignored.
+ */
+int ebr_score_all(const ebr_index *ix, const ebr_cross *cross, const ebr_query *q,
+                  float *out_scores, void *stream);
+
+/*
+ * Diagnostic: only the wide (HitMatch) term of one request via Algorithm 2's
+ * key-major walk: out_wide[N] (device) = sum over query entries (k, w^) of
+ * w^ * L[a, k].
+ */
+int ebr_wide_scores(const ebr_index *ix, const ebr_cross *cross, const ebr_query *q,
+                    float *out_wide, void *stream);
+
+/*
+ * Diagnostic: quantise n floats (device) with the library's converters:
+ * dtype EBR_BF16 writes uint16 codes, EBR_FP8E4M3 writes E4M3 bytes of x
+ * (saturating to +-448, no scaling).
+ */
+int ebr_quantize(const float *x, uint64_t n, ebr_dtype dtype, void *out, void *stream);
+
+/* ------------------------------------------------------------ profiling */
+/*
+ * Per-stage device time of ebr_score_topk calls on one index, measured with
+ * CUDA events recorded on the caller's stream around each stage:
+ * query expansion, the wide term (Algorithm 2), the streaming scan with the
+ * fused add + per-CTA top-K, and the final selection (+ FP32 rescoring).
+ * ebr_profile_enable resets the counters; ebr_profile_read waits for the
+ * recorded events and returns the sums.  Disabled by default.
+ */
+typedef struct {
+  uint64_t calls;          /* requests profiled */
+  uint64_t launches;       /* kernels of this library launched by those requests */
+  uint64_t lib_launches;   /* device-library (CUB scan) kernels launched */
+  double ms_expand, ms_wide, ms_scan, ms_final;
+} ebr_profile;
+int ebr_profile_enable(ebr_index *ix, int on);
+int ebr_profile_read(ebr_index *ix, ebr_profile *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EBR_H */

@@ -1,0 +1,127 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <array>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/ebr.h"
+
+namespace ebr {
+
+// ------------------------------------------------------------ error state
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define EBR_CUDA_TRY(expr)                                                         \
+  do {                                                                             \
+    cudaError_t _e = (expr);                                                       \
+    if (_e != cudaSuccess) {                                                       \
+      ::ebr::set_error("%s failed at %s:%d: %s", #expr, __FILE__, __LINE__,         \
+                       cudaGetErrorString(_e));                                    \
+      return EBR_ECUDA;                                                            \
+    }                                                                              \
+  } while (0)
+
+#define EBR_TRY(expr)             \
+  do {                            \
+    int _rc = (expr);             \
+    if (_rc != EBR_OK) return _rc; \
+  } while (0)
+
+// Device error flags (bitwise OR of these lands in a device word).
+enum : uint32_t {
+  DEVERR_BAD_KEY = 1u,        // query key >= n_keys
+  DEVERR_BAD_AD = 2u,         // ad id >= n_ads in build input
+  DEVERR_BAD_USER = 4u,       // user value >= vocabulary
+  DEVERR_TIMEOUT = 8u,        // a bounded wait ran out
+  DEVERR_OVERFLOW = 16u,      // a capacity check failed
+  DEVERR_BAD_BUILD_KEY = 32u, // key >= n_keys in build input
+};
+
+int check_device_flags(uint32_t flags, const char *where);
+
+// RAII-less device buffer helper (explicit free).
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+int dev_alloc(DevBuf &b, size_t bytes);
+void dev_free(DevBuf &b);
+int dev_reserve(DevBuf &b, size_t bytes);  // grow-only
+
+// ---------------------------------------------------------- object layout
+constexpr int kGroups = 9;
+
+// Scratch used by one query call on one index.
+struct Workspace {
+  DevBuf wide;        // float [N] wide-score accumulator (Algorithm 2's score array)
+  DevBuf w_dense;     // float [n_keys] expanded query (from user_vals)
+  DevBuf lens;        // uint2 [9 * n_q + 1] (units, nonempty) per (group, query entry)
+  DevBuf scan;        // uint2 [9 * n_q + 1] exclusive scan of lens
+  DevBuf work;        // WorkEntry [9 * n_q] compacted non-empty (group, entry)
+  DevBuf cub_tmp;     // CUB temporary storage
+  DevBuf cand;        // uint64 [G * KCAP] per-CTA candidates
+  DevBuf ctrl;        // Ctrl block (counters, threshold, flags)
+  DevBuf io_in;       // staging for host inputs
+  DevBuf io_out;      // staging for outputs
+  void *host_ctrl = nullptr;  // pinned mirror of Ctrl
+};
+
+struct Ctrl {
+  unsigned long long thr;    // global running K-th key
+  unsigned int n_cand;       // candidates appended
+  unsigned int flags;        // DEVERR_* bits
+  unsigned long long total_units;  // Algorithm 2 work units
+  unsigned int n_work;       // compacted work entries
+  unsigned int pad;
+};
+
+}  // namespace ebr
+
+struct ebr_index {
+  int device = 0;
+  uint32_t n_ads = 0, n_keys = 0, d = 0;
+  ebr_dtype dtype = EBR_F32;
+  uint32_t rescore_mult = 4;
+  uint64_t nnz_unique = 0;
+  uint64_t n_blocks[ebr::kGroups] = {0};
+  uint32_t *keys[ebr::kGroups] = {nullptr};
+  uint32_t *header[ebr::kGroups] = {nullptr};
+  uint8_t *values[ebr::kGroups] = {nullptr};
+  ebr::DevBuf mem_keys, mem_header, mem_values;
+  ebr::DevBuf emb_f32;    // float [N][d]
+  ebr::DevBuf emb_q;      // bf16 / e4m3 [N][d]
+  ebr::DevBuf emb_scale;  // float [N] (FP8)
+  float build_ms = 0.f;
+  int num_sms = 0;
+  ebr::Workspace ws;
+  // profiling (ebr_profile_enable)
+  bool prof = false;
+  std::vector<std::array<cudaEvent_t, 5>> prof_pending, prof_pool;
+  ebr_profile prof_acc = {};
+  uint64_t launches = 0, lib_launches = 0;  // counted on every call
+};
+
+struct ebr_cross {
+  int device = 0;
+  uint32_t f_u = 0, f_a = 0, n_pairs = 0, n_keys = 0;
+  ebr_wkind kind = EBR_W_HASHED;
+  uint32_t hash_bits = 24;
+  ebr::DevBuf table;       // float [w_len]
+  ebr::DevBuf meta;        // packed uint32 metadata (see ebr_query.cu)
+  uint64_t w_len = 0;
+  // host copies
+  std::string host_meta;   // bytes of the packed metadata
+};
+
+namespace ebr {
+// Launchers implemented in ebr_query.cu, used by the serving loop.
+int query_one(const ebr_index *ix, const ebr_cross *cross, const ebr_query &q, uint32_t *ids,
+              float *scores, uint32_t kmax, cudaStream_t st);
+}

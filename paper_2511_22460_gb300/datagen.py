@@ -227,8 +227,7 @@ def make_filters(rng, n: int, B: int, frac) -> np.ndarray:
         bits = rng.random(n) < f
         padded = np.zeros(words * 64, dtype=bool)
         padded[:n] = bits
-        out[b] = np.packbits(padded.reshape(-1, 8), axis=1, bitorder="little").view(
-            np.uint64).reshape(-1)
+        out[b] = np.packbits(padded, bitorder="little").view(np.uint64)
     return out
 
 

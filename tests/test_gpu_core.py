@@ -1,0 +1,336 @@
+"""GPU parity of the single-request path against the FP64 oracle (C ABI calls).
+
+Covers Algorithm 1 (bit-exact index), query expansion, Algorithm 2's wide
+scatter, the streaming inner product, the fused add + top-K, the targeting
+filter, host-buffer IO, the BF16/FP8 converters and the BF16/FP8 scans with
+FP32 rescoring.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_2511_22460_gb300 import ebr  # noqa: E402
+from paper_2511_22460_gb300.datagen import make_filters, make_workload  # noqa: E402
+
+from gpu_util import (bitmap_to_mask, check_scores, check_topk, recall,  # noqa: E402
+                      ref_scores)
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _export_all(ix):
+    out = {"keys": [], "header": [], "values": []}
+    for g in range(9):
+        k, h, v = ix.export(g)
+        out["keys"].append(k)
+        out["header"].append(h)
+        out["values"].append(v)
+    return out
+
+
+def _assert_index_equal(ix, pk, pa, n_keys, n_ads):
+    ref = oracle.build_index(n_keys, n_ads, pk, pa)
+    got = _export_all(ix)
+    for g in range(9):
+        np.testing.assert_array_equal(got["keys"][g], ref["keys"][g], err_msg="keys g=%d" % g)
+        np.testing.assert_array_equal(got["header"][g], ref["header"][g], err_msg="hdr g=%d" % g)
+        np.testing.assert_array_equal(got["values"][g], ref["values"][g], err_msg="val g=%d" % g)
+    info = ix.info()
+    assert info.nnz_unique == len(set(zip(pk.tolist(), pa.tolist())))
+
+
+# ------------------------------------------------------------ Algorithm 1
+
+def test_index_hand_example_bit_exact():
+    with open(os.path.join(GOLD, "alg1_tiny.json")) as f:
+        g = json.load(f)
+    pk, pa = [], []
+    for k, a in g["postings"]:
+        ads = range(1280, 1536) if isinstance(a, str) else [a]
+        for ad in ads:
+            pk.append(k)
+            pa.append(ad)
+    pk = np.array(pk, np.uint32)
+    pa = np.array(pa, np.uint32)
+    emb = np.zeros((g["n_ads"], 4), np.float32)
+    ix = ebr.build_index(g["n_ads"], g["n_keys"], pk, pa, emb)
+    _assert_index_equal(ix, pk, pa, g["n_keys"], g["n_ads"])
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_index_random_skewed_bit_exact(seed):
+    rng = np.random.default_rng(seed)
+    n_keys, n_ads, nnz = 300, 70_001, 400_000
+    pk = (rng.zipf(1.3, nnz) % n_keys).astype(np.uint32)
+    pa = rng.integers(0, n_ads, nnz).astype(np.uint32)
+    pk[:5000] = 17  # one key with dense windows
+    pa[:5000] = np.arange(5000, dtype=np.uint32) * 3
+    emb = np.zeros((n_ads, 4), np.float32)
+    ix = ebr.build_index(n_ads, n_keys, dev(pk), dev(pa), dev(emb))  # device inputs
+    _assert_index_equal(ix, pk, pa, n_keys, n_ads)
+
+
+def test_index_workload_bit_exact_and_rejects_bad_input():
+    w = make_workload("single_fp32_2m", n_ads=60_000, seed=2)
+    pk, pa = w.postings(shuffle=True)
+    ix = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb)
+    _assert_index_equal(ix, pk, pa, w.n_keys, w.n_ads)
+    bad = pa.copy()
+    bad[5] = w.n_ads
+    with pytest.raises(ebr.EbrError) as e:
+        ebr.build_index(w.n_ads, w.n_keys, pk, bad, w.emb)
+    assert e.value.code == ebr.EBR_EDATA
+    badk = pk.copy()
+    badk[9] = w.n_keys
+    with pytest.raises(ebr.EbrError) as e:
+        ebr.build_index(w.n_ads, w.n_keys, badk, pa, w.emb)
+    assert e.value.code == ebr.EBR_EDATA
+    with pytest.raises(ebr.EbrError) as e:
+        ebr.build_index(w.n_ads, w.n_keys, pk, pa, np.zeros((w.n_ads, 6), np.float32))
+    assert e.value.code == ebr.EBR_EINVAL
+
+
+# ---------------------------------------------------------- expansion
+
+@pytest.mark.parametrize("name", ["single_fp32_10k", "single_fp32_2m"])
+def test_expand_query_matches_oracle(name):
+    w = make_workload(name, n_ads=1000, batch=5, seed=4)
+    cross = ebr.cross_from_workload(w)
+    oc = oracle.Cross.from_workload(w)
+    out = torch.empty((5, w.n_keys), dtype=torch.float32, device=DEV)
+    ebr.expand_query(cross, dev(w.users), out)
+    got = out.cpu().numpy()
+    for b in range(5):
+        ref = oracle.expand(oc, w.users[b])
+        tol = 1e-6 * np.maximum(np.abs(ref), 1e-30) + 4e-7 * 8
+        np.testing.assert_allclose(got[b], ref, rtol=2e-6, atol=1e-6)
+    bad = w.users.copy()
+    bad[2, 1] = w.vocab_u[1]
+    with pytest.raises(ebr.EbrError) as e:
+        ebr.expand_query(cross, dev(bad), out)
+    assert e.value.code == ebr.EBR_EDATA
+
+
+# ------------------------------------------------------ Algorithm 2 (wide)
+
+def _wide_ref(w, q_key, q_w, postings):
+    zero_h = np.zeros(w.recipe.d, np.float32)
+    pk, pa = postings
+    s = oracle.scores_postings(zero_h, w.emb, w.n_keys, pk, pa, q_key, q_w)
+    # condition scale: sum of |w| over the ad's hits
+    a = oracle.scores_postings(zero_h, w.emb, w.n_keys, pk, pa, q_key, np.abs(q_w))
+    return s, 1e-5 * np.maximum(np.abs(s), a) + 1e-30
+
+
+@pytest.mark.parametrize("name,n", [("single_fp32_10k", 10_000), ("single_fp32_2m", 150_000),
+                                    ("fp8_10m", 90_000)])
+def test_wide_dense_query_matches_oracle(name, n):
+    w = make_workload(name, n_ads=n, seed=5)
+    pk, pa = w.postings(shuffle=True)
+    ix = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb)
+    cross = ebr.cross_from_workload(w)
+    out = torch.empty(w.n_ads, dtype=torch.float32, device=DEV)
+    q = ebr.Query(h_u=dev(w.h_u[0]), k=1, user_vals=dev(w.users[0]))
+    ebr.wide_scores(ix, cross, q, out)
+    wh = oracle.expand(oracle.Cross.from_workload(w), w.users[0])
+    keys = np.arange(w.n_keys, dtype=np.uint32)
+    ref, tol = _wide_ref(w, keys, wh, (pk, pa))
+    check_scores(out.cpu().numpy(), ref, tol, "wide")
+
+
+def test_wide_sparse_list_duplicates_and_bad_key():
+    w = make_workload("single_fp32_2m", n_ads=120_000, seed=6)
+    pk, pa = w.postings()
+    ix = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb)
+    rng = np.random.default_rng(0)
+    # a few hundred keys, heavy ones included, with repeats and a zero weight
+    heavy = np.bincount(pk, minlength=w.n_keys).argsort()[-20:]
+    q_key = np.concatenate([rng.integers(0, w.n_keys, 300), heavy, heavy[:5]]).astype(np.uint32)
+    q_w = rng.standard_normal(q_key.size).astype(np.float32)
+    q_w[3] = 0.0
+    out = torch.empty(w.n_ads, dtype=torch.float32, device=DEV)
+    q = ebr.Query(h_u=dev(w.h_u[0]), k=1, q_key=dev(q_key), q_w=dev(q_w))
+    ebr.wide_scores(ix, None, q, out)
+    ref, tol = _wide_ref(w, q_key, q_w.astype(np.float64), (pk, pa))
+    check_scores(out.cpu().numpy(), ref, tol, "wide sparse")
+    # one-hot: a single key adds exactly its weight to its posting list only
+    k = int(heavy[-1])
+    q1 = ebr.Query(h_u=dev(w.h_u[0]), k=1, q_key=dev(np.array([k], np.uint32)),
+                   q_w=dev(np.array([0.375], np.float32)))
+    ebr.wide_scores(ix, None, q1, out)
+    got = out.cpu().numpy()
+    members = np.zeros(w.n_ads, bool)
+    members[pa[pk == k]] = True
+    assert np.all(got[members] == 0.375) and np.all(got[~members] == 0.0)
+    badq = ebr.Query(h_u=dev(w.h_u[0]), k=1, q_key=dev(np.array([w.n_keys], np.uint32)),
+                     q_w=dev(np.array([1.0], np.float32)))
+    with pytest.raises(ebr.EbrError) as e:
+        ebr.wide_scores(ix, None, badq, out)
+    assert e.value.code == ebr.EBR_EDATA
+
+
+# -------------------------------------------------- full scores and top-K
+
+def _setup(name, n, seed=0, dtype="f32", **kw):
+    w = make_workload(name, n_ads=n, seed=seed, **kw)
+    pk, pa = w.postings(shuffle=seed % 2 == 1)
+    ix = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype=dtype)
+    cross = ebr.cross_from_workload(w)
+    return w, (pk, pa), ix, cross
+
+
+@pytest.mark.parametrize("name,n", [("single_fp32_10k", 10_000), ("single_fp32_2m", 250_013)])
+def test_score_all_matches_oracle(name, n):
+    w, post, ix, cross = _setup(name, n, seed=1)
+    ref, tol = ref_scores(w, 0, post)
+    out = torch.empty(w.n_ads, dtype=torch.float32, device=DEV)
+    ebr.score_all(ix, cross, ebr.Query(h_u=dev(w.h_u[0]), k=1, user_vals=dev(w.users[0])), out)
+    check_scores(out.cpu().numpy(), ref, tol)
+
+
+@pytest.mark.parametrize("name,n,k", [("single_fp32_10k", 10_000, 100),
+                                      ("single_fp32_2m", 300_007, 500),
+                                      ("single_fp32_2m", 100_000, 2000),
+                                      ("single_fp32_2m", 5_000, 5000),
+                                      ("single_fp32_10k", 700, 1000)])
+def test_topk_matches_oracle(name, n, k):
+    w, post, ix, cross = _setup(name, n, seed=2)
+    ref, tol = ref_scores(w, 0, post)
+    ids = torch.empty(k, dtype=torch.int32, device=DEV)
+    sc = torch.empty(k, dtype=torch.float32, device=DEV)
+    ebr.score_topk(ix, cross, [ebr.Query(h_u=dev(w.h_u[0]), k=k, user_vals=dev(w.users[0]))],
+                   ids, sc)
+    check_topk(ids.cpu().numpy().view(np.uint32), sc.cpu().numpy(), ref, tol, k)
+
+
+def test_topk_with_filter_dense_q_w_and_batch():
+    w, post, ix, cross = _setup("single_fp32_2m", 200_000, seed=3, batch=3)
+    filt = make_filters(np.random.default_rng(9), w.n_ads, 3, (0.001, 0.3))
+    filt[2] = np.iinfo(np.uint64).max  # all ones == no filter
+    k = 300
+    oc = oracle.Cross.from_workload(w)
+    qs = []
+    for b in range(3):
+        wh = oracle.expand(oc, w.users[b]).astype(np.float32)
+        qs.append(ebr.Query(h_u=dev(w.h_u[b]), k=k, q_w=dev(wh), filter=dev(filt[b])))
+    ids = torch.empty((3, k), dtype=torch.int32, device=DEV)
+    sc = torch.empty((3, k), dtype=torch.float32, device=DEV)
+    ebr.score_topk(ix, None, qs, ids, sc)
+    for b in range(3):
+        ref, tol = ref_scores(w, b, post)
+        mask = bitmap_to_mask(filt[b], w.n_ads)
+        check_topk(ids[b].cpu().numpy().view(np.uint32), sc[b].cpu().numpy(), ref, tol, k, mask)
+    # an all-ones bitmap gives the unfiltered result
+    ids2 = torch.empty((1, k), dtype=torch.int32, device=DEV)
+    sc2 = torch.empty((1, k), dtype=torch.float32, device=DEV)
+    q_nf = ebr.Query(h_u=qs[2].h_u, k=k, q_w=qs[2].q_w)
+    ebr.score_topk(ix, None, [q_nf], ids2, sc2)
+    assert torch.equal(ids2[0], ids[2])
+
+
+def test_topk_host_io_equals_device_io():
+    w, post, ix, cross = _setup("single_fp32_2m", 150_000, seed=4)
+    k = 500
+    ids = torch.empty(k, dtype=torch.int32, device=DEV)
+    sc = torch.empty(k, dtype=torch.float32, device=DEV)
+    ebr.score_topk(ix, cross, [ebr.Query(h_u=dev(w.h_u[0]), k=k, user_vals=dev(w.users[0]))],
+                   ids, sc)
+    hids = np.empty(k, np.uint32)
+    hsc = np.empty(k, np.float32)
+    ebr.score_topk(ix, cross, [ebr.Query(h_u=w.h_u[0].copy(), k=k, user_vals=w.users[0].copy())],
+                   hids, hsc, io=ebr.IO_HOST)
+    ref, tol = ref_scores(w, 0, post)
+    check_topk(hids, hsc, ref, tol, k)
+    assert set(hids.tolist()) == set(ids.cpu().numpy().view(np.uint32).tolist())
+
+
+def test_zero_cross_weights_reduce_to_dual_tower():
+    w, post, ix, cross = _setup("single_fp32_2m", 80_000, seed=5)
+    k = 200
+    zero = dev(np.zeros(w.n_keys, np.float32))
+    ids = torch.empty(k, dtype=torch.int32, device=DEV)
+    sc = torch.empty(k, dtype=torch.float32, device=DEV)
+    ebr.score_topk(ix, None, [ebr.Query(h_u=dev(w.h_u[0]), k=k, q_w=zero)], ids, sc)
+    ref = w.emb.astype(np.float64) @ w.h_u[0].astype(np.float64)
+    tol = 1e-5 * np.maximum(np.abs(ref), np.abs(w.emb.astype(np.float64)) @ np.abs(
+        w.h_u[0].astype(np.float64)))
+    check_topk(ids.cpu().numpy().view(np.uint32), sc.cpu().numpy(), ref, tol, k)
+
+
+def test_rejects_bad_k():
+    w, post, ix, cross = _setup("single_fp32_10k", 1000, seed=0)
+    ids = torch.empty(10, dtype=torch.int32, device=DEV)
+    sc = torch.empty(10, dtype=torch.float32, device=DEV)
+    for k in (0, 9000):
+        with pytest.raises(ebr.EbrError) as e:
+            ebr.score_topk(ix, cross, [ebr.Query(h_u=dev(w.h_u[0]), k=k,
+                                                 user_vals=dev(w.users[0]))], ids, sc)
+        assert e.value.code == ebr.EBR_EINVAL
+
+
+# --------------------------------------------------------- quantisers
+
+def test_bf16_converter_matches_oracle():
+    rng = np.random.default_rng(7)
+    x = np.concatenate([
+        (rng.standard_normal(200_000) * 10.0 ** rng.integers(-38, 38, 200_000)).astype(np.float32),
+        oracle.bf16_value(np.arange(1 << 16, dtype=np.uint32).astype(np.uint16)),
+        (np.arange(1 << 16, dtype=np.uint32) << 16 | 0x8000).view(np.float32),  # halfway points
+    ]).astype(np.float32)
+    x = x[~np.isnan(x)]
+    out = torch.empty(x.size, dtype=torch.int16, device=DEV)
+    ebr.quantize(dev(x), "bf16", out)
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint16), oracle.bf16_rne(x))
+
+
+def test_fp8_converter_matches_oracle():
+    rng = np.random.default_rng(8)
+    codes = np.arange(256, dtype=np.uint8)
+    vals = oracle.fp8_e4m3_value(codes)
+    fin = vals[~np.isnan(vals)]
+    mids = (np.sort(fin)[1:] + np.sort(fin)[:-1]) / 2  # halfway points (exact in float32)
+    x = np.concatenate([fin, mids, rng.standard_normal(100_000) * 10.0 ** rng.uniform(
+        -5, 3, 100_000), [500.0, -1e6, 448.0, 464.0, 470.0]]).astype(np.float32)
+    out = torch.empty(x.size, dtype=torch.uint8, device=DEV)
+    ebr.quantize(dev(x), "fp8e4m3", out)
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.fp8_e4m3_rne_sat(x))
+
+
+def test_index_quantised_tables_match_oracle():
+    w = make_workload("fp8_10m", n_ads=20_000, seed=1)
+    pk, pa = w.postings()
+    ix8 = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype="fp8e4m3")
+    q, s = ix8.export_emb()
+    rq, rs = oracle.quantize_fp8_rows(w.emb)
+    np.testing.assert_array_equal(s, rs)
+    np.testing.assert_array_equal(q, rq)
+    ixb = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype="bf16")
+    qb, _ = ixb.export_emb()
+    np.testing.assert_array_equal(qb.reshape(-1), oracle.bf16_rne(w.emb.reshape(-1)))
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8e4m3"])
+def test_quantised_scan_with_rescoring_reaches_full_recall(dtype):
+    w, post, ix, cross = _setup("fp8_10m", 200_000, seed=6, dtype=dtype)
+    k = 500
+    ids = torch.empty(k, dtype=torch.int32, device=DEV)
+    sc = torch.empty(k, dtype=torch.float32, device=DEV)
+    ebr.score_topk(ix, cross, [ebr.Query(h_u=dev(w.h_u[0]), k=k, user_vals=dev(w.users[0]))],
+                   ids, sc)
+    ref, tol = ref_scores(w, 0, post)
+    got = ids.cpu().numpy().view(np.uint32)
+    assert recall(got, ref, tol, k) == 1.0
+    check_topk(got, sc.cpu().numpy(), ref, tol, k)
