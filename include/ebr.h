@@ -222,6 +222,37 @@ int ebr_wide_scores(const ebr_index *ix, const ebr_cross *cross, const ebr_query
  */
 int ebr_quantize(const float *x, uint64_t n, ebr_dtype dtype, void *out, void *stream);
 
+/* ------------------------------------------------------- no-allocation form */
+/*
+ * Allocation-free scan + top-K.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- a serving process
+ * whose device memory is owned up front by another allocator (a framework's
+ * caching pool or a fixed HBM budget), or a latency-critical thread that
+ * cannot afford cudaMalloc's implicit device-wide synchronisation.
+ *
+ * Computes s[a] = <h_u, emb[a]> (+ wide[a] when wide != NULL) for every ad
+ * and returns the k best, like ebr_score_topk: out_ids/out_scores[k] by score
+ * descending then id ascending, padded with (0xFFFFFFFF, -inf) past the
+ * number of eligible ads.  All pointers are device pointers on `device`:
+ * emb [n_ads][d] FP32 row-major, h_u [d], wide [n_ads] or NULL, filter
+ * (bit a of word a >> 6 keeps ad a) or NULL.  d is 4, 8, 16, 32, 64 or 128;
+ * 1 <= k <= 1024, larger k returns EBR_EINVAL.
+ *
+ * It allocates nothing: its scratch is a static device array of 1.25 MiB
+ * (candidates of up to 160 CTAs x 1024, plus a 64-byte control block), held by
+ * every GPU that loads this library until the process exits.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress),
+ * so make the first call on each device before any stream capture.  Every
+ * call clears the control block and reuses the array, so calls whose work
+ * overlaps on the GPU (different streams, or different host threads without
+ * ordering) race and corrupt each other's results; order them on one stream.
+ * Stream-ordered: returns before the GPU is done; device-side status is not
+ * reported.
+ */
+int ebr_scan_topk_noalloc(const float *emb, uint32_t n_ads, uint32_t d, const float *h_u,
+                          const float *wide, const uint64_t *filter, uint32_t k,
+                          uint32_t *out_ids, float *out_scores, int device, void *stream);
+
 /* ------------------------------------------------------------ profiling */
 /*
  * Per-stage device time of ebr_score_topk calls on one index, measured with

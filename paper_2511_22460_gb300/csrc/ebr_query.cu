@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <array>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "ebr_device.cuh"
@@ -1263,4 +1264,146 @@ extern "C" int ebr_profile_read(ebr_index *ix, ebr_profile *out) {
   out->launches = ix->launches;
   out->lib_launches = ix->lib_launches;
   return EBR_OK;
+}
+
+// =====================================================================
+// Allocation-free variant of the scan + top-K (ebr_scan_topk_noalloc)
+// =====================================================================
+// For callers that must not allocate device memory: a serving process whose
+// device memory is owned up front by another allocator (a framework's caching
+// pool, a fixed HBM budget), or a latency-critical thread that cannot afford
+// cudaMalloc's implicit device-wide synchronisation.  Its scratch (the
+// per-CTA candidate lists and the control block) lives in the file-scope
+// array below, which every GPU that loads this library holds until exit.
+namespace ebr {
+namespace {
+
+constexpr uint32_t kNoAllocMaxK = 1024;     // largest K accepted
+constexpr uint32_t kNoAllocMaxGrid = 160;   // CTAs of the scan (>= SM count of a GB300)
+constexpr uint32_t kNoAllocCtrlWords = 8;   // 64 bytes reserved for the Ctrl block
+constexpr size_t kNoAllocWords = kNoAllocCtrlWords + (size_t)kNoAllocMaxGrid * kNoAllocMaxK;
+// 8 * (8 + 160 * 1024) bytes = 1.25 MiB.
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocWords];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+int g_noalloc_sms[kNoAllocMaxDevices] = {0};
+
+template <int D>
+int noalloc_launch(const ScanArgs &a0, int sms, cudaStream_t st) {
+  using Sh = ScanShape<float, D>;
+  ScanArgs a = a0;
+  a.cap = a.k + std::max<uint32_t>(a.k, 2 * Sh::kTileRows);
+  a.cap = (a.cap + 255) / 256 * 256;
+  const size_t cand_bytes = (size_t)2 * a.cap * 8;
+  uint32_t stages = 4;
+  while (stages > 2 && cand_bytes + (size_t)stages * Sh::kStageBytes > 200 * 1024) stages--;
+  a.stages = stages;
+  const size_t smem = cand_bytes + (size_t)stages * Sh::kStageBytes;
+  const uint32_t n_tiles = (a.n_ads + Sh::kTileRows - 1) / Sh::kTileRows;
+  const int grid = (int)std::min<uint32_t>(std::min<uint32_t>((uint32_t)sms, kNoAllocMaxGrid),
+                                           n_tiles);
+  auto kern = k_scan_topk<float, D, MODE_TOPK>;
+  EBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  kern<<<grid, kScanThreads, smem, st>>>(a);
+  EBR_CUDA_TRY(cudaGetLastError());
+  return EBR_OK;
+}
+
+}  // namespace
+}  // namespace ebr
+
+extern "C" int ebr_scan_topk_noalloc(const float *emb, uint32_t n_ads, uint32_t d,
+                                     const float *h_u, const float *wide,
+                                     const uint64_t *filter, uint32_t k, uint32_t *out_ids,
+                                     float *out_scores, int device, void *stream) {
+  clear_error();
+  if (!emb || !h_u || !out_ids || !out_scores || n_ads == 0) {
+    set_error("ebr_scan_topk_noalloc: null pointer or n_ads == 0");
+    return EBR_EINVAL;
+  }
+  if (k == 0 || k > kNoAllocMaxK) {
+    set_error("ebr_scan_topk_noalloc: k = %u is outside 1..%u (the static scratch holds %u "
+              "candidates per CTA)", k, kNoAllocMaxK, kNoAllocMaxK);
+    return EBR_EINVAL;
+  }
+  if (!(d == 4 || d == 8 || d == 16 || d == 32 || d == 64 || d == 128)) {
+    set_error("ebr_scan_topk_noalloc: d = %u unsupported (4, 8, 16, 32, 64 or 128)", d);
+    return EBR_EINVAL;
+  }
+  if (device < 0 || device >= kNoAllocMaxDevices) {
+    set_error("ebr_scan_topk_noalloc: device %d out of range", device);
+    return EBR_EINVAL;
+  }
+  int prev = 0;
+  EBR_CUDA_TRY(cudaGetDevice(&prev));
+  if (prev != device) EBR_CUDA_TRY(cudaSetDevice(device));
+  void *base = nullptr;
+  int sms = 0;
+  {
+    // One-time set-up per device, with that device current: resolve the
+    // device address of the static scratch array (the host-side symbol is
+    // only a stand-in and must never reach a kernel).
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+      void *p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&g_noalloc_sms[device], cudaDevAttrMultiProcessorCount,
+                                   device);
+      if (e != cudaSuccess) {
+        set_error("ebr_scan_topk_noalloc: set-up failed: %s", cudaGetErrorString(e));
+        if (prev != device) cudaSetDevice(prev);
+        return EBR_ECUDA;
+      }
+      g_noalloc_addr[device] = p;
+    }
+    base = g_noalloc_addr[device];
+    sms = g_noalloc_sms[device];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Ctrl *ctrl = reinterpret_cast<Ctrl *>(base);
+  uint64_t *cand = reinterpret_cast<uint64_t *>(base) + kNoAllocCtrlWords;
+  int rc = EBR_OK;
+  // The array keeps the previous call's contents: clear the control block.
+  cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st);
+  if (e != cudaSuccess) {
+    set_error("ebr_scan_topk_noalloc: %s", cudaGetErrorString(e));
+    rc = EBR_ECUDA;
+  }
+  if (rc == EBR_OK) {
+    ScanArgs a;
+    memset(&a, 0, sizeof(a));
+    a.emb = emb;
+    a.h_u = h_u;
+    a.wide = wide;
+    a.filter = filter;
+    a.n_ads = n_ads;
+    a.k = k;
+    a.cand_out = cand;
+    a.ctrl = ctrl;
+    switch (d) {
+      case 4: rc = noalloc_launch<4>(a, sms, st); break;
+      case 8: rc = noalloc_launch<8>(a, sms, st); break;
+      case 16: rc = noalloc_launch<16>(a, sms, st); break;
+      case 32: rc = noalloc_launch<32>(a, sms, st); break;
+      case 64: rc = noalloc_launch<64>(a, sms, st); break;
+      default: rc = noalloc_launch<128>(a, sms, st); break;
+    }
+  }
+  if (rc == EBR_OK) {
+    uint32_t p2 = 1;
+    while (p2 < k) p2 <<= 1;
+    k_final_select<<<1, kFinalThreads, (size_t)p2 * 8, st>>>(cand, ctrl, 0, k, k, out_ids,
+                                                             out_scores, nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_error("ebr_scan_topk_noalloc: %s", cudaGetErrorString(e));
+      rc = EBR_ECUDA;
+    }
+  }
+  if (prev != device) cudaSetDevice(prev);
+  return rc;
 }

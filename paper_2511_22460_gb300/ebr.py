@@ -85,6 +85,8 @@ ebr_score_topk = _sig("ebr_score_topk", i32, [vp, vp, C.POINTER(QueryC), u32, vp
 ebr_score_all = _sig("ebr_score_all", i32, [vp, vp, C.POINTER(QueryC), vp, vp])
 ebr_wide_scores = _sig("ebr_wide_scores", i32, [vp, vp, C.POINTER(QueryC), vp, vp])
 ebr_quantize = _sig("ebr_quantize", i32, [vp, u64, i32, vp, vp])
+ebr_scan_topk_noalloc = _sig("ebr_scan_topk_noalloc", i32,
+                             [vp, u32, u32, vp, vp, vp, u32, vp, vp, i32, vp])
 ebr_profile_enable = _sig("ebr_profile_enable", i32, [vp, i32])
 ebr_profile_read = _sig("ebr_profile_read", i32, [vp, C.POINTER(Profile)])
 
@@ -282,3 +284,10 @@ def wide_scores(index: Index, cross: Optional[Cross], query: Query, out_wide, st
 def quantize(x, dtype, out, stream=None):
     dt = _DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
     _check(ebr_quantize(ptr(x), int(x.numel()), dt, ptr(out), stream_ptr(stream)), "ebr_quantize")
+
+
+def scan_topk_noalloc(emb, h_u, wide, filt, k, out_ids, out_scores, device=0, stream=None):
+    """Allocation-free scan + top-K over caller-owned device buffers."""
+    _check(ebr_scan_topk_noalloc(ptr(emb), int(emb.shape[0]), int(emb.shape[1]), ptr(h_u),
+                                 ptr(wide), ptr(filt), int(k), ptr(out_ids), ptr(out_scores),
+                                 device, stream_ptr(stream)), "ebr_scan_topk_noalloc")
