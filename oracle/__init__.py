@@ -65,6 +65,8 @@ def _load():
             lib.orc_scores_postings.restype = i32
             lib.orc_scores_postings.argtypes = [u32, u32, vp, vp, u32, u64, vp, vp, u32, vp,
                                                 vp, vp]
+            lib.orc_unique_pairs.restype = C.c_int64
+            lib.orc_unique_pairs.argtypes = [u64, vp, vp, vp, vp]
             lib.orc_build_index.restype = i32
             lib.orc_build_index.argtypes = [u32, u32, u64, vp, vp, vp]
             lib.orc_free_index.restype = None
@@ -158,13 +160,30 @@ def expand(cross: Cross, user):
     return out
 
 
-def scores_postings(h_u, emb, n_keys, post_key, post_ad, q_key, q_w):
-    """O2: FP64 scores from uncompressed postings and the query's (key, w_hat) list."""
+def unique_pairs(post_key, post_ad):
+    """Distinct (key, ad) pairs: L is a 0/1 matrix, a repeated pair is one non-zero."""
+    lib = _load()
+    post_key, post_ad = _c(post_key, np.uint32), _c(post_ad, np.uint32)
+    ok = np.empty(max(post_key.size, 1), np.uint32)
+    oa = np.empty(max(post_key.size, 1), np.uint32)
+    m = lib.orc_unique_pairs(post_key.size, _p(post_key), _p(post_ad), _p(ok), _p(oa))
+    if m < 0:
+        raise MemoryError
+    return ok[:m].copy(), oa[:m].copy()
+
+
+def scores_postings(h_u, emb, n_keys, post_key, post_ad, q_key, q_w, assume_unique=False):
+    """O2: FP64 scores from uncompressed postings and the query's (key, w_hat) list.
+
+    Repeated (key, ad) pairs are collapsed first unless the caller guarantees
+    there are none (workload postings are distinct by construction)."""
     lib = _load()
     emb = _c(emb, np.float32)
     n, d = emb.shape
     h_u = _c(h_u, np.float32)
     post_key, post_ad = _c(post_key, np.uint32), _c(post_ad, np.uint32)
+    if not assume_unique:
+        post_key, post_ad = unique_pairs(post_key, post_ad)
     q_key, q_w = _c(q_key, np.uint32), _c(q_w, np.float64)
     out = np.empty(n, dtype=np.float64)
     rc = lib.orc_scores_postings(n, d, _p(h_u), _p(emb), n_keys, post_key.size, _p(post_key),
@@ -272,7 +291,8 @@ def score_query(w, b: int, cross: Cross = None, postings=None):
     wh = expand(cross, w.users[b])
     keys = np.nonzero(wh)[0].astype(np.uint32)
     pk, pa = postings if postings is not None else w.postings()
-    return scores_postings(w.h_u[b], w.emb, w.n_keys, pk, pa, keys, wh[keys])
+    # one value per ad field and disjoint key ranges per field: pairs are distinct
+    return scores_postings(w.h_u[b], w.emb, w.n_keys, pk, pa, keys, wh[keys], assume_unique=True)
 
 
 def tolerance(scores_ref, cond, rel=1e-5):

@@ -131,8 +131,10 @@ int orc_expand(const orc_cross *c, const uint32_t *key_off, const uint32_t *user
 
 /*
  * scores[a] = <h_u, h_a> + sum over query entries (k, w) of w * L[a, k],
- * walking the uncompressed posting pairs (key, ad).  Duplicate query keys add
- * (linearity).  This is the product L w~ of Sec. 3.4 evaluated key by key.
+ * walking the uncompressed posting pairs (key, ad), which must be distinct
+ * (each is one non-zero of the 0/1 matrix L; orc_unique_pairs collapses
+ * repeats).  Duplicate query keys add (linearity).  This is the product L w~
+ * of Sec. 3.4 evaluated key by key.
  */
 int orc_scores_postings(uint32_t n_ads, uint32_t d, const float *h_u, const float *emb,
                         uint32_t n_keys, uint64_t nnz, const uint32_t *post_key,
@@ -155,6 +157,29 @@ int orc_scores_postings(uint32_t n_ads, uint32_t d, const float *h_u, const floa
   }
   free(w_of_key);
   return ORC_OK;
+}
+
+/*
+ * L is a 0/1 matrix (Sec. 3.3): a (key, ad) pair listed more than once is
+ * still one non-zero.  Writes the distinct pairs (sorted by key, then ad)
+ * and returns their number.
+ */
+static int cmp_u64(const void *x, const void *y);
+int64_t orc_unique_pairs(uint64_t nnz, const uint32_t *key, const uint32_t *ad,
+                         uint32_t *out_key, uint32_t *out_ad) {
+  uint64_t *kv = (uint64_t *)malloc((nnz ? nnz : 1) * sizeof(uint64_t));
+  if (!kv) return ORC_ENOMEM;
+  for (uint64_t e = 0; e < nnz; e++) kv[e] = ((uint64_t)key[e] << 32) | ad[e];
+  qsort(kv, nnz, sizeof(uint64_t), cmp_u64);
+  uint64_t m = 0;
+  for (uint64_t e = 0; e < nnz; e++) {
+    if (e > 0 && kv[e] == kv[e - 1]) continue;
+    out_key[m] = (uint32_t)(kv[e] >> 32);
+    out_ad[m] = (uint32_t)kv[e];
+    m++;
+  }
+  free(kv);
+  return (int64_t)m;
 }
 
 /* ------------------------------------------------------------------ */

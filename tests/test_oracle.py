@@ -164,6 +164,25 @@ def test_linearity_duplicates_and_one_hot():
     np.testing.assert_array_equal(oh[~members], 0.0)
 
 
+def test_repeated_pairs_count_once():
+    # L is binary (Sec. 3.3): listing a (key, ad) pair twice changes nothing.
+    rng = np.random.default_rng(12)
+    n_keys, n_ads = 40, 300
+    pk = rng.integers(0, n_keys, 2000).astype(np.uint32)
+    pa = rng.integers(0, n_ads, 2000).astype(np.uint32)
+    pk2, pa2 = np.concatenate([pk, pk[:700]]), np.concatenate([pa, pa[:700]])
+    w_k = rng.standard_normal(n_keys)
+    keys = np.arange(n_keys, dtype=np.uint32)
+    h = np.zeros(4, np.float32)
+    emb = np.zeros((n_ads, 4), np.float32)
+    dense = np.zeros((n_ads, n_keys))
+    dense[pa, pk] = 1.0  # 0/1 matrix, repeats collapse
+    got = oracle.scores_postings(h, emb, n_keys, pk2, pa2, keys, w_k)
+    np.testing.assert_allclose(got, dense @ w_k, rtol=1e-13, atol=1e-13)
+    uk, ua = oracle.unique_pairs(pk2, pa2)
+    assert len(uk) == len(set(zip(pk.tolist(), pa.tolist())))
+
+
 def test_postings_of_each_field_partition_the_ads():
     w = _small()
     pk, pa = w.postings()
