@@ -81,6 +81,13 @@ typedef struct {
 } ebr_index_desc;
 
 /*
+ * Besides the paper's key-major arrays, the index keeps a window-major view
+ * of the same blocks (per group, ordered by (window h = ad >> 8, key k), each
+ * with its key and its 2^g value bytes, plus per-window offsets).  Requests
+ * whose query covers the whole key space (dense w^ or raw user features) walk
+ * that view window by window inside the scan; sparse key lists walk the
+ * key-major arrays with Algorithm 2.
+ *
  * Build the compressed inverted list of Algorithm 1 (Block Grouping by
  * ad >> 8, Logarithmic Categorization into groups g = ceil(log2 n) = 0..8,
  * Block Compression to one 24-bit header per block plus one byte per ad,
@@ -101,6 +108,8 @@ typedef struct {
   uint64_t index_bytes;         /* sum_g 4*(n_keys+1) + 4*n_blocks[g] + 2^g*n_blocks[g] */
   uint64_t emb_bytes;           /* bytes of the scanned embedding table (+ FP8 row scales) */
   float build_ms;               /* device time of the index build (Algorithm 1 only) */
+  float window_view_ms;         /* device time of the window-major view (below) */
+  uint64_t window_view_bytes;   /* its size: per-block keys + value bytes + window offsets */
 } ebr_index_info;
 int ebr_index_get_info(const ebr_index *ix, ebr_index_info *out);
 
@@ -180,7 +189,13 @@ typedef struct {
   const float *q_w;            /* [n_q] or [n_keys] */
   const uint64_t *filter;      /* [ceil(N / 64)] or NULL */
   uint32_t k;
+  uint32_t flags;              /* EBR_QF_* bits */
 } ebr_query;
+
+/* Walk the key-major arrays with Algorithm 2 (global scatter into a per-ad
+ * score buffer) even when the query is dense; by default dense queries use
+ * the fused window-major scan and sparse key lists use Algorithm 2. */
+#define EBR_QF_KEY_MAJOR 1u
 
 #define EBR_IO_DEVICE 0   /* all query arrays and outputs are device pointers; stream-ordered */
 #define EBR_IO_HOST 1     /* all query arrays and outputs are host pointers; the call copies them

@@ -20,7 +20,8 @@ LIB = os.path.join(HERE, "libebr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
-SOURCES = ["ebr_common.cu", "ebr_index.cu", "ebr_query.cu", "ebr_batch.cu", "ebr_serve.cu"]
+SOURCES = ["ebr_common.cu", "ebr_index.cu", "ebr_query.cu", "ebr_fused.cu", "ebr_batch.cu",
+           "ebr_serve.cu"]
 
 
 def _nvcc() -> str:

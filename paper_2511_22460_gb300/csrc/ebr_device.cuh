@@ -151,4 +151,119 @@ __device__ uint64_t cta_radix_select(const uint64_t *buf, uint32_t n, uint32_t n
   return prefix;
 }
 
+// ---------------------------------------------- histogram threshold (K-th bound)
+// hist_c[256] counts candidates by the top 8 bits of ord(score), hist_f[65536]
+// by the top 16 bits.  Every counted candidate is a distinct ad, so if at
+// least K counted candidates have ord(score) >= T, the K-th best score
+// overall is >= T and anything below T can be dropped.  Returns the largest
+// such T of the form (coarse, fine) << 16, as a key threshold (T << 32), or 0.
+// Counts only grow, so racy snapshots give a smaller, still valid, bound.
+// Called by one full warp.
+__device__ __forceinline__ uint64_t hist_threshold(const uint32_t *hist_c, const uint32_t *hist_f,
+                                                   uint32_t K) {
+  const int lane = threadIdx.x & 31;
+  uint32_t c[8], tot = 0;
+#pragma unroll
+  for (int e = 0; e < 8; e++) {
+    c[e] = __ldcg(hist_c + 255 - 8 * lane - e);
+    tot += c[e];
+  }
+  uint32_t incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  int cb = -1;
+  uint32_t above_c = 0;
+  {
+    uint32_t acc = incl - tot;
+    int found = -1;
+    uint32_t fa = 0;
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+      if (found < 0 && acc < K && K <= acc + c[e]) {
+        found = 255 - 8 * lane - e;
+        fa = acc;
+      }
+      acc += c[e];
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, found >= 0);
+    if (!bal) return 0ull;
+    const int src = __ffs(bal) - 1;
+    cb = __shfl_sync(0xffffffffu, found, src);
+    above_c = __shfl_sync(0xffffffffu, fa, src);
+  }
+  const uint32_t *hf = hist_f + (uint32_t)cb * 256u;
+  tot = 0;
+#pragma unroll
+  for (int e = 0; e < 8; e++) {
+    c[e] = __ldcg(hf + 255 - 8 * lane - e);
+    tot += c[e];
+  }
+  incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  uint32_t acc = above_c + incl - tot;
+  int found = -1;
+#pragma unroll
+  for (int e = 0; e < 8; e++) {
+    if (found < 0 && acc < K && K <= acc + c[e]) found = 255 - 8 * lane - e;
+    acc += c[e];
+  }
+  const uint32_t bal = __ballot_sync(0xffffffffu, found >= 0);
+  if (!bal) return ((uint64_t)((uint32_t)cb << 24)) << 32;  // coarse bound only
+  const int fb = __shfl_sync(0xffffffffu, found, __ffs(bal) - 1);
+  return ((uint64_t)(((uint32_t)cb << 24) | ((uint32_t)fb << 16))) << 32;
+}
+
+// ------------------------------------------------------- embedding rows
+// Scan element types: a 16-byte vector holds kVec elements, widened to float.
+template <typename Elt> struct EltTraits;
+template <> struct EltTraits<float> {
+  static constexpr int kBytes = 4;
+  static constexpr int kVec = 4;  // elements per 16-byte vector
+  __device__ static __forceinline__ void load(const uint4 &v, float *f) {
+    f[0] = __uint_as_float(v.x);
+    f[1] = __uint_as_float(v.y);
+    f[2] = __uint_as_float(v.z);
+    f[3] = __uint_as_float(v.w);
+  }
+};
+struct Bf16Tag {};
+template <> struct EltTraits<Bf16Tag> {
+  static constexpr int kBytes = 2;
+  static constexpr int kVec = 8;
+  __device__ static __forceinline__ void load(const uint4 &v, float *f) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      f[2 * i] = __uint_as_float(w[i] << 16);
+      f[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+    }
+  }
+};
+struct Fp8Tag {};
+// E4M3 byte -> float, from the format: bias 7, exponent field 0 subnormal.
+__device__ __forceinline__ float e4m3_to_f32(uint32_t c) {
+  const uint32_t s = (c & 0x80u) << 24, e = (c >> 3) & 15u, m = c & 7u;
+  if (e == 0) return __uint_as_float(s | __float_as_uint((float)m * 0.001953125f));  // m * 2^-9
+  return __uint_as_float(s | ((e + 120u) << 23) | (m << 20));
+}
+template <> struct EltTraits<Fp8Tag> {
+  static constexpr int kBytes = 1;
+  static constexpr int kVec = 16;
+  __device__ static __forceinline__ void load(const uint4 &v, float *f) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+      for (int k = 0; k < 4; k++) f[4 * i + k] = e4m3_to_f32((w[i] >> (8 * k)) & 255u);
+  }
+};
+
+
 }  // namespace ebr

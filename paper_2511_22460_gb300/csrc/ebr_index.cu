@@ -109,6 +109,48 @@ __global__ void k_emit(const uint64_t *__restrict__ x, const uint32_t *__restric
   }
 }
 
+// Window-major view of the same blocks: sort key (g, h, k) per block, with the
+// block's position in the group-sorted order as payload.
+__global__ void k_wm_keys(const uint64_t *__restrict__ x, const uint32_t *__restrict__ start,
+                          const uint32_t *__restrict__ perm, const uint8_t *__restrict__ grp_sorted,
+                          uint32_t nb, uint64_t *__restrict__ skey, uint32_t *__restrict__ sval) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < nb; p += gridDim.x * blockDim.x) {
+    const uint64_t w0 = x[start[perm[p]]];
+    const uint64_t h = (w0 >> 8) & 0xFFFFFFull, k = w0 >> 32;
+    skey[p] = ((uint64_t)grp_sorted[p] << 56) | (h << 32) | k;
+    sval[p] = p;
+  }
+}
+
+struct WmArgs {
+  const uint8_t *values[kGroups];
+  uint32_t *wkey[kGroups];
+  uint8_t *wvals[kGroups];
+  uint32_t *wcnt;  // [9][n_win + 1]
+  uint32_t n_win;
+  unsigned long long gstart[kGroups + 1];
+};
+
+// q-th block in (g, h, k) order: store its key and copy its 2^g value bytes.
+__global__ void k_wm_emit(const uint64_t *__restrict__ skey, const uint32_t *__restrict__ sval,
+                          uint32_t nb, WmArgs a) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nb; q += gridDim.x * blockDim.x) {
+    const uint64_t sk = skey[q];
+    const uint32_t g = (uint32_t)(sk >> 56), h = (uint32_t)((sk >> 32) & 0xFFFFFFu);
+    const uint64_t rank = q - a.gstart[g], src = sval[q] - a.gstart[g];
+    a.wkey[g][rank] = (uint32_t)sk;
+    const uint8_t *from = a.values[g] + (src << g);
+    uint8_t *to = a.wvals[g] + (rank << g);
+    if (g >= 2) {
+      for (uint32_t s = 0; s < (1u << g); s += 4)
+        *reinterpret_cast<uint32_t *>(to + s) = *reinterpret_cast<const uint32_t *>(from + s);
+    } else {
+      for (uint32_t s = 0; s < (1u << g); s++) to[s] = from[s];
+    }
+    atomicAdd(&a.wcnt[(uint64_t)g * (a.n_win + 1) + h], 1u);
+  }
+}
+
 inline int grid_for(uint64_t n, int threads = 256, int cap = 1 << 16) {
   uint64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -127,8 +169,10 @@ static int build_impl(const ebr_index_desc *desc, ebr_index *ix, cudaStream_t st
   const uint64_t nnz = desc->nnz;
   const uint32_t n_keys = desc->n_keys, n_ads = desc->n_ads;
   DevBuf d_key, d_ad, w0, w1, tmp, bs, bid, start, grp, grp2, perm, perm2, cnt, gcount, flags;
+  DevBuf skey, skey2, sval, sval2, wcnt;
   std::vector<DevBuf *> temps = {&d_key, &d_ad, &w0, &w1, &tmp, &bs, &bid, &start,
-                                 &grp, &grp2, &perm, &perm2, &cnt, &gcount, &flags};
+                                 &grp, &grp2, &perm, &perm2, &cnt, &gcount, &flags,
+                                 &skey, &skey2, &sval, &sval2, &wcnt};
   auto cleanup = [&]() {
     for (auto *b : temps) dev_free(*b);
   };
@@ -296,6 +340,65 @@ static int build_impl(const ebr_index_desc *desc, ebr_index *ix, cudaStream_t st
     BCUDA(cudaEventRecord(e1, st));
     BCUDA(cudaEventSynchronize(e1));
     BCUDA(cudaEventElapsedTime(&ix->build_ms, e0, e1));
+
+    // ---- window-major view of the same blocks (for the fused dense scan)
+    {
+      const uint32_t n_win = (n_ads + 255) / 256;
+      ix->n_win = n_win;
+      BCUDA(cudaEventRecord(e0, st));
+      BTRY(dev_alloc(ix->mem_wkey, hdr_total + 256));
+      BTRY(dev_alloc(ix->mem_wvals, val_total + 256));
+      BTRY(dev_alloc(ix->mem_winptr, (size_t)kGroups * (n_win + 1) * 4));
+      BTRY(dev_alloc(wcnt, (size_t)kGroups * (n_win + 1) * 4));
+      BCUDA(cudaMemsetAsync(wcnt.p, 0, (size_t)kGroups * (n_win + 1) * 4, st));
+      WmArgs wa;
+      wa.wcnt = (uint32_t *)wcnt.p;
+      wa.n_win = n_win;
+      for (int g = 0; g < kGroups; g++) {
+        ix->wkey[g] = (uint32_t *)((char *)ix->mem_wkey.p + hdr_off[g]);
+        ix->wvals[g] = (uint8_t *)ix->mem_wvals.p + val_off[g];
+        ix->win_ptr[g] = (uint32_t *)ix->mem_winptr.p + (size_t)g * (n_win + 1);
+        wa.values[g] = ix->values[g];
+        wa.wkey[g] = ix->wkey[g];
+        wa.wvals[g] = ix->wvals[g];
+        wa.gstart[g] = ea.gstart[g];
+      }
+      wa.gstart[kGroups] = ea.gstart[kGroups];
+      if (nb) {
+        BTRY(dev_alloc(skey, (size_t)nb * 8));
+        BTRY(dev_alloc(skey2, (size_t)nb * 8));
+        BTRY(dev_alloc(sval, (size_t)nb * 4));
+        BTRY(dev_alloc(sval2, (size_t)nb * 4));
+        k_wm_keys<<<grid_for(nb), 256, 0, st>>>(x, (const uint32_t *)start.p,
+                                                (const uint32_t *)perm2.p,
+                                                (const uint8_t *)grp2.p, nb, (uint64_t *)skey.p,
+                                                (uint32_t *)sval.p);
+        BCUDA(cudaGetLastError());
+        size_t t3 = 0;
+        BCUDA(cub::DeviceRadixSort::SortPairs(nullptr, t3, (const uint64_t *)skey.p,
+                                              (uint64_t *)skey2.p, (const uint32_t *)sval.p,
+                                              (uint32_t *)sval2.p, (int)nb, 0, 60, st));
+        BTRY(dev_reserve(tmp, t3 + 256));
+        BCUDA(cub::DeviceRadixSort::SortPairs(tmp.p, t3, (const uint64_t *)skey.p,
+                                              (uint64_t *)skey2.p, (const uint32_t *)sval.p,
+                                              (uint32_t *)sval2.p, (int)nb, 0, 60, st));
+        k_wm_emit<<<grid_for(nb), 256, 0, st>>>((const uint64_t *)skey2.p,
+                                                (const uint32_t *)sval2.p, nb, wa);
+        BCUDA(cudaGetLastError());
+      }
+      size_t t4 = 0;
+      BCUDA(cub::DeviceScan::ExclusiveSum(nullptr, t4, (uint32_t *)nullptr, (uint32_t *)nullptr,
+                                          (int)(n_win + 1), st));
+      BTRY(dev_reserve(tmp, t4 + 256));
+      for (int g = 0; g < kGroups; g++) {
+        size_t t5 = t4;
+        BCUDA(cub::DeviceScan::ExclusiveSum(tmp.p, t5, (uint32_t *)wcnt.p + (size_t)g * (n_win + 1),
+                                            ix->win_ptr[g], (int)(n_win + 1), st));
+      }
+      BCUDA(cudaEventRecord(e1, st));
+      BCUDA(cudaEventSynchronize(e1));
+      BCUDA(cudaEventElapsedTime(&ix->wm_build_ms, e0, e1));
+    }
   }
   cleanup();
   cudaEventDestroy(e0);
@@ -335,12 +438,15 @@ extern "C" void ebr_index_free(ebr_index *ix) {
   dev_free(ix->mem_keys);
   dev_free(ix->mem_header);
   dev_free(ix->mem_values);
+  dev_free(ix->mem_wkey);
+  dev_free(ix->mem_wvals);
+  dev_free(ix->mem_winptr);
   dev_free(ix->emb_f32);
   dev_free(ix->emb_q);
   dev_free(ix->emb_scale);
   Workspace &w = ix->ws;
   for (DevBuf *b : {&w.wide, &w.w_dense, &w.lens, &w.scan, &w.work, &w.cub_tmp, &w.cand,
-                    &w.ctrl, &w.io_in, &w.io_out})
+                    &w.ctrl, &w.io_in, &w.io_out, &w.hist})
     dev_free(*b);
   if (w.host_ctrl) cudaFreeHost(w.host_ctrl);
   for (auto *v : {&ix->prof_pending, &ix->prof_pool})
@@ -415,6 +521,8 @@ extern "C" int ebr_index_get_info(const ebr_index *ix, ebr_index_info *out) {
   uint64_t per = ix->dtype == EBR_F32 ? 4 : (ix->dtype == EBR_BF16 ? 2 : 1);
   out->emb_bytes = (uint64_t)ix->n_ads * ix->d * per + (ix->dtype == EBR_FP8E4M3 ? 4ull * ix->n_ads : 0);
   out->build_ms = ix->build_ms;
+  out->window_view_ms = ix->wm_build_ms;
+  out->window_view_bytes = bytes - 4ull * kGroups * (ix->n_keys + 1) + 4ull * kGroups * (ix->n_win + 1);
   return EBR_OK;
 }
 

@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ebr.h"
+#include "ebr.h"
 
 namespace ebr {
 
@@ -70,6 +70,7 @@ struct Workspace {
   DevBuf ctrl;        // Ctrl block (counters, threshold, flags)
   DevBuf io_in;       // staging for host inputs
   DevBuf io_out;      // staging for outputs
+  DevBuf hist;        // uint32 [kHistWords] candidate-score histogram
   void *host_ctrl = nullptr;  // pinned mirror of Ctrl
 };
 
@@ -95,6 +96,15 @@ struct ebr_index {
   uint32_t *header[ebr::kGroups] = {nullptr};
   uint8_t *values[ebr::kGroups] = {nullptr};
   ebr::DevBuf mem_keys, mem_header, mem_values;
+  // Window-major view of the same blocks: per group, blocks ordered by
+  // (window h, key k); wkey = key per block, wvals = its 2^g value bytes,
+  // win_ptr[g][h] = first block of window h.
+  uint32_t n_win = 0;
+  uint32_t *wkey[ebr::kGroups] = {nullptr};
+  uint8_t *wvals[ebr::kGroups] = {nullptr};
+  uint32_t *win_ptr[ebr::kGroups] = {nullptr};
+  ebr::DevBuf mem_wkey, mem_wvals, mem_winptr;
+  float wm_build_ms = 0.f;
   ebr::DevBuf emb_f32;    // float [N][d]
   ebr::DevBuf emb_q;      // bf16 / e4m3 [N][d]
   ebr::DevBuf emb_scale;  // float [N] (FP8)
@@ -121,6 +131,12 @@ struct ebr_cross {
 };
 
 namespace ebr {
+constexpr int kMaxCtasPerSm = 4;  // bound on scan CTAs per SM (candidate buffer sizing)
+int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
+                 const uint64_t *filter, uint32_t k, uint64_t *cand_out, Ctrl *ctrl,
+                 float *all_out, float *wide_out, uint32_t *hist, int max_grid,
+                 cudaStream_t st);
+constexpr size_t kHistWords = 256 + 65536;  // candidate-score histogram (coarse + fine)
 // Launchers implemented in ebr_query.cu, used by the serving loop.
 int query_one(const ebr_index *ix, const ebr_cross *cross, const ebr_query &q, uint32_t *ids,
               float *scores, uint32_t kmax, cudaStream_t st);

@@ -310,49 +310,6 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_scatter(
 // =====================================================================
 enum { MODE_TOPK = 0, MODE_ALL = 1 };
 
-template <typename Elt> struct EltTraits;
-template <> struct EltTraits<float> {
-  static constexpr int kBytes = 4;
-  static constexpr int kVec = 4;  // elements per 16-byte vector
-  __device__ static __forceinline__ void load(const uint4 &v, float *f) {
-    f[0] = __uint_as_float(v.x);
-    f[1] = __uint_as_float(v.y);
-    f[2] = __uint_as_float(v.z);
-    f[3] = __uint_as_float(v.w);
-  }
-};
-struct Bf16Tag {};
-template <> struct EltTraits<Bf16Tag> {
-  static constexpr int kBytes = 2;
-  static constexpr int kVec = 8;
-  __device__ static __forceinline__ void load(const uint4 &v, float *f) {
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-      f[2 * i] = __uint_as_float(w[i] << 16);
-      f[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
-    }
-  }
-};
-struct Fp8Tag {};
-// E4M3 byte -> float, from the format: bias 7, exponent field 0 subnormal.
-__device__ __forceinline__ float e4m3_to_f32(uint32_t c) {
-  const uint32_t s = (c & 0x80u) << 24, e = (c >> 3) & 15u, m = c & 7u;
-  if (e == 0) return __uint_as_float(s | __float_as_uint((float)m * 0.001953125f));  // m * 2^-9
-  return __uint_as_float(s | ((e + 120u) << 23) | (m << 20));
-}
-template <> struct EltTraits<Fp8Tag> {
-  static constexpr int kBytes = 1;
-  static constexpr int kVec = 16;
-  __device__ static __forceinline__ void load(const uint4 &v, float *f) {
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-      for (int k = 0; k < 4; k++) f[4 * i + k] = e4m3_to_f32((w[i] >> (8 * k)) & 255u);
-  }
-};
-
 constexpr int kScanThreads = 256;
 constexpr int kScanWarps = kScanThreads / 32;
 
@@ -374,13 +331,14 @@ struct ScanArgs {
 template <typename Elt, int D>
 struct ScanShape {
   static constexpr int kRowBytes = D * EltTraits<Elt>::kBytes;
-  static constexpr int kTileRows = (32768 / kRowBytes) < 512 ? (32768 / kRowBytes) : 512;
+  static constexpr int kTileRows = (32768 / kRowBytes) < 256 ? (32768 / kRowBytes) : 256;
   static constexpr int kStageBytes = kTileRows * kRowBytes;
   static constexpr int kLPR = D / EltTraits<Elt>::kVec;  // lanes per row
   static constexpr int kRowsPerIter = 32 / kLPR;
   static constexpr int kRowsPerWarp = kTileRows / kScanWarps;
   static_assert(kLPR >= 1 && kLPR <= 32, "unsupported row width");
   static_assert(kRowsPerWarp % kRowsPerIter == 0, "tile split");
+  static_assert(kRowsPerWarp <= 32, "one prefetched row per lane");
 };
 
 template <typename Elt, int D, int MODE>
@@ -435,6 +393,22 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_topk(ScanArgs a) {
   uint64_t thr = 0;
   for (uint32_t j = 0; j < my_tiles; j++) {
     const uint32_t s = j % S, parity = (j / S) & 1u;
+    const uint32_t tile = blockIdx.x + j * gridDim.x;
+    const uint32_t row0 = tile * Sh::kTileRows;
+    const uint32_t rows = min((uint32_t)Sh::kTileRows, a.n_ads - row0);
+    // Per-row side inputs of this warp's rows, one row per lane, fetched before
+    // the wait so their latency overlaps the tile's arrival.
+    float pre_w = 0.f, pre_s = 1.f;
+    bool pre_f = true;
+    {
+      const uint32_t rl = warp * Sh::kRowsPerWarp + lane;
+      if (lane < Sh::kRowsPerWarp && rl < rows) {
+        const uint32_t ad = row0 + rl;
+        if (a.wide) pre_w = a.wide[ad];
+        if (a.scale) pre_s = a.scale[ad];
+        if (a.filter) pre_f = (a.filter[ad >> 6] >> (ad & 63)) & 1ull;
+      }
+    }
     if (tid == 0) {
       if (!mbar_wait_bounded(&s_bar[s], parity, kWaitTimeoutNs)) {
         s_status = 1;
@@ -444,16 +418,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_topk(ScanArgs a) {
     __syncthreads();
     if (s_status) break;
     mbar_try_wait(&s_bar[s], parity);  // per-thread acquire of the completed phase
-    const uint32_t tile = blockIdx.x + j * gridDim.x;
-    const uint32_t row0 = tile * Sh::kTileRows;
-    const uint32_t rows = min((uint32_t)Sh::kTileRows, a.n_ads - row0);
     const uint8_t *st = stage0 + (size_t)s * Sh::kStageBytes;
     if (MODE == MODE_TOPK) {
       thr = s_thr;
     }
 #pragma unroll 2
     for (int it = 0; it < Sh::kRowsPerWarp / Sh::kRowsPerIter; it++) {
-      const uint32_t r = warp * Sh::kRowsPerWarp + it * Sh::kRowsPerIter + lane / Sh::kLPR;
+      const uint32_t rw = it * Sh::kRowsPerIter + lane / Sh::kLPR;  // row within the warp's rows
+      const uint32_t r = warp * Sh::kRowsPerWarp + rw;
       float dot = 0.f;
       if (r < rows) {
         const uint4 v = *reinterpret_cast<const uint4 *>(st + (size_t)r * Sh::kRowBytes +
@@ -465,19 +437,21 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_topk(ScanArgs a) {
       }
 #pragma unroll
       for (int o = Sh::kLPR / 2; o >= 1; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+      const float rw_w = __shfl_sync(0xffffffffu, pre_w, rw);
+      const float rw_s = __shfl_sync(0xffffffffu, pre_s, rw);
+      const bool rw_f = __shfl_sync(0xffffffffu, (int)pre_f, rw) != 0;
       const bool leader = (lane % Sh::kLPR) == 0 && r < rows;
       const uint32_t ad = row0 + r;
       float score = 0.f;
       if (leader) {
         score = dot;
-        if (a.scale) score *= a.scale[ad];
-        if (a.wide) score += a.wide[ad];
+        if (a.scale) score *= rw_s;
+        if (a.wide) score += rw_w;
       }
       if (MODE == MODE_ALL) {
         if (leader) a.all_out[ad] = score;
       } else {
-        bool keep = leader;
-        if (keep && a.filter) keep = (a.filter[ad >> 6] >> (ad & 63)) & 1ull;
+        bool keep = leader && rw_f;
         uint64_t key = 0;
         if (keep) {
           key = make_key(score, ad);
@@ -721,8 +695,10 @@ static int ws_prepare(ebr_index *ix, uint32_t n_q, uint32_t kcap) {
                                               (LenPair *)nullptr, LenPairSum(), LenPair{0, 0, 0},
                                               (int)entries));
   EBR_TRY(dev_reserve(w.cub_tmp, tb + 256));
-  EBR_TRY(dev_reserve(w.cand, (size_t)(ix->num_sms + 1) * kcap * 8 + 2 * (size_t)kcap * 8));
+  EBR_TRY(dev_reserve(w.cand, ((size_t)ix->num_sms * kMaxCtasPerSm + 1) * kcap * 8 +
+                                  2 * (size_t)kcap * 8));
   EBR_TRY(dev_reserve(w.ctrl, 256));
+  EBR_TRY(dev_reserve(w.hist, kHistWords * 4));
   return EBR_OK;
 }
 
@@ -822,25 +798,36 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
     n_q = ix->n_keys;
   }
   pm.mark(1, st);
-  EBR_TRY(run_wide(ix, q_key, q_w, n_q, ctrl, st));
-  if (n_q) {
-    ix->launches += 3;
-    ix->lib_launches += 2;
+  const bool fused = q_key == nullptr && !(q.flags & EBR_QF_KEY_MAJOR);
+  if (fused) {
+    // dense query: wide term decoded window by window inside the scan
+    pm.mark(2, st);
+    EBR_CUDA_TRY(cudaMemsetAsync(w.hist.p, 0, kHistWords * 4, st));
+    EBR_TRY(launch_fused(ix, q.h_u, q_w, q.filter, kscan, (uint64_t *)w.cand.p, ctrl, nullptr,
+                         quant ? (float *)w.wide.p : nullptr, (uint32_t *)w.hist.p,
+                         ix->num_sms * kMaxCtasPerSm, st));
+    ix->launches += 1;
+  } else {
+    EBR_TRY(run_wide(ix, q_key, q_w, n_q, ctrl, st));
+    if (n_q) {
+      ix->launches += 3;
+      ix->lib_launches += 2;
+    }
+    pm.mark(2, st);
+    ScanArgs a;
+    memset(&a, 0, sizeof(a));
+    a.emb = quant ? ix->emb_q.p : ix->emb_f32.p;
+    a.scale = ix->dtype == EBR_FP8E4M3 ? (const float *)ix->emb_scale.p : nullptr;
+    a.h_u = q.h_u;
+    a.wide = (const float *)w.wide.p;
+    a.filter = q.filter;
+    a.n_ads = ix->n_ads;
+    a.k = kscan;
+    a.cand_out = (uint64_t *)w.cand.p;
+    a.ctrl = ctrl;
+    EBR_TRY(launch_scan<MODE_TOPK>(ix, a, st));
+    ix->launches += 1;
   }
-  pm.mark(2, st);
-  ScanArgs a;
-  memset(&a, 0, sizeof(a));
-  a.emb = quant ? ix->emb_q.p : ix->emb_f32.p;
-  a.scale = ix->dtype == EBR_FP8E4M3 ? (const float *)ix->emb_scale.p : nullptr;
-  a.h_u = q.h_u;
-  a.wide = (const float *)w.wide.p;
-  a.filter = q.filter;
-  a.n_ads = ix->n_ads;
-  a.k = kscan;
-  a.cand_out = (uint64_t *)w.cand.p;
-  a.ctrl = ctrl;
-  EBR_TRY(launch_scan<MODE_TOPK>(ix, a, st));
-  ix->launches += 1;
   pm.mark(3, st);
   const uint32_t p2 = pow2_at_least(std::max<uint32_t>(kscan, 1));
   if (!quant) {
@@ -1179,20 +1166,26 @@ extern "C" int ebr_score_all(const ebr_index *cix, const ebr_cross *cross, const
   uint32_t n_q;
   Ctrl *ctrl;
   int rc = single_query_prep(ix, cross, q, &q_key, &q_w, &n_q, &ctrl, st);
-  if (rc == EBR_OK) rc = run_wide(ix, q_key, q_w, n_q, ctrl, st);
-  if (rc == EBR_OK) {
-    ScanArgs a;
-    memset(&a, 0, sizeof(a));
-    const bool quant = ix->dtype != EBR_F32;
-    a.emb = quant ? ix->emb_q.p : ix->emb_f32.p;
-    a.scale = ix->dtype == EBR_FP8E4M3 ? (const float *)ix->emb_scale.p : nullptr;
-    a.h_u = q->h_u;
-    a.wide = (const float *)ix->ws.wide.p;
-    a.n_ads = ix->n_ads;
-    a.k = 1;
-    a.ctrl = ctrl;
-    a.all_out = out_scores;
-    rc = launch_scan<MODE_ALL>(ix, a, st);
+  const bool fused = rc == EBR_OK && q_key == nullptr && !(q->flags & EBR_QF_KEY_MAJOR);
+  if (fused) {
+    rc = launch_fused(ix, q->h_u, q_w, nullptr, 1, nullptr, ctrl, out_scores, nullptr,
+                      (uint32_t *)ix->ws.hist.p, ix->num_sms * kMaxCtasPerSm, st);
+  } else {
+    if (rc == EBR_OK) rc = run_wide(ix, q_key, q_w, n_q, ctrl, st);
+    if (rc == EBR_OK) {
+      ScanArgs a;
+      memset(&a, 0, sizeof(a));
+      const bool quant = ix->dtype != EBR_F32;
+      a.emb = quant ? ix->emb_q.p : ix->emb_f32.p;
+      a.scale = ix->dtype == EBR_FP8E4M3 ? (const float *)ix->emb_scale.p : nullptr;
+      a.h_u = q->h_u;
+      a.wide = (const float *)ix->ws.wide.p;
+      a.n_ads = ix->n_ads;
+      a.k = 1;
+      a.ctrl = ctrl;
+      a.all_out = out_scores;
+      rc = launch_scan<MODE_ALL>(ix, a, st);
+    }
   }
   if (rc == EBR_OK) rc = finish_sync(ix, st, "ebr_score_all");
   cudaSetDevice(prev);

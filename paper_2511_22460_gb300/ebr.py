@@ -28,6 +28,7 @@ EBR_OK, EBR_EINVAL, EBR_ENOMEM, EBR_ECUDA, EBR_EAGAIN, EBR_ETIMEDOUT, EBR_EDATA 
 F32, BF16, FP8E4M3 = 0, 1, 2
 W_DENSE, W_HASHED = 0, 1
 IO_DEVICE, IO_HOST = 0, 1
+QF_KEY_MAJOR = 1
 _DTYPES = {"f32": F32, "bf16": BF16, "fp8e4m3": FP8E4M3}
 
 vp, u32, u64, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
@@ -42,7 +43,8 @@ class IndexDesc(C.Structure):
 class IndexInfo(C.Structure):
     _fields_ = [("n_ads", u32), ("n_keys", u32), ("d", u32), ("emb_dtype", i32),
                 ("rescore_mult", u32), ("nnz_unique", u64), ("n_blocks", u64 * 9),
-                ("index_bytes", u64), ("emb_bytes", u64), ("build_ms", C.c_float)]
+                ("index_bytes", u64), ("emb_bytes", u64), ("build_ms", C.c_float),
+                ("window_view_ms", C.c_float), ("window_view_bytes", u64)]
 
 
 class CrossDesc(C.Structure):
@@ -54,7 +56,7 @@ class CrossDesc(C.Structure):
 
 class QueryC(C.Structure):
     _fields_ = [("h_u", vp), ("user_vals", vp), ("n_q", u32), ("q_key", vp), ("q_w", vp),
-                ("filter", vp), ("k", u32)]
+                ("filter", vp), ("k", u32), ("flags", u32)]
 
 
 class Profile(C.Structure):
@@ -246,13 +248,14 @@ class Query:
     q_w: object = None
     n_q: int = 0
     filter: object = None
+    flags: int = 0
 
     def c(self) -> QueryC:
         n_q = self.n_q
         if self.q_key is not None and not n_q:
             n_q = int(self.q_key.numel() if hasattr(self.q_key, "numel") else self.q_key.size)
         return QueryC(ptr(self.h_u), ptr(self.user_vals), n_q, ptr(self.q_key), ptr(self.q_w),
-                      ptr(self.filter), int(self.k))
+                      ptr(self.filter), int(self.k), int(self.flags))
 
 
 def _queries(qs: Sequence[Query]):

@@ -193,26 +193,30 @@ def _setup(name, n, seed=0, dtype="f32", **kw):
 
 
 @pytest.mark.parametrize("name,n", [("single_fp32_10k", 10_000), ("single_fp32_2m", 250_013)])
-def test_score_all_matches_oracle(name, n):
+@pytest.mark.parametrize("flags", [0, ebr.QF_KEY_MAJOR], ids=["window_major", "key_major"])
+def test_score_all_matches_oracle(name, n, flags):
     w, post, ix, cross = _setup(name, n, seed=1)
     ref, tol = ref_scores(w, 0, post)
     out = torch.empty(w.n_ads, dtype=torch.float32, device=DEV)
-    ebr.score_all(ix, cross, ebr.Query(h_u=dev(w.h_u[0]), k=1, user_vals=dev(w.users[0])), out)
+    ebr.score_all(ix, cross, ebr.Query(h_u=dev(w.h_u[0]), k=1, user_vals=dev(w.users[0]),
+                                       flags=flags), out)
     check_scores(out.cpu().numpy(), ref, tol)
 
 
-@pytest.mark.parametrize("name,n,k", [("single_fp32_10k", 10_000, 100),
-                                      ("single_fp32_2m", 300_007, 500),
-                                      ("single_fp32_2m", 100_000, 2000),
-                                      ("single_fp32_2m", 5_000, 5000),
-                                      ("single_fp32_10k", 700, 1000)])
-def test_topk_matches_oracle(name, n, k):
+@pytest.mark.parametrize("name,n,k,flags", [("single_fp32_10k", 10_000, 100, 0),
+                                            ("single_fp32_2m", 300_007, 500, 0),
+                                            ("single_fp32_2m", 300_007, 500, ebr.QF_KEY_MAJOR),
+                                            ("single_fp32_2m", 100_000, 2000, 0),
+                                            ("single_fp32_2m", 5_000, 5000, 0),
+                                            ("single_fp32_2m", 5_000, 5000, ebr.QF_KEY_MAJOR),
+                                            ("single_fp32_10k", 700, 1000, 0)])
+def test_topk_matches_oracle(name, n, k, flags):
     w, post, ix, cross = _setup(name, n, seed=2)
     ref, tol = ref_scores(w, 0, post)
     ids = torch.empty(k, dtype=torch.int32, device=DEV)
     sc = torch.empty(k, dtype=torch.float32, device=DEV)
-    ebr.score_topk(ix, cross, [ebr.Query(h_u=dev(w.h_u[0]), k=k, user_vals=dev(w.users[0]))],
-                   ids, sc)
+    ebr.score_topk(ix, cross, [ebr.Query(h_u=dev(w.h_u[0]), k=k, user_vals=dev(w.users[0]),
+                                         flags=flags)], ids, sc)
     check_topk(ids.cpu().numpy().view(np.uint32), sc.cpu().numpy(), ref, tol, k)
 
 
@@ -323,14 +327,42 @@ def test_index_quantised_tables_match_oracle():
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "fp8e4m3"])
-def test_quantised_scan_with_rescoring_reaches_full_recall(dtype):
+@pytest.mark.parametrize("flags", [0, ebr.QF_KEY_MAJOR], ids=["window_major", "key_major"])
+def test_quantised_scan_with_rescoring_reaches_full_recall(dtype, flags):
     w, post, ix, cross = _setup("fp8_10m", 200_000, seed=6, dtype=dtype)
     k = 500
     ids = torch.empty(k, dtype=torch.int32, device=DEV)
     sc = torch.empty(k, dtype=torch.float32, device=DEV)
-    ebr.score_topk(ix, cross, [ebr.Query(h_u=dev(w.h_u[0]), k=k, user_vals=dev(w.users[0]))],
-                   ids, sc)
+    ebr.score_topk(ix, cross, [ebr.Query(h_u=dev(w.h_u[0]), k=k, user_vals=dev(w.users[0]),
+                                         flags=flags)], ids, sc)
     ref, tol = ref_scores(w, 0, post)
     got = ids.cpu().numpy().view(np.uint32)
     assert recall(got, ref, tol, k) == 1.0
     check_topk(got, sc.cpu().numpy(), ref, tol, k)
+
+
+def test_window_view_is_a_permutation_of_the_blocks():
+    """The window-major view holds exactly the index's blocks (checked via the
+    full-score path on a skewed index with empty and multi-valued ads)."""
+    rng = np.random.default_rng(21)
+    n_keys, n_ads, nnz = 500, 40_000, 300_000
+    pk = (rng.zipf(1.2, nnz) % n_keys).astype(np.uint32)
+    pa = rng.integers(0, n_ads, nnz).astype(np.uint32)
+    emb = rng.standard_normal((n_ads, 16)).astype(np.float32)
+    ix = ebr.build_index(n_ads, n_keys, pk, pa, emb)
+    q_w = rng.standard_normal(n_keys).astype(np.float32)
+    h = rng.standard_normal(16).astype(np.float32)
+    out_w = torch.empty(n_ads, dtype=torch.float32, device=DEV)
+    out_k = torch.empty(n_ads, dtype=torch.float32, device=DEV)
+    ebr.score_all(ix, None, ebr.Query(h_u=dev(h), k=1, q_w=dev(q_w)), out_w)
+    ebr.score_all(ix, None, ebr.Query(h_u=dev(h), k=1, q_w=dev(q_w), flags=ebr.QF_KEY_MAJOR),
+                  out_k)
+    keys = np.arange(n_keys, dtype=np.uint32)
+    ref = oracle.scores_postings(h, emb, n_keys, pk, pa, keys, q_w.astype(np.float64))
+    mag = oracle.scores_postings(np.abs(h), np.abs(emb), n_keys, pk, pa, keys,
+                                 np.abs(q_w).astype(np.float64))
+    tol = 1e-5 * np.maximum(np.abs(ref), mag) + 1e-30
+    check_scores(out_w.cpu().numpy(), ref, tol, "window-major")
+    check_scores(out_k.cpu().numpy(), ref, tol, "key-major")
+    info = ix.info()
+    assert info.window_view_bytes > 0
