@@ -28,12 +28,15 @@ int check_device_flags(uint32_t flags, const char *where) {
     set_error("%s: a bounded device wait timed out (flags 0x%x)", where, flags);
     return EBR_ETIMEDOUT;
   }
-  set_error("%s: device-side input check failed (flags 0x%x: %s%s%s%s%s)", where, flags,
+  set_error("%s: device-side input check failed (flags 0x%x: %s%s%s%s%s%s)", where, flags,
             (flags & DEVERR_BAD_KEY) ? "query key >= n_keys " : "",
             (flags & DEVERR_BAD_AD) ? "ad id >= n_ads " : "",
             (flags & DEVERR_BAD_USER) ? "user value >= vocabulary " : "",
             (flags & DEVERR_OVERFLOW) ? "capacity overflow " : "",
-            (flags & DEVERR_BAD_BUILD_KEY) ? "key >= n_keys " : "");
+            (flags & DEVERR_BAD_BUILD_KEY) ? "key >= n_keys " : "",
+            (flags & DEVERR_RANGE) ? "a query weight times the most keys of one ad is >= 8192 "
+                                     "(exact window accumulator range; use EBR_QF_KEY_MAJOR) "
+                                   : "");
   return EBR_EDATA;
 }
 

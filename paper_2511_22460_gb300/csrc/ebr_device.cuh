@@ -50,6 +50,20 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_u32(b))
       : "memory");
 }
+// Same, with an L2 cache-policy hint (e.g. evict-first for data read once).
+__device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *b, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(b)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -77,6 +91,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity,
 
 constexpr uint64_t kWaitTimeoutNs = 2000000000ull;  // 2 s
 
+// Plain arrive (release semantics) on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// Barrier over a subset of the CTA's warps (hardware named barrier `id`).
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // ------------------------------------------------------- warp-aggregated append
 // Lanes with pred reserve consecutive slots of *counter; returns the slot
 // (undefined where !pred).  One atomic per warp.
@@ -97,22 +120,38 @@ __device__ __forceinline__ uint32_t warp_append(bool pred, uint32_t *counter) {
 // unique).  8-bit digits from the top; stops as soon as the chosen digit's
 // bucket is taken whole.  Collective over the CTA; hist holds 256 words and
 // s_misc 4 words of shared memory.  Returns T to every thread.
-template <int NT>
-__device__ uint64_t cta_radix_select(const uint64_t *buf, uint32_t n, uint32_t need,
-                                     uint32_t *hist, uint32_t *s_misc) {
+struct CtaSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct GroupSync {  // named barrier over the first `n` threads of the CTA
+  int id, n;
+  __device__ __forceinline__ void operator()() const { named_sync(id, n); }
+};
+
+// Generic form: `t` is the caller's index in its group of NT threads (the
+// first warp of the group computes the digit), `sync` synchronises the group.
+template <int NT, typename Sync>
+__device__ uint64_t group_radix_select(const uint64_t *buf, uint32_t n, uint32_t need,
+                                       uint32_t *hist, uint32_t *s_misc, int t, Sync sync) {
   uint64_t prefix = 0;
   for (int shift = 56; shift >= 0; shift -= 8) {
-    for (int i = threadIdx.x; i < 256; i += NT) hist[i] = 0;
-    __syncthreads();
+    for (int i = t; i < 256; i += NT) hist[i] = 0;
+    sync();
     const uint64_t hi_mask = (shift == 56) ? 0ull : (~0ull << (shift + 8));
-    for (uint32_t i = threadIdx.x; i < n; i += NT) {
+    for (uint32_t i = t; i < n; i += NT) {
       uint64_t x = buf[i];
-      if ((x & hi_mask) == prefix) atomicAdd(&hist[(x >> shift) & 255u], 1u);
+      if ((x & hi_mask) == prefix) {
+        // aggregate equal digits within the warp: one atomic per distinct digit
+        const uint32_t dg = (uint32_t)(x >> shift) & 255u;
+        const uint32_t peers = __match_any_sync(__activemask(), dg);
+        if ((threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1))
+          atomicAdd(&hist[dg], (uint32_t)__popc(peers));
+      }
     }
-    __syncthreads();
-    if (threadIdx.x < 32) {
+    sync();
+    if (t < 32) {
       // lane l owns bins 255-8l .. 248-8l (descending)
-      const int lane = threadIdx.x;
+      const int lane = t;
       uint32_t c[8], tot = 0;
 #pragma unroll
       for (int e = 0; e < 8; e++) {
@@ -140,15 +179,21 @@ __device__ uint64_t cta_radix_select(const uint64_t *buf, uint32_t n, uint32_t n
         }
       }
     }
-    __syncthreads();
+    sync();
     const uint32_t dg = s_misc[0];
     need = s_misc[1];
     const uint32_t whole = s_misc[2];
     prefix |= (uint64_t)dg << shift;
-    __syncthreads();
+    sync();
     if (whole) break;
   }
   return prefix;
+}
+
+template <int NT>
+__device__ uint64_t cta_radix_select(const uint64_t *buf, uint32_t n, uint32_t need,
+                                     uint32_t *hist, uint32_t *s_misc) {
+  return group_radix_select<NT>(buf, n, need, hist, s_misc, threadIdx.x, CtaSync());
 }
 
 // ---------------------------------------------- histogram threshold (K-th bound)

@@ -1,18 +1,28 @@
 // Fused window-major scan for requests whose query covers the whole key space.
 //
-// One CTA handles one window of 256 consecutive ads at a time (the block
-// granularity of Algorithm 1: ads sharing ad >> 8).  For its window it
-//   1. issues the streaming loads of the 256 embedding rows (kept in registers),
-//   2. decodes every block of the window from the window-major view of the
-//      compressed list -- all nine size groups -- and scatter-adds the block's
-//      w^[key] into a 256-entry shared-memory accumulator (the wide term of
-//      the HitMatch equation, Sec. 3.3, for these ads),
-//   3. computes the inner products (Eq. 1), adds the accumulator and the FP8
-//      row scale, applies the targeting filter and appends candidates to a
-//      per-CTA buffer that a radix select trims to the K best,
-// so the wide term never leaves shared memory and the score vector is never
-// written.  Candidates surviving the running global threshold are appended to
-// a global list for the final selection.
+// The wide term of the HitMatch equation (Sec. 3.3) is accumulated per window
+// of 256 consecutive ads -- the block granularity of Algorithm 1 (ads sharing
+// ad >> 8) -- from the window-major view of the compressed inverted list, in
+// shared memory, and added to the dual-tower inner product (Eq. 1) of the same
+// ads as their embedding rows stream through; the K best survive in a per-CTA
+// buffer.  Neither the wide term nor the score vector is written to global
+// memory.
+//
+// One persistent CTA per SM, three warp roles:
+//   producer (1 warp): for every window, stages its compressed-list segments
+//       (keys and value bytes of all nine size groups) into one of two index
+//       slots, and its embedding rows into a ring of 16 KB stages, all by TMA
+//       bulk copies (cp.async.bulk + mbarrier, L2 evict-first);
+//   decoders (2 teams x 5 warps): each team takes every other window; warps
+//       walk the window's blocks in chunks of 32 work units of one size group,
+//       gather w^[key] and add it into one of four exact fixed-point
+//       accumulators of 256 ads (two 32-bit integer atomics per ad slot);
+//   scorers (8 warps): one thread per row (two for 128-element rows) forms the
+//       inner product with its rotated copy of h_u held in registers, adds the
+//       window's accumulator (and the FP8 row scale), applies the filter and
+//       appends candidates; a radix select trims the buffer to the K best.
+// All hand-offs are mbarrier phases; every wait is bounded (2 s) and a CTA
+// that times out flags the request and drains its copies.
 #include <algorithm>
 #include <cstring>
 
@@ -21,9 +31,20 @@
 
 namespace ebr {
 
-constexpr int kFusedThreads = 256;
-constexpr int kFusedWarps = kFusedThreads / 32;
 constexpr int kWin = 256;
+constexpr int kDotWarps = 8, kTeamWarps = 5, kTeams = 2;
+constexpr int kDotThreads = kDotWarps * 32;
+constexpr int kTeamThreads = kTeamWarps * 32;
+constexpr int kProducerWarp = kDotWarps + kTeams * kTeamWarps;
+constexpr int kFusedThreads = (kProducerWarp + 1) * 32;  // 608 (19 warps)
+constexpr int kAccBufs = 4;
+constexpr int kIdxSlots = 2;  // one per decoder team
+constexpr int kStageBytes = 16384;
+constexpr int kMaxStages = 12;
+constexpr int kChunksInFlight = 8;  // decoder chunks of 32 units per warp per round
+constexpr int kMaxChunkTab = 1024;  // chunk -> (group, chunk in group) table per team
+static_assert(kWin % kDotThreads == 0, "scorer threads split the window evenly");
+static_assert(kIdxSlots == kTeams, "team t owns index slot t");
 
 struct FusedArgs {
   const void *emb;
@@ -34,193 +55,417 @@ struct FusedArgs {
   const uint8_t *wvals[kGroups];
   const uint32_t *win_ptr[kGroups];
   const uint64_t *filter;
-  uint32_t n_ads, n_win, k, cap, stages;
+  uint32_t n_ads, n_win, k, cap, stages, slot_bytes;
   uint64_t *cand_out;
   Ctrl *ctrl;
-  float *all_out;  // score-all mode
-  float *wide_out; // if set: the per-ad wide term is written here (needed by FP32 rescoring)
-  uint32_t *hist;  // [256 + 65536] candidate-score histogram (zeroed per request)
+  float *all_out;   // score-all mode
+  float *wide_out;  // if set: the per-ad wide term is written here (FP32 rescoring needs it)
+  uint32_t *hist;   // [256 + 65536] candidate-score histogram (zeroed per request)
+  float w_lim;      // |w^| must stay below this (exact accumulator range)
 };
 
 template <typename Elt, int D>
 struct FusedShape {
   static constexpr int kRowBytes = D * EltTraits<Elt>::kBytes;
   static constexpr int kChunks = kRowBytes / 16;                 // 16-byte chunks per row
+  static constexpr int kRowsPerStage =                           // rows per stage
+      (kStageBytes / kRowBytes) < kWin ? (kStageBytes / kRowBytes) : kWin;
+  static constexpr int kStagesPerWin = kWin / kRowsPerStage;
+  static constexpr int kTPR = D > 64 ? D / 64 : 1;               // scorer threads per row
+  static constexpr int kCPT = kChunks / kTPR;                    // chunks per scorer thread
+  static constexpr int kRowsPerPass = kDotThreads / kTPR;
+  static constexpr int kPasses = kWin / kRowsPerPass;
   static constexpr int kRowsPer128 = kRowBytes >= 128 ? 1 : 128 / kRowBytes;
-  static constexpr int kStageBytes = kWin * kRowBytes;           // one window of rows
-  static_assert(kChunks >= 1, "row width");
+  static constexpr int kHPT = kCPT * EltTraits<Elt>::kVec;       // h_u entries per thread
+  static_assert(kRowsPerStage <= kWin && kWin % kRowsPerStage == 0, "stage split");
+  static_assert(kTPR >= 1 && kCPT >= 1 && kHPT <= 64, "row split");
 };
 
 __device__ __forceinline__ uint32_t unit_shift_f(uint32_t g) { return g >= 2 ? g - 2 : 0; }
 
-// Shared memory (dynamic): [stages x window rows][h_u, D floats][2 x cap candidates]
+struct SlotDesc {                // one window's staged segments
+  uint32_t key_off[kGroups];     // byte offset of the window's first key in the slot
+  uint32_t val_off[kGroups];     // byte offset of its first value byte
+  uint32_t nblk[kGroups];        // blocks of the window in group g
+  uint32_t window;
+};
+
+constexpr int kPrefetch = 4;  // producer reads window offsets this many windows ahead
+
+// The window accumulators hold each ad's wide term exactly, in fixed point
+// with 36 fraction bits split over two 32-bit words (shared-memory integer
+// atomics are fast where FP32 ones are not): w = round(w^ * 2^36) is added as
+// hi = w >> 18 (signed) and lo = w & (2^18 - 1); the term is
+// hi * 2^-18 + lo * 2^-36.  With |w^| * (most keys of one ad) < 2^13 neither
+// word overflows; the decoders flag weights outside that range.
+constexpr float kFixScale = 68719476736.0f;      // 2^36
+constexpr float kHiUnit = 3.814697265625e-06f;   // 2^-18
+constexpr float kLoUnit = 1.4551915228366852e-11f;  // 2^-36
+
+struct FusedSmem {
+  int acc_hi[kAccBufs][kWin];
+  uint32_t acc_lo[kAccBufs][kWin];
+  uint32_t wp[kPrefetch][kGroups];  // producer's ring of window offsets
+  uint32_t ctab[kTeams][kMaxChunkTab];  // per team: group << 16 | chunk within the group
+  SlotDesc desc[kIdxSlots];
+  uint32_t hist[256];
+  uint32_t misc[8];
+  uint32_t wtot[2][kDotWarps];
+  uint64_t full[kMaxStages], empty[kMaxStages], acc_full[kAccBufs], acc_empty[kAccBufs];
+  uint64_t idx_full[kIdxSlots], idx_empty[kIdxSlots];
+  unsigned long long thr;
+  uint32_t n, abort;
+  // group-uniform stop decisions: written by one thread before a barrier of
+  // its group, read by all after it (a named barrier must never be skipped
+  // by only part of its group)
+  uint32_t stop_acc, stop_end, team_stop[kTeams];
+};
+
 template <typename Elt, int D, bool ALL>
-__global__ void __launch_bounds__(kFusedThreads, 2) k_fused_window(FusedArgs a) {
+__global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
   using Sh = FusedShape<Elt, D>;
   using Tr = EltTraits<Elt>;
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ float s_acc[kWin];
-  __shared__ uint32_t s_lo[kGroups], s_pre[kGroups + 1];
-  __shared__ uint32_t s_hist[256];
-  __shared__ uint32_t s_misc[8];
-  __shared__ uint32_t s_n, s_n2, s_status, s_fail_j;
-  __shared__ unsigned long long s_thr;
-  __shared__ uint64_t s_bar[4];
+  __shared__ FusedSmem sm;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t S = a.stages;
   uint8_t *stage0 = smem;
-  float *s_h = reinterpret_cast<float *>(smem + (size_t)S * Sh::kStageBytes);
+  uint8_t *slot0 = smem + (size_t)S * kStageBytes;
+  float *s_h = reinterpret_cast<float *>(slot0 + (size_t)kIdxSlots * a.slot_bytes);
   uint64_t *cand = reinterpret_cast<uint64_t *>(s_h + D);
-  uint64_t *cand2 = cand + a.cap;
 
-  const uint32_t my_wins =
-      blockIdx.x < a.n_win ? (a.n_win - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-  auto issue = [&](uint32_t j) {  // window j of this CTA into stage j % S
-    const uint32_t w = blockIdx.x + j * gridDim.x;
-    const uint32_t row0 = w * kWin;
-    const uint32_t rows = min((uint32_t)kWin, a.n_ads - row0);
-    uint64_t *bar = &s_bar[j % S];
-    mbar_arrive_expect_tx(bar, rows * Sh::kRowBytes);
-    bulk_g2s(stage0 + (size_t)(j % S) * Sh::kStageBytes,
-             reinterpret_cast<const uint8_t *>(a.emb) + (uint64_t)row0 * Sh::kRowBytes,
-             rows * Sh::kRowBytes, bar);
-  };
-  s_acc[tid] = 0.f;
+  // a contiguous, balanced range of windows per CTA: one sequential stream per SM
+  const uint32_t w_begin = (uint32_t)(((uint64_t)a.n_win * blockIdx.x) / gridDim.x);
+  const uint32_t w_end = (uint32_t)(((uint64_t)a.n_win * (blockIdx.x + 1)) / gridDim.x);
+  const uint32_t my_wins = w_end - w_begin;
+
+  for (int i = tid; i < kAccBufs * kWin; i += kFusedThreads) {
+    (&sm.acc_hi[0][0])[i] = 0;
+    (&sm.acc_lo[0][0])[i] = 0u;
+  }
   for (int i = tid; i < D; i += kFusedThreads) s_h[i] = a.h_u[i];
   if (tid == 0) {
-    s_n = 0;
-    s_status = 0;
-    s_thr = 0ull;
-    for (uint32_t q = 0; q < S; q++) mbar_init(&s_bar[q], 1);
+    sm.n = 0;
+    sm.abort = 0;
+    sm.thr = 0ull;
+    for (uint32_t q = 0; q < S; q++) {
+      mbar_init(&sm.full[q], 1);
+      mbar_init(&sm.empty[q], 1);
+    }
+    for (int q = 0; q < kAccBufs; q++) {
+      mbar_init(&sm.acc_full[q], kTeamThreads);
+      mbar_init(&sm.acc_empty[q], kDotThreads);
+    }
+    for (int q = 0; q < kIdxSlots; q++) {
+      mbar_init(&sm.idx_full[q], 1);
+      mbar_init(&sm.idx_empty[q], 1);
+    }
     fence_mbar_init();
-    for (uint32_t j = 0; j < S && j < my_wins; j++) issue(j);
   }
   __syncthreads();
 
-  for (uint32_t j = 0; j < my_wins; j++) {
-    const uint32_t w = blockIdx.x + j * gridDim.x;
-    const uint32_t row0 = w * kWin;
-    const uint32_t rows = min((uint32_t)kWin, a.n_ads - row0);
-    // ---- 1. wide term of window w from its blocks in all nine groups
-    if (tid < kGroups) {
-      const uint32_t lo = a.win_ptr[tid][w], hi = a.win_ptr[tid][w + 1];
-      s_lo[tid] = lo;
-      s_pre[tid + 1] = (hi - lo) << unit_shift_f(tid);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      s_pre[0] = 0;
-#pragma unroll
-      for (int g = 0; g < kGroups; g++) s_pre[g + 1] += s_pre[g];
-    }
-    __syncthreads();
-    uint32_t pre[kGroups + 1];
-#pragma unroll
-    for (int g = 0; g <= kGroups; g++) pre[g] = s_pre[g];
-    const uint32_t total = pre[kGroups];
-    constexpr int kB = 4;  // units per thread in flight
-    for (uint32_t u0 = tid; u0 < total; u0 += kB * kFusedThreads) {
-      uint32_t key[kB], word[kB], meta[kB];  // meta: group | first-word << 4 | valid << 5
-#pragma unroll
-      for (int q = 0; q < kB; q++) {
-        const uint32_t u = u0 + q * kFusedThreads;
-        key[q] = 0;
-        word[q] = 0;
-        meta[q] = 0;
-        if (u < total) {
-          uint32_t g = 0;
-#pragma unroll
-          for (int t = 1; t < kGroups; t++) g += (u >= pre[t]) ? 1u : 0u;
-          const uint32_t us = unit_shift_f(g);
-          const uint32_t vv = u - s_pre[g];
-          const uint32_t b = s_lo[g] + (vv >> us);
-          const uint32_t wi = vv & ((1u << us) - 1u);
-          key[q] = __ldcs(a.wkey[g] + b);
-          if (g >= 2)
-            word[q] = __ldcs(reinterpret_cast<const uint32_t *>(a.wvals[g]) +
-                             (((uint64_t)b << us) + wi));
-          else if (g == 1)
-            word[q] = __ldcs(reinterpret_cast<const unsigned short *>(a.wvals[1]) + b);
-          else
-            word[q] = __ldcs(reinterpret_cast<const unsigned char *>(a.wvals[0]) + b);
-          meta[q] = g | ((wi == 0) ? 16u : 0u) | 32u;
+  if (warp == kProducerWarp) {
+    // ---------------------------------------------------------- producer
+    const uint64_t pol = l2_evict_first_policy();
+    uint32_t seq = 0;  // embedding stages issued
+    bool stop = false;
+    // window offsets win_ptr[g][w], w = w_begin .. w_end, read kPrefetch windows ahead
+    if (lane < kGroups)
+      for (uint32_t p = 0; p < (uint32_t)kPrefetch && p <= my_wins; p++)
+        sm.wp[p][lane] = a.win_ptr[lane][w_begin + p];
+    __syncwarp();
+    for (uint32_t j = 0; j < my_wins && !stop; j++) {
+      uint32_t next_ptr = 0;  // win_ptr[lane][w_begin + j + kPrefetch], in flight
+      const bool pf = lane < kGroups && j + kPrefetch <= my_wins;
+      if (pf) next_ptr = a.win_ptr[lane][w_begin + j + kPrefetch];
+      const uint32_t w = w_begin + j;
+      const uint32_t sl = j % kIdxSlots, use = j / kIdxSlots;
+      // (a) index segments of window w into slot sl
+      if (use > 0) {
+        bool ok = true;
+        if (lane == 0) ok = mbar_wait_bounded(&sm.idx_empty[sl], (use - 1) & 1u, kWaitTimeoutNs);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        const bool ab = __shfl_sync(0xffffffffu, *((volatile uint32_t *)&sm.abort) != 0, 0);
+        if (!ok || ab) {
+          if (lane == 0 && !ok) {
+            atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
+            sm.abort = 1;
+          }
+          stop = true;
+          break;
         }
       }
-      float wt[kB];
+      // lane g (< 9): the segments of group g; 16-byte aligned, in group order
+      uint32_t lo = 0, hi = 0;
+      if (lane < kGroups) {
+        lo = sm.wp[j % kPrefetch][lane];
+        hi = sm.wp[(j + 1) % kPrefetch][lane];
+      }
+      const uint32_t g = lane;
+      uint64_t k0 = 0, k1 = 0, v0 = 0, v1 = 0;
+      if (lane < kGroups && hi > lo) {
+        k0 = ((uint64_t)lo * 4) & ~15ull;
+        k1 = ((uint64_t)hi * 4 + 15) & ~15ull;
+        v0 = ((uint64_t)lo << g) & ~15ull;
+        v1 = (((uint64_t)hi << g) + 15) & ~15ull;
+      }
+      const uint32_t mine = (uint32_t)((k1 - k0) + (v1 - v0));
+      uint32_t incl = mine;
 #pragma unroll
-      for (int q = 0; q < kB; q++) wt[q] = (meta[q] & 32u) ? __ldg(a.w_hat + key[q]) : 0.f;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const uint32_t cursor = incl - mine;
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      uint8_t *slot = slot0 + (size_t)sl * a.slot_bytes;
+      if (lane < kGroups) {
+        SlotDesc &dsc = sm.desc[sl];
+        dsc.nblk[g] = hi - lo;
+        // empty groups get in-slot offsets too: the decoders' predicated
+        // reads may touch them (and discard what they read)
+        dsc.key_off[g] = hi > lo ? cursor + (uint32_t)((uint64_t)lo * 4 - k0) : 0u;
+        dsc.val_off[g] =
+            hi > lo ? cursor + (uint32_t)(k1 - k0) + (uint32_t)(((uint64_t)lo << g) - v0) : 0u;
+        if (lane == 0) dsc.window = w;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive_expect_tx(&sm.idx_full[sl], total);  // release: descriptor
+      __syncwarp();
+      if (lane < kGroups && hi > lo) {
+        bulk_g2s_hint(slot + cursor, reinterpret_cast<const uint8_t *>(a.wkey[g]) + k0,
+                      (uint32_t)(k1 - k0), &sm.idx_full[sl], pol);
+        bulk_g2s_hint(slot + cursor + (uint32_t)(k1 - k0), a.wvals[g] + v0, (uint32_t)(v1 - v0),
+                      &sm.idx_full[sl], pol);
+      }
+      // (b) the window's embedding rows into the stage ring
+      if (lane == 0) {
+        for (uint32_t q = 0; q < (uint32_t)Sh::kStagesPerWin; q++, seq++) {
+          const uint32_t s = seq % S;
+          if (seq >= S && !mbar_wait_bounded(&sm.empty[s], ((seq / S) - 1) & 1u, kWaitTimeoutNs)) {
+            atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
+            sm.abort = 1;
+            stop = true;
+            break;
+          }
+          const uint32_t row0 = w * kWin + q * Sh::kRowsPerStage;
+          const uint32_t rows =
+              row0 < a.n_ads ? min((uint32_t)Sh::kRowsPerStage, a.n_ads - row0) : 0u;
+          if (rows) {
+            mbar_arrive_expect_tx(&sm.full[s], rows * Sh::kRowBytes);
+            bulk_g2s_hint(stage0 + (size_t)s * kStageBytes,
+                          reinterpret_cast<const uint8_t *>(a.emb) +
+                              (uint64_t)row0 * Sh::kRowBytes,
+                          rows * Sh::kRowBytes, &sm.full[s], pol);
+          } else {
+            mbar_arrive(&sm.full[s]);
+          }
+        }
+      }
+      stop = __shfl_sync(0xffffffffu, stop, 0);
+      seq = __shfl_sync(0xffffffffu, seq, 0);
+      __syncwarp();
+      if (pf) sm.wp[(j + kPrefetch) % kPrefetch][lane] = next_ptr;  // slot of window j, now free
+      __syncwarp();
+    }
+    if (stop && lane == 0) {
+      // stopped early: wait (bounded) for the copies still in flight
+      for (uint32_t q = (seq > S ? seq - S : 0); q < seq; q++)
+        mbar_wait_bounded(&sm.full[q % S], (q / S) & 1u, kWaitTimeoutNs / 4);
+      for (int q = 0; q < kIdxSlots; q++) {
+        // the latest phase of each slot: wait for it, whatever its parity
+        mbar_wait_bounded(&sm.idx_full[q], 0, kWaitTimeoutNs / 8);
+        mbar_wait_bounded(&sm.idx_full[q], 1, kWaitTimeoutNs / 8);
+      }
+    }
+    return;
+  }
+
+  if (warp >= kDotWarps) {
+    // ---------------------------------------------------------- decoders
+    const int team = (warp - kDotWarps) / kTeamWarps;
+    const int tw = (warp - kDotWarps) % kTeamWarps;  // warp within the team
+    const int tt = tid - kDotThreads - team * kTeamThreads;
+    const uint8_t *slot = slot0 + (size_t)team * a.slot_bytes;
+    for (uint32_t j = team; j < my_wins; j += kTeams) {
+      const uint32_t b = j % kAccBufs, use = j / kAccBufs, iuse = j / kIdxSlots;
+      if (tt == 0) {
+        uint32_t stop = *((volatile uint32_t *)&sm.abort);
+        if (!stop && use > 0 &&
+            !mbar_wait_bounded(&sm.acc_empty[b], (use - 1) & 1u, kWaitTimeoutNs))
+          stop = 1;
+        if (!stop && !mbar_wait_bounded(&sm.idx_full[team], iuse & 1u, kWaitTimeoutNs)) stop = 1;
+        if (stop && !*((volatile uint32_t *)&sm.abort)) {
+          atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
+          sm.abort = 1;
+        }
+        sm.team_stop[team] = stop;
+      }
+      named_sync(2 + team, kTeamThreads);
+      if (sm.team_stop[team]) break;
+      if (use > 0) mbar_try_wait(&sm.acc_empty[b], (use - 1) & 1u);  // per-thread acquire
+      mbar_try_wait(&sm.idx_full[team], iuse & 1u);
+      const SlotDesc &dsc = sm.desc[team];
+      // chunk prefix over the groups (chunks of 32 units never straddle groups)
+      // and a chunk -> group table, one entry per thread, so the hot loop
+      // below needs no search
+      uint32_t cpre[kGroups + 1];
+      cpre[0] = 0;
 #pragma unroll
-      for (int q = 0; q < kB; q++) {
-        if (wt[q] == 0.f) continue;
-        const uint32_t g = meta[q] & 15u;
-        if (g >= 2) {
+      for (int g = 0; g < kGroups; g++)
+        cpre[g + 1] = cpre[g] + (((dsc.nblk[g] << unit_shift_f(g)) + 31) >> 5);
+      const uint32_t n_chunks = cpre[kGroups];
+      uint32_t *tab = sm.ctab[team];
+      for (uint32_t i = tt; i < n_chunks; i += kTeamThreads) {
+        uint32_t g = 0;
+#pragma unroll
+        for (int t = 1; t < kGroups; t++) g += (i >= cpre[t]) ? 1u : 0u;
+        uint32_t cb = 0;
+#pragma unroll
+        for (int t = 0; t < kGroups; t++) cb = (t == (int)g) ? cpre[t] : cb;
+        tab[i] = (g << 16) | (i - cb);
+      }
+      named_sync(2 + team, kTeamThreads);
+      int *acc_hi = sm.acc_hi[b];
+      uint32_t *acc_lo = sm.acc_lo[b];
+      bool range_ok = true;
+      // Branch-free rounds: every chunk's loads are independent of the
+      // others', so the shared-memory reads and w^ gathers of a round overlap.
+      for (uint32_t c0 = tw; c0 < n_chunks; c0 += kChunksInFlight * kTeamWarps) {
+        uint32_t word[kChunksInFlight], meta[kChunksInFlight], key[kChunksInFlight];
+#pragma unroll
+        for (int q = 0; q < kChunksInFlight; q++) {
+          const uint32_t c = c0 + q * kTeamWarps;  // warp-uniform
+          const bool cv = c < n_chunks;
+          const uint32_t e = tab[cv ? c : 0u];
+          const uint32_t g = e >> 16;
+          const uint32_t us = unit_shift_f(g);
+          const uint32_t u = ((e & 0xFFFFu) << 5) + lane;
+          const bool v = cv && u < (dsc.nblk[g] << us);
+          const uint32_t bk = v ? (u >> us) : 0u;
+          const uint32_t wi = v ? (u & ((1u << us) - 1u)) : 0u;
+          key[q] = *reinterpret_cast<const uint32_t *>(slot + dsc.key_off[g] + 4 * bk);
+          // the aligned 32-bit word holding this unit's 1, 2 or 4 value bytes
+          const uint32_t off = dsc.val_off[g] + (bk << g) + 4 * wi;
+          const uint32_t w32 = *reinterpret_cast<const uint32_t *>(slot + (off & ~3u));
+          const uint32_t sh = 8 * (off & 3u);
+          word[q] = g >= 2 ? w32 : ((w32 >> sh) & (g == 1 ? 0xFFFFu : 0xFFu));
+          // meta: slots in the word (1, 2 or 4) | first word of its block << 4
+          meta[q] = v ? ((g >= 2 ? 4u : (g == 1 ? 2u : 1u)) | (wi == 0 ? 16u : 0u)) : 0u;
+        }
+        float wt[kChunksInFlight];
+#pragma unroll
+        for (int q = 0; q < kChunksInFlight; q++)
+          wt[q] = meta[q] ? __ldg(a.w_hat + key[q]) : 0.f;
+#pragma unroll
+        for (int q = 0; q < kChunksInFlight; q++) {
+          range_ok = range_ok && fabsf(wt[q]) < a.w_lim;
+          const long long fx = __float2ll_rn(wt[q] * kFixScale);
+          const int hi = (int)(fx >> 18);
+          const uint32_t lo = (uint32_t)(fx & 0x3FFFFll);
+          const uint32_t ns = meta[q] & 7u;
 #pragma unroll
           for (int s2 = 0; s2 < 4; s2++) {
             const uint32_t l = (word[q] >> (8 * s2)) & 255u;
-            if ((s2 == 0 && (meta[q] & 16u)) || l != 0) atomicAdd(&s_acc[l], wt[q]);
+            const bool real = (uint32_t)s2 < ns && ((s2 == 0 && (meta[q] & 16u)) || l != 0);
+            if (real && hi != 0) atomicAdd(&acc_hi[l], hi);
+            if (real && lo != 0) atomicAdd(&acc_lo[l], lo);
           }
-        } else if (g == 1) {
-          atomicAdd(&s_acc[word[q] & 255u], wt[q]);
-          if (word[q] >> 8) atomicAdd(&s_acc[word[q] >> 8], wt[q]);
-        } else {
-          atomicAdd(&s_acc[word[q]], wt[q]);
         }
       }
+      if (!range_ok) atomicOr(&a.ctrl->flags, DEVERR_RANGE);
+      named_sync(2 + team, kTeamThreads);  // every read of the slot is done
+      if (tt == 0) mbar_arrive(&sm.idx_empty[team]);
+      mbar_arrive(&sm.acc_full[b]);  // release: this thread's additions into acc[b]
     }
-    // ---- 2. this window's rows (TMA) must have landed
-    const uint32_t st = j % S, parity = (j / S) & 1u;
-    if (tid == 0 && !mbar_wait_bounded(&s_bar[st], parity, kWaitTimeoutNs)) {
-      s_status = 1;
-      s_fail_j = j;
-    }
-    __syncthreads();  // also: accumulator complete
-    if (s_status) break;
-    mbar_try_wait(&s_bar[st], parity);  // per-thread acquire of the completed phase
-    // ---- 3. one row per thread: inner product, wide add, filter, candidate
-    {
-      const uint32_t r = tid;
-      const uint8_t *row = stage0 + (size_t)st * Sh::kStageBytes + (size_t)r * Sh::kRowBytes;
-      const uint32_t rot = r / Sh::kRowsPer128;  // chunk rotation: conflict-free 16-byte reads
-      float dot = 0.f;
-      if (r < rows) {
+    return;
+  }
+
+  // ------------------------------------------------------------ scorers
+  const GroupSync gsync{1, kDotThreads};
+  // this thread's row part and its rotated copy of h_u (constant for the kernel)
+  const int qd = tid % Sh::kTPR;
+  const int prow = tid / Sh::kTPR;              // row within a pass
+  const uint32_t rot = tid / Sh::kRowsPer128;   // 16-byte reads of neighbours hit other banks
+  float hreg[Sh::kHPT];
 #pragma unroll
-        for (int c = 0; c < Sh::kChunks; c++) {
-          const uint32_t cc = (c + rot) % Sh::kChunks;
-          const uint4 v = *reinterpret_cast<const uint4 *>(row + cc * 16);
+  for (int i = 0; i < Sh::kCPT; i++) {
+    const uint32_t c = qd * Sh::kCPT + (i + rot) % Sh::kCPT;
+#pragma unroll
+    for (int e = 0; e < Tr::kVec; e++) hreg[i * Tr::kVec + e] = s_h[c * Tr::kVec + e];
+  }
+  for (uint32_t j = 0; j < my_wins; j++) {
+    const uint32_t b = j % kAccBufs, apar = (j / kAccBufs) & 1u;
+    if (tid == 0) {
+      uint32_t stop = *((volatile uint32_t *)&sm.abort);
+      if (!stop && !mbar_wait_bounded(&sm.acc_full[b], apar, kWaitTimeoutNs)) stop = 1;
+      for (uint32_t q = 0; !stop && q < (uint32_t)Sh::kStagesPerWin; q++) {
+        const uint32_t seq = j * Sh::kStagesPerWin + q;
+        if (!mbar_wait_bounded(&sm.full[seq % S], (seq / S) & 1u, kWaitTimeoutNs)) stop = 1;
+      }
+      if (stop && !*((volatile uint32_t *)&sm.abort)) {
+        atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
+        sm.abort = 1;
+      }
+      sm.stop_acc = stop;
+    }
+    gsync();
+    if (sm.stop_acc) break;
+    mbar_try_wait(&sm.acc_full[b], apar);  // per-thread acquire
+#pragma unroll
+    for (uint32_t q = 0; q < (uint32_t)Sh::kStagesPerWin; q++) {
+      const uint32_t seq = j * Sh::kStagesPerWin + q;
+      mbar_try_wait(&sm.full[seq % S], (seq / S) & 1u);
+    }
+    const uint32_t w = w_begin + j;
+    const int *acc_hi = sm.acc_hi[b];
+    const uint32_t *acc_lo = sm.acc_lo[b];
+#pragma unroll
+    for (int ps = 0; ps < Sh::kPasses; ps++) {
+      const uint32_t rw = ps * Sh::kRowsPerPass + prow;  // row within the window
+      const uint32_t ad = w * kWin + rw;
+      const bool valid = ad < a.n_ads;
+      const uint32_t seq = j * Sh::kStagesPerWin + rw / Sh::kRowsPerStage;
+      const uint8_t *row = stage0 + (size_t)(seq % S) * kStageBytes +
+                           (size_t)(rw % Sh::kRowsPerStage) * Sh::kRowBytes;
+      float2 dot2 = make_float2(0.f, 0.f);
+      if (valid) {
+#pragma unroll
+        for (int i = 0; i < Sh::kCPT; i++) {
+          const uint32_t c = qd * Sh::kCPT + (i + rot) % Sh::kCPT;
+          const uint4 v = *reinterpret_cast<const uint4 *>(row + c * 16);
           float f[Tr::kVec];
           Tr::load(v, f);
-          const float4 *hp = reinterpret_cast<const float4 *>(s_h + cc * Tr::kVec);
 #pragma unroll
-          for (int e4 = 0; e4 < Tr::kVec / 4; e4++) {
-            const float4 hv = hp[e4];
-            dot = fmaf(hv.x, f[4 * e4 + 0], dot);
-            dot = fmaf(hv.y, f[4 * e4 + 1], dot);
-            dot = fmaf(hv.z, f[4 * e4 + 2], dot);
-            dot = fmaf(hv.w, f[4 * e4 + 3], dot);
-          }
+          for (int e = 0; e < Tr::kVec; e += 2)  // packed FP32 FMA: two lanes of the sum
+            dot2 = __ffma2_rn(make_float2(hreg[i * Tr::kVec + e], hreg[i * Tr::kVec + e + 1]),
+                              make_float2(f[e], f[e + 1]), dot2);
         }
       }
-      const bool valid = r < rows;
-      const uint32_t ad = row0 + r;
+      float dot = dot2.x + dot2.y;
+#pragma unroll
+      for (int o = Sh::kTPR / 2; o >= 1; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+      const bool leader = valid && qd == 0;
       float score = 0.f;
-      if (valid) {
+      if (leader) {
+        const float wide = fmaf((float)acc_lo[rw], kLoUnit, (float)acc_hi[rw] * kHiUnit);
         score = dot;
         if (a.scale) score *= a.scale[ad];
-        score += s_acc[r];
-        if (a.wide_out) a.wide_out[ad] = s_acc[r];
+        score += wide;
+        if (a.wide_out) a.wide_out[ad] = wide;
       }
       if (ALL) {
-        if (valid) a.all_out[ad] = score;
+        if (leader) a.all_out[ad] = score;
       } else {
-        bool keep = valid;
+        bool keep = leader;
         if (keep && a.filter) keep = (a.filter[ad >> 6] >> (ad & 63)) & 1ull;
         uint64_t kk = 0;
         if (keep) {
           kk = make_key(score, ad);
-          keep = kk >= s_thr;
+          keep = kk >= sm.thr;
         }
-        const uint32_t pos = warp_append(keep, &s_n);
+        const uint32_t pos = warp_append(keep, &sm.n);
         if (keep) {
           cand[pos] = kk;
           const uint32_t o = (uint32_t)(kk >> 32);
@@ -229,65 +474,72 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_fused_window(FusedArgs a) 
         }
       }
     }
-    __syncthreads();  // stage and accumulator consumed
-    if (tid == 0 && j + S < my_wins) issue(j + S);
-    s_acc[tid] = 0.f;
-    if (!ALL) {
-      if (s_n + kWin > a.cap) {
-        const uint32_t n = s_n;
-        const uint64_t T = cta_radix_select<kFusedThreads>(cand, n, a.k, s_hist, s_misc);
-        if (tid == 0) s_n2 = 0;
-        __syncthreads();
-        for (uint32_t b0 = 0; b0 < n; b0 += kFusedThreads) {
-          const uint32_t i = b0 + tid;
-          const uint64_t x = i < n ? cand[i] : 0ull;
-          const bool kp = i < n && x >= T;
-          const uint32_t pos = warp_append(kp, &s_n2);
-          if (kp) cand2[pos] = x;
+    gsync();  // the window's stages and accumulator are fully read; appends visible
+    if (tid == 0)
+      for (uint32_t q = 0; q < (uint32_t)Sh::kStagesPerWin; q++)
+        mbar_arrive(&sm.empty[(j * Sh::kStagesPerWin + q) % S]);
+    for (int i = tid; i < kWin; i += kDotThreads) {  // hand the accumulator back, zeroed
+      sm.acc_hi[b][i] = 0;
+      sm.acc_lo[b][i] = 0u;
+    }
+    mbar_arrive(&sm.acc_empty[b]);
+    if (!ALL && sm.n + kWin > a.cap) {
+      // trim the candidates to the K best: radix select, then a stable
+      // in-place compaction in rounds of one entry per scorer thread
+      const uint32_t n = sm.n;
+      const uint64_t T =
+          group_radix_select<kDotThreads>(cand, n, a.k, sm.hist, sm.misc, tid, gsync);
+      uint32_t kept = 0;
+      for (uint32_t b0 = 0, rnd = 0; b0 < n; b0 += kDotThreads, rnd++) {
+        const uint32_t i = b0 + tid;
+        const uint64_t x = i < n ? cand[i] : 0ull;
+        const bool kp = i < n && x >= T;
+        const uint32_t bal = __ballot_sync(0xffffffffu, kp);
+        if (lane == 0) sm.wtot[rnd & 1][warp] = __popc(bal);
+        gsync();
+        uint32_t before = kept, round_total = 0;
+#pragma unroll
+        for (int q2 = 0; q2 < kDotWarps; q2++) {
+          const uint32_t t2 = sm.wtot[rnd & 1][q2];
+          before += (q2 < warp) ? t2 : 0u;
+          round_total += t2;
         }
-        __syncthreads();
-        uint64_t *t = cand;
-        cand = cand2;
-        cand2 = t;
-        if (tid == 0) {
-          s_n = s_n2;
-          const unsigned long long g = atomicMax(&a.ctrl->thr, (unsigned long long)T);
-          s_thr = max((unsigned long long)T, max(g, (unsigned long long)s_thr));
-        }
-      } else if (warp == 0 && (j & 3) == 3) {
-        const unsigned long long h = hist_threshold(a.hist, a.hist + 256, a.k);
-        if (lane == 0) {
-          const unsigned long long g = *((volatile unsigned long long *)&a.ctrl->thr);
-          s_thr = max(s_thr, max(g, h));
-        }
+        if (kp) cand[before + __popc(bal & ((1u << lane) - 1u))] = x;
+        kept += round_total;
+      }
+      gsync();
+      if (tid == 0) {
+        sm.n = kept;
+        const unsigned long long g = atomicMax(&a.ctrl->thr, (unsigned long long)T);
+        sm.thr = max((unsigned long long)T, max(g, (unsigned long long)sm.thr));
+      }
+      gsync();
+    } else if (!ALL && warp == 0 && (j & 7) == 7) {
+      const unsigned long long h = hist_threshold(a.hist, a.hist + 256, a.k);
+      if (lane == 0) {
+        const unsigned long long g = *((volatile unsigned long long *)&a.ctrl->thr);
+        sm.thr = max(sm.thr, max(g, h));
       }
     }
-    __syncthreads();
-  }
-  if (s_status) {
-    // A window's rows never arrived: record it, drain the copies in flight, leave.
-    if (tid == 0) {
-      atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
-      for (uint32_t q = s_fail_j; q < s_fail_j + S && q < my_wins; q++)
-        mbar_wait_bounded(&s_bar[q % S], (q / S) & 1u, kWaitTimeoutNs / 4);
-    }
-    return;
   }
   if (ALL) return;
-  uint32_t n = s_n;
+  if (tid == 0) sm.stop_end = *((volatile uint32_t *)&sm.abort);
+  gsync();
+  if (sm.stop_end) return;
+  const uint32_t n = sm.n;
   uint64_t T = 0;
-  if (n > a.k) T = cta_radix_select<kFusedThreads>(cand, n, a.k, s_hist, s_misc);
+  if (n > a.k) T = group_radix_select<kDotThreads>(cand, n, a.k, sm.hist, sm.misc, tid, gsync);
   if (warp == 0) {
     const unsigned long long h = hist_threshold(a.hist, a.hist + 256, a.k);
     if (lane == 0) {
       const unsigned long long g = *((volatile unsigned long long *)&a.ctrl->thr);
-      s_thr = max(max((unsigned long long)T, (unsigned long long)s_thr), max(g, h));
+      sm.thr = max(max((unsigned long long)T, (unsigned long long)sm.thr), max(g, h));
       if (n > a.k) atomicMax(&a.ctrl->thr, (unsigned long long)T);
     }
   }
-  __syncthreads();
-  const uint64_t fin = s_thr;
-  for (uint32_t b0 = 0; b0 < n; b0 += kFusedThreads) {
+  gsync();
+  const uint64_t fin = sm.thr;
+  for (uint32_t b0 = 0; b0 < n; b0 += kDotThreads) {
     const uint32_t i = b0 + tid;
     const uint64_t x = i < n ? cand[i] : 0ull;
     const bool kp = i < n && x >= fin;
@@ -296,23 +548,47 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_fused_window(FusedArgs a) 
   }
 }
 
+// Shared memory the fused scan needs besides its stage ring.
+static size_t fused_fixed_bytes(const ebr_index *ix, uint32_t d, uint32_t cap,
+                                uint32_t *slot_bytes) {
+  *slot_bytes = (ix->max_win_bytes + 127) / 128 * 128;
+  if (*slot_bytes == 0) *slot_bytes = 128;
+  return (size_t)kIdxSlots * *slot_bytes + (size_t)d * 4 + (size_t)cap * 8;
+}
+
+constexpr size_t kFusedSmemBudget = 206 * 1024;  // dynamic part; the static part is ~18 KB
+
+static uint32_t fused_cap(uint32_t k) {
+  return (std::max<uint32_t>(k, 1) + std::max<uint32_t>(k / 2, 1024) + 255) / 256 * 256;
+}
+
 template <typename Elt, int D, bool ALL>
 static int launch_fused_t(const ebr_index *ix, FusedArgs a, int max_grid, cudaStream_t st) {
-  using Sh = FusedShape<Elt, D>;
-  a.cap = ALL ? 0 : (a.k + std::max<uint32_t>(a.k, 2 * kWin) + 255) / 256 * 256;
-  const size_t fixed = (size_t)D * 4 + (size_t)2 * a.cap * 8;
-  // as many window stages as leave room for two CTAs per SM (at least one)
-  const size_t budget = 110 * 1024;
-  uint32_t stages = 1;
-  while (stages < 4 && fixed + (size_t)(stages + 1) * Sh::kStageBytes <= budget) stages++;
+  a.cap = ALL ? 0 : fused_cap(a.k);
+  uint32_t slot_bytes = 0;
+  const size_t fixed = fused_fixed_bytes(ix, D, a.cap, &slot_bytes);
+  if (fixed + 4 * (size_t)kStageBytes > kFusedSmemBudget) {
+    set_error("fused scan: k = %u with %u-byte window segments needs too much shared memory",
+              a.k, ix->max_win_bytes);
+    return EBR_EINVAL;
+  }
+  uint32_t stages = 4;
+  while (stages < (uint32_t)kMaxStages &&
+         fixed + (size_t)(stages + 1) * kStageBytes <= kFusedSmemBudget)
+    stages++;
   a.stages = stages;
-  const size_t smem = fixed + (size_t)stages * Sh::kStageBytes;
+  a.slot_bytes = slot_bytes;
+  const size_t smem = fixed + (size_t)stages * kStageBytes;
   auto kern = k_fused_window<Elt, D, ALL>;
   EBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   EBR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kFusedThreads, smem));
-  if (occ < 1) occ = 1;
-  int grid = ix->num_sms * occ;
+  if (occ < 1) {
+    set_error("fused scan: one CTA of %d threads with %zu bytes of shared memory does not fit an SM",
+              kFusedThreads, smem);
+    return EBR_ECUDA;
+  }
+  int grid = ix->num_sms;
   if (max_grid > 0) grid = std::min(grid, max_grid);
   grid = std::min<int>(grid, (int)a.n_win);
   if (grid < 1) grid = 1;
@@ -334,6 +610,15 @@ static int launch_fused_d(const ebr_index *ix, const FusedArgs &a, int max_grid,
   }
   set_error("embedding dimension %u unsupported for this dtype", ix->d);
   return EBR_EINVAL;
+}
+
+// Whether the fused scan fits shared memory for top-k on this index; if not,
+// dense queries take the key-major path (Algorithm 2) instead.
+bool fused_fits(const ebr_index *ix, uint32_t k) {
+  uint32_t slot_bytes = 0;
+  return ix->max_win_chunks <= (uint32_t)kMaxChunkTab && ix->max_keys_per_ad < 8192u &&
+         fused_fixed_bytes(ix, ix->d, fused_cap(k), &slot_bytes) + 4 * (size_t)kStageBytes <=
+             kFusedSmemBudget;
 }
 
 // Launches the fused scan over all windows.  all_out != nullptr: write every
@@ -363,6 +648,7 @@ int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
   a.all_out = all_out;
   a.wide_out = wide_out;
   a.hist = hist;
+  a.w_lim = 8192.0f / (float)std::max<uint32_t>(ix->max_keys_per_ad, 1);
   if (all_out) {
     if (ix->dtype == EBR_F32) return launch_fused_d<float, true>(ix, a, max_grid, st);
     if (ix->dtype == EBR_BF16) return launch_fused_d<Bf16Tag, true>(ix, a, max_grid, st);

@@ -41,6 +41,18 @@ __global__ void k_pack(const uint32_t *__restrict__ key, const uint32_t *__restr
   if (bad) atomicOr(flags, bad);
 }
 
+// keys per ad over the distinct (key, ad) pairs, and their maximum
+__global__ void k_keys_per_ad(const uint64_t *__restrict__ x, uint32_t m, uint32_t *__restrict__ cnt) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    atomicAdd(&cnt[(uint32_t)x[i]], 1u);
+}
+__global__ void k_max_u32(const uint32_t *__restrict__ v, uint32_t n, unsigned int *__restrict__ out) {
+  uint32_t mx = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    mx = max(mx, v[i]);
+  atomicMax(out, mx);
+}
+
 // bs[i] = 1 where a new (k, h) run starts in the sorted, duplicate-free words.
 __global__ void k_block_flags(const uint64_t *__restrict__ x, uint32_t m,
                               uint32_t *__restrict__ bs) {
@@ -122,6 +134,10 @@ __global__ void k_wm_keys(const uint64_t *__restrict__ x, const uint32_t *__rest
   }
 }
 
+struct WinPtrs {
+  const uint32_t *p[kGroups];
+};
+
 struct WmArgs {
   const uint8_t *values[kGroups];
   uint32_t *wkey[kGroups];
@@ -149,6 +165,29 @@ __global__ void k_wm_emit(const uint64_t *__restrict__ skey, const uint32_t *__r
     }
     atomicAdd(&a.wcnt[(uint64_t)g * (a.n_win + 1) + h], 1u);
   }
+}
+
+// Bytes a window's segments of the window-major view occupy once each segment
+// is widened to 16-byte boundaries (the staging size of the fused scan).
+// Also: the most 32-unit work chunks any window has (a unit is one 4-slot
+// word in groups >= 2, one block in groups 0 and 1).
+__global__ void k_win_bytes(WinPtrs wp, uint32_t n_win, unsigned int *out_max) {
+  uint32_t mx = 0, mc = 0;
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < n_win; w += gridDim.x * blockDim.x) {
+    uint64_t total = 0, chunks = 0;
+    for (int g = 0; g < kGroups; g++) {
+      const uint64_t lo = wp.p[g][w], hi = wp.p[g][w + 1];
+      if (hi == lo) continue;
+      const uint64_t k0 = (lo * 4) & ~15ull, k1 = (hi * 4 + 15) & ~15ull;
+      const uint64_t v0 = (lo << g) & ~15ull, v1 = ((hi << g) + 15) & ~15ull;
+      total += (k1 - k0) + (v1 - v0);
+      chunks += (((hi - lo) << (g >= 2 ? g - 2 : 0)) + 31) >> 5;
+    }
+    mx = max(mx, (uint32_t)min(total, (uint64_t)0xFFFFFFFFu));
+    mc = max(mc, (uint32_t)min(chunks, (uint64_t)0xFFFFFFFFu));
+  }
+  atomicMax(out_max, mx);
+  atomicMax(out_max + 1, mc);
 }
 
 inline int grid_for(uint64_t n, int threads = 256, int cap = 1 << 16) {
@@ -272,6 +311,16 @@ static int build_impl(const ebr_index_desc *desc, ebr_index *ix, cudaStream_t st
     const uint32_t m = (uint32_t)m_host;
     ix->nnz_unique = m_host;
     if (m > 0) {
+      // most keys any ad has (bounds the fused scan's exact accumulators)
+      BTRY(dev_alloc(bs, (size_t)std::max<uint64_t>(m, n_ads) * 4));
+      BCUDA(cudaMemsetAsync(bs.p, 0, (size_t)n_ads * 4, st));
+      BCUDA(cudaMemsetAsync(flags.p, 0, 4, st));
+      k_keys_per_ad<<<grid_for(m), 256, 0, st>>>(x, m, (uint32_t *)bs.p);
+      k_max_u32<<<grid_for(n_ads), 256, 0, st>>>((const uint32_t *)bs.p, n_ads,
+                                                (unsigned int *)flags.p);
+      BCUDA(cudaMemcpyAsync(&ix->max_keys_per_ad, flags.p, 4, cudaMemcpyDeviceToHost, st));
+      BCUDA(cudaStreamSynchronize(st));
+      dev_free(bs);
       BTRY(dev_alloc(bs, (size_t)m * 4));
       BTRY(dev_alloc(bid, (size_t)m * 4));
       k_block_flags<<<grid_for(m), 256, 0, st>>>(x, m, (uint32_t *)bs.p);
@@ -394,6 +443,18 @@ static int build_impl(const ebr_index_desc *desc, ebr_index *ix, cudaStream_t st
         size_t t5 = t4;
         BCUDA(cub::DeviceScan::ExclusiveSum(tmp.p, t5, (uint32_t *)wcnt.p + (size_t)g * (n_win + 1),
                                             ix->win_ptr[g], (int)(n_win + 1), st));
+      }
+      {
+        WinPtrs wp;
+        for (int g = 0; g < kGroups; g++) wp.p[g] = ix->win_ptr[g];
+        BCUDA(cudaMemsetAsync(flags.p, 0, 8, st));
+        k_win_bytes<<<grid_for(n_win), 256, 0, st>>>(wp, n_win, (unsigned int *)flags.p);
+        BCUDA(cudaGetLastError());
+        uint32_t mm[2] = {0, 0};
+        BCUDA(cudaMemcpyAsync(mm, flags.p, 8, cudaMemcpyDeviceToHost, st));
+        BCUDA(cudaStreamSynchronize(st));
+        ix->max_win_bytes = mm[0];
+        ix->max_win_chunks = mm[1];
       }
       BCUDA(cudaEventRecord(e1, st));
       BCUDA(cudaEventSynchronize(e1));

@@ -42,6 +42,7 @@ enum : uint32_t {
   DEVERR_TIMEOUT = 8u,        // a bounded wait ran out
   DEVERR_OVERFLOW = 16u,      // a capacity check failed
   DEVERR_BAD_BUILD_KEY = 32u, // key >= n_keys in build input
+  DEVERR_RANGE = 64u,         // a weight beyond the fused scan's exact accumulator range
 };
 
 int check_device_flags(uint32_t flags, const char *where);
@@ -105,6 +106,9 @@ struct ebr_index {
   uint32_t *win_ptr[ebr::kGroups] = {nullptr};
   ebr::DevBuf mem_wkey, mem_wvals, mem_winptr;
   float wm_build_ms = 0.f;
+  uint32_t max_win_bytes = 0;   // largest 16-byte-widened window segment total
+  uint32_t max_win_chunks = 0;  // most 32-unit work chunks in one window
+  uint32_t max_keys_per_ad = 0; // most distinct keys any ad belongs to
   ebr::DevBuf emb_f32;    // float [N][d]
   ebr::DevBuf emb_q;      // bf16 / e4m3 [N][d]
   ebr::DevBuf emb_scale;  // float [N] (FP8)
@@ -136,6 +140,7 @@ int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
                  const uint64_t *filter, uint32_t k, uint64_t *cand_out, Ctrl *ctrl,
                  float *all_out, float *wide_out, uint32_t *hist, int max_grid,
                  cudaStream_t st);
+bool fused_fits(const ebr_index *ix, uint32_t k);
 constexpr size_t kHistWords = 256 + 65536;  // candidate-score histogram (coarse + fine)
 // Launchers implemented in ebr_query.cu, used by the serving loop.
 int query_one(const ebr_index *ix, const ebr_cross *cross, const ebr_query &q, uint32_t *ids,

@@ -798,7 +798,8 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
     n_q = ix->n_keys;
   }
   pm.mark(1, st);
-  const bool fused = q_key == nullptr && !(q.flags & EBR_QF_KEY_MAJOR);
+  const bool fused =
+      q_key == nullptr && !(q.flags & EBR_QF_KEY_MAJOR) && fused_fits(ix, kscan);
   if (fused) {
     // dense query: wide term decoded window by window inside the scan
     pm.mark(2, st);
@@ -1166,7 +1167,8 @@ extern "C" int ebr_score_all(const ebr_index *cix, const ebr_cross *cross, const
   uint32_t n_q;
   Ctrl *ctrl;
   int rc = single_query_prep(ix, cross, q, &q_key, &q_w, &n_q, &ctrl, st);
-  const bool fused = rc == EBR_OK && q_key == nullptr && !(q->flags & EBR_QF_KEY_MAJOR);
+  const bool fused = rc == EBR_OK && q_key == nullptr && !(q->flags & EBR_QF_KEY_MAJOR) &&
+                     fused_fits(ix, 1);
   if (fused) {
     rc = launch_fused(ix, q->h_u, q_w, nullptr, 1, nullptr, ctrl, out_scores, nullptr,
                       (uint32_t *)ix->ws.hist.p, ix->num_sms * kMaxCtasPerSm, st);
