@@ -237,6 +237,17 @@ int ebr_wide_scores(const ebr_index *ix, const ebr_cross *cross, const ebr_query
  */
 int ebr_quantize(const float *x, uint64_t n, ebr_dtype dtype, void *out, void *stream);
 
+/*
+ * Diagnostic: out[i][b] = sum_t A[i][t] * U[b][t] on the tensor cores
+ * (tcgen05.mma, BF16 inputs, FP32 accumulation in TMEM, operands loaded by
+ * tensor TMA) -- the deep term (Eq. 1) of a batch of users against ads, as the
+ * batched scan computes it.  A: device [n][d] BF16 bits, U: device [B][d],
+ * out: device [n][B] FP32.  d in {64, 128}; B a multiple of 32 in 32..256.
+ * Synchronous.
+ */
+int ebr_debug_gemm_bf16(const uint16_t *A, uint32_t n, const uint16_t *U, uint32_t B, uint32_t d,
+                        float *out, void *stream);
+
 /* ------------------------------------------------------- no-allocation form */
 /*
  * Allocation-free scan + top-K.  The paper has no counterpart: this entry

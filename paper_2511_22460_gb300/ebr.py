@@ -89,6 +89,7 @@ ebr_wide_scores = _sig("ebr_wide_scores", i32, [vp, vp, C.POINTER(QueryC), vp, v
 ebr_quantize = _sig("ebr_quantize", i32, [vp, u64, i32, vp, vp])
 ebr_scan_topk_noalloc = _sig("ebr_scan_topk_noalloc", i32,
                              [vp, u32, u32, vp, vp, vp, u32, vp, vp, i32, vp])
+ebr_debug_gemm_bf16 = _sig("ebr_debug_gemm_bf16", i32, [vp, u32, vp, u32, u32, vp, vp])
 ebr_profile_enable = _sig("ebr_profile_enable", i32, [vp, i32])
 ebr_profile_read = _sig("ebr_profile_read", i32, [vp, C.POINTER(Profile)])
 
@@ -294,3 +295,9 @@ def scan_topk_noalloc(emb, h_u, wide, filt, k, out_ids, out_scores, device=0, st
     _check(ebr_scan_topk_noalloc(ptr(emb), int(emb.shape[0]), int(emb.shape[1]), ptr(h_u),
                                  ptr(wide), ptr(filt), int(k), ptr(out_ids), ptr(out_scores),
                                  device, stream_ptr(stream)), "ebr_scan_topk_noalloc")
+
+
+def debug_gemm_bf16(A, U, out, stream=None):
+    """out[n][B] = A[n][d] @ U[B][d]^T on the tensor cores (BF16 in, FP32 out)."""
+    _check(ebr_debug_gemm_bf16(ptr(A), int(A.shape[0]), ptr(U), int(U.shape[0]), int(A.shape[1]),
+                               ptr(out), stream_ptr(stream)), "ebr_debug_gemm_bf16")

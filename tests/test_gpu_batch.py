@@ -1,0 +1,26 @@
+"""GPU checks of the batched (tensor-core) path against plain references."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from paper_2511_22460_gb300 import ebr  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+@pytest.mark.parametrize("n,B,d", [(1000, 64, 64), (333, 256, 128), (4096, 32, 64),
+                                   (129, 96, 128)])
+def test_tcgen05_gemm_matches_fp64(n, B, d):
+    g = torch.Generator().manual_seed(n + B + d)
+    A = (torch.randn(n, d, generator=g) / d ** 0.5).to(torch.bfloat16)
+    U = (torch.randn(B, d, generator=g) / d ** 0.5).to(torch.bfloat16)
+    out = torch.full((n, B), float("nan"), dtype=torch.float32, device=DEV)
+    ebr.debug_gemm_bf16(A.to(DEV).view(torch.int16), U.to(DEV).view(torch.int16), out)
+    ref = A.double() @ U.double().T  # products of BF16 values are exact in FP64
+    mag = A.double().abs() @ U.double().abs().T
+    err = (out.cpu().double() - ref).abs()
+    assert torch.all(err <= 1e-6 * mag + 1e-30), float((err / (mag + 1e-30)).max())
