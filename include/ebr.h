@@ -293,6 +293,9 @@ typedef struct {
   uint64_t launches;       /* kernels of this library launched by those requests */
   uint64_t lib_launches;   /* device-library (CUB scan) kernels launched */
   double ms_expand, ms_wide, ms_scan, ms_final;
+  uint64_t batched;        /* requests served by the batched tensor-core scan */
+  uint64_t recomputed;     /* of those, recomputed by the single-request scan because the
+                              batched candidate buffers could not prove exactness */
 } ebr_profile;
 int ebr_profile_enable(ebr_index *ix, int on);
 int ebr_profile_read(ebr_index *ix, ebr_profile *out);

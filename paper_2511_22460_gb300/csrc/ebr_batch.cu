@@ -157,3 +157,808 @@ extern "C" int ebr_debug_gemm_bf16(const uint16_t *A, uint32_t n, const uint16_t
   cudaFreeAsync(flags, st);
   return check_device_flags(hf, "ebr_debug_gemm_bf16");
 }
+
+// =====================================================================
+// Batched scan: B users against every ad, one pass over the inventory
+// =====================================================================
+// Per window of 256 ads (one persistent CTA per SM, contiguous windows):
+//   producer warp   -- tensor TMA of the window's BF16 rows (two 128-row
+//                      M-tiles) into a stage ring; the users' BF16 vectors
+//                      are loaded once;
+//   MMA warp        -- tcgen05.mma: deep[256 ads x Bp users] in TMEM (Eq. 1);
+//   list warps (4)  -- walk the window's blocks in the window-major view of
+//                      the compressed list and build, per ad, the list of its
+//                      keys (the window's slice of L, transposed);
+//   epilogue (8)    -- warp w owns ads 32w .. 32w+31; for each group of 32
+//                      users: lanes = users sum w^T[key][user] over each ad's
+//                      keys (coalesced rows of the expanded weights), the
+//                      32x32 tile is transposed through shared memory, added
+//                      to the TMEM deep scores of the warp's rows, filtered,
+//                      and each user's candidates above its running threshold
+//                      go to this CTA's per-user buffer (top-m kept exactly).
+namespace ebr {
+
+constexpr int kBWin = 256;
+constexpr int kEpiWarps = 8, kListWarps = 4;
+constexpr int kEpiThreads = kEpiWarps * 32, kListThreads = kListWarps * 32;
+constexpr int kMmaWarp = kEpiWarps + kListWarps, kProdWarpB = kMmaWarp + 1;
+constexpr int kBatchThreads = (kProdWarpB + 1) * 32;  // 448
+constexpr int kMaxUsers = 256;
+
+struct CandEntry {
+  unsigned long long key;  // approximate score | id
+  float wide;              // the ad's wide term for this user (FP32 sum)
+  uint32_t pad;
+};
+
+struct BatchArgs {
+  CUtensorMap ta;  // ad rows, BF16 [N][d], box {64, 128}
+  CUtensorMap tu;  // users, BF16 [Bp][d], box {64, Bp}
+  const uint32_t *wkey[kGroups];
+  const uint8_t *wvals[kGroups];
+  const uint32_t *win_ptr[kGroups];
+  const float *wT;             // [n_keys][Bp] expanded weights, user-minor
+  const uint64_t *filters;     // [B][words] (rows of users without a filter are unused)
+  const uint32_t *has_filter;  // [B]
+  uint32_t n_ads, n_win, B, Bp, d, m, cap_u, list_cap, words;
+  uint32_t sa, lb, tb;         // A stages, list buffers, TMEM buffers
+  CandEntry *cand;             // [grid][B][cap_u]
+  uint32_t *cand_n;            // [grid][B]
+  unsigned long long *cand_thr;  // [grid][B]
+  Ctrl *ctrl;
+};
+
+struct BatchSmem {
+  uint64_t a_full[2], a_empty[2], t_full[2], t_empty[2], l_full[2], l_empty[2], u_full;
+  uint32_t tmem_base;
+  uint32_t cnt_u[kMaxUsers];
+  unsigned long long thr_u[kMaxUsers];
+  uint32_t abort, stop_epi, stop_list, n_issued, n_mma;
+};
+
+__device__ __forceinline__ uint32_t ushift(uint32_t g) { return g >= 2 ? g - 2 : 0; }
+
+// Walk the real slots of window w: f(ad_in_window, key).  `t`/`nt`: this
+// thread's index in the walking group.
+template <typename F>
+__device__ __forceinline__ void walk_window(const BatchArgs &a, uint32_t w, int t, int nt, F f) {
+#pragma unroll 1
+  for (uint32_t g = 0; g < (uint32_t)kGroups; g++) {
+    const uint32_t lo = __ldg(a.win_ptr[g] + w), hi = __ldg(a.win_ptr[g] + w + 1);
+    const uint32_t us = ushift(g);
+    const uint32_t units = (hi - lo) << us;
+    for (uint32_t u = t; u < units; u += nt) {
+      const uint32_t bk = lo + (u >> us), wi = u & ((1u << us) - 1u);
+      const uint32_t key = __ldg(a.wkey[g] + bk);
+      uint32_t word, ns;
+      if (g >= 2) {
+        word = __ldg(reinterpret_cast<const uint32_t *>(a.wvals[g]) + (((uint64_t)bk << us) + wi));
+        ns = 4;
+      } else if (g == 1) {
+        word = __ldg(reinterpret_cast<const unsigned short *>(a.wvals[1]) + bk);
+        ns = 2;
+      } else {
+        word = __ldg(a.wvals[0] + bk);
+        ns = 1;
+      }
+      for (uint32_t s = 0; s < ns; s++) {
+        const uint32_t l = (word >> (8 * s)) & 255u;
+        if ((s == 0 && wi == 0) || l != 0) f(l, key);
+      }
+    }
+  }
+}
+
+// Warp-level radix select: T with exactly `need` keys >= T among n (global).
+__device__ uint64_t warp_radix_select(const CandEntry *buf, uint32_t n, uint32_t need,
+                                      uint32_t *hist /* 256 words, this warp's */) {
+  const int lane = threadIdx.x & 31;
+  uint64_t prefix = 0;
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int i = lane; i < 256; i += 32) hist[i] = 0;
+    __syncwarp();
+    const uint64_t hi_mask = (shift == 56) ? 0ull : (~0ull << (shift + 8));
+    for (uint32_t i = lane; i < n; i += 32) {
+      const uint64_t x = buf[i].key;
+      if ((x & hi_mask) == prefix) atomicAdd(&hist[(x >> shift) & 255u], 1u);
+    }
+    __syncwarp();
+    uint32_t c[8], tot = 0;
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+      c[e] = hist[255 - 8 * lane - e];
+      tot += c[e];
+    }
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    uint32_t acc = incl - tot, dg = 0, nn = 0, whole = 0;
+    bool found = false;
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+      if (!found && acc < need && need <= acc + c[e]) {
+        found = true;
+        dg = 255 - 8 * lane - e;
+        nn = need - acc;
+        whole = (need - acc == c[e]) ? 1u : 0u;
+      }
+      acc += c[e];
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, found);
+    const int src = __ffs(bal) - 1;
+    dg = __shfl_sync(0xffffffffu, dg, src);
+    need = __shfl_sync(0xffffffffu, nn, src);
+    whole = __shfl_sync(0xffffffffu, whole, src);
+    prefix |= (uint64_t)dg << shift;
+    __syncwarp();
+    if (whole) break;
+  }
+  return prefix;
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_constant__ BatchArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  __shared__ BatchSmem sm;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t kb_n = a.d / 64;
+  const uint32_t a_stage = 2u * kb_n * 16384u;  // two 128-row M-tiles
+  uint8_t *su = smem;                             // kb_n x [Bp x 128 B]
+  uint8_t *sa = su + (size_t)kb_n * a.Bp * 128;   // sa stages
+  uint32_t *lists = reinterpret_cast<uint32_t *>(sa + (size_t)a.sa * a_stage);
+  const uint32_t list_words = 2 * (kBWin + 1) + a.list_cap;  // off[257], fill[257], keys
+  float *wtile = reinterpret_cast<float *>(lists + (size_t)a.lb * list_words);  // [8][32][33]
+
+  const uint32_t w_begin = (uint32_t)(((uint64_t)a.n_win * blockIdx.x) / gridDim.x);
+  const uint32_t w_end = (uint32_t)(((uint64_t)a.n_win * (blockIdx.x + 1)) / gridDim.x);
+  const uint32_t my_wins = w_end - w_begin;
+  const uint32_t tcols = 2u * a.Bp;  // TMEM columns per window (two M-tiles)
+  uint32_t ncols = 32;
+  while (ncols < tcols * a.tb) ncols <<= 1;
+
+  for (uint32_t b = tid; b < a.B; b += kBatchThreads) {
+    sm.cnt_u[b] = 0;
+    sm.thr_u[b] = 0ull;
+  }
+  if (warp == kMmaWarp) {
+    tmem_alloc(&sm.tmem_base, ncols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    sm.abort = 0;
+    sm.stop_epi = 0;
+    sm.n_issued = 0;
+    sm.n_mma = 0;
+    for (int q = 0; q < 2; q++) {
+      mbar_init(&sm.a_full[q], 1);
+      mbar_init(&sm.a_empty[q], 1);
+      mbar_init(&sm.t_full[q], 1);
+      mbar_init(&sm.t_empty[q], 1);
+      mbar_init(&sm.l_full[q], kListThreads);
+      mbar_init(&sm.l_empty[q], 1);
+    }
+    mbar_init(&sm.u_full, 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem_base;
+
+  if (warp == kProdWarpB) {
+    // ---------------------------------------------------------- producer
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&sm.u_full, kb_n * a.Bp * 128u);
+      for (uint32_t kb = 0; kb < kb_n; kb++)
+        tma_load_2d(su + (size_t)kb * a.Bp * 128, &a.tu, (int)(kb * 64), 0, &sm.u_full);
+      for (uint32_t j = 0; j < my_wins; j++) {
+        const uint32_t s = j % a.sa;
+        if (j >= a.sa && !mbar_wait_bounded(&sm.a_empty[s], ((j / a.sa) - 1) & 1u, kWaitTimeoutNs)) {
+          atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
+          sm.abort = 1;
+          break;
+        }
+        if (*((volatile uint32_t *)&sm.abort)) break;
+        const int row0 = (int)((w_begin + j) * kBWin);
+        uint8_t *dst = sa + (size_t)s * a_stage;
+        mbar_arrive_expect_tx(&sm.a_full[s], a_stage);
+        for (uint32_t mt = 0; mt < 2; mt++)
+          for (uint32_t kb = 0; kb < kb_n; kb++)
+            tma_load_2d(dst + (mt * kb_n + kb) * 16384, &a.ta, (int)(kb * 64), row0 + (int)mt * 128,
+                        &sm.a_full[s]);
+        sm.n_issued = j + 1;
+      }
+    }
+  } else if (warp == kMmaWarp) {
+    // ---------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      bool ok = mbar_wait_bounded(&sm.u_full, 0, kWaitTimeoutNs);
+      const uint32_t idesc = idesc_bf16_f32(128, a.Bp);
+      for (uint32_t j = 0; ok && j < my_wins; j++) {
+        const uint32_t s = j % a.sa, tb = j % a.tb;
+        ok = mbar_wait_bounded(&sm.a_full[s], (j / a.sa) & 1u, kWaitTimeoutNs);
+        if (ok && j >= a.tb) ok = mbar_wait_bounded(&sm.t_empty[tb], ((j / a.tb) - 1) & 1u, kWaitTimeoutNs);
+        if (!ok || *((volatile uint32_t *)&sm.abort)) break;
+        tc_fence_after();
+        const uint8_t *as = sa + (size_t)s * a_stage;
+        for (uint32_t mt = 0; mt < 2; mt++) {
+          const uint32_t dcol = tmem + tb * tcols + mt * a.Bp;
+          for (uint32_t k = 0; k < a.d / 16; k++) {
+            const uint32_t kb = k / 4, kk = k % 4;
+            const uint64_t ad = sdesc_k_sw128(smem_u32(as + (mt * kb_n + kb) * 16384 + kk * 32));
+            const uint64_t bd = sdesc_k_sw128(smem_u32(su + (size_t)kb * a.Bp * 128 + kk * 32));
+            umma_bf16(dcol, ad, bd, idesc, k > 0 ? 1u : 0u);
+          }
+        }
+        umma_commit(&sm.a_empty[s]);
+        umma_commit(&sm.t_full[tb]);
+        sm.n_mma = j + 1;
+      }
+      if (!ok) {
+        atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
+        sm.abort = 1;
+      }
+    }
+  } else if (warp >= kEpiWarps) {
+    // ---------------------------------------------------------- list builders
+    const int lt = tid - kEpiThreads;
+    for (uint32_t j = 0; j < my_wins; j++) {
+      const uint32_t lbuf = j % a.lb;
+      if (lt == 0) {
+        uint32_t stop = *((volatile uint32_t *)&sm.abort);
+        if (!stop && j >= a.lb &&
+            !mbar_wait_bounded(&sm.l_empty[lbuf], ((j / a.lb) - 1) & 1u, kWaitTimeoutNs)) {
+          atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
+          sm.abort = 1;
+          stop = 1;
+        }
+        sm.stop_list = stop;
+      }
+      named_sync(2, kListThreads);
+      if (sm.stop_list) break;
+      if (j >= a.lb) mbar_try_wait(&sm.l_empty[lbuf], ((j / a.lb) - 1) & 1u);
+      uint32_t *off = lists + (size_t)lbuf * list_words;
+      uint32_t *fill = off + (kBWin + 1);
+      uint32_t *keys = fill + (kBWin + 1);
+      for (int i = lt; i < 2 * (kBWin + 1); i += kListThreads) off[i] = 0;
+      named_sync(2, kListThreads);
+      const uint32_t w = w_begin + j;
+      walk_window(a, w, lt, kListThreads, [&](uint32_t l, uint32_t) { atomicAdd(&fill[l], 1u); });
+      named_sync(2, kListThreads);
+      if (lt < 32) {  // exclusive scan of 256 counts -> off[0..256]
+        uint32_t c[8], tot = 0;
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+          c[e] = fill[8 * lt + e];
+          tot += c[e];
+        }
+        uint32_t incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lt >= o) incl += v;
+        }
+        uint32_t run = incl - tot;
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+          off[8 * lt + e] = run;
+          fill[8 * lt + e] = 0;
+          run += c[e];
+        }
+        if (lt == 31) off[kBWin] = run;
+      }
+      named_sync(2, kListThreads);
+      walk_window(a, w, lt, kListThreads, [&](uint32_t l, uint32_t key) {
+        const uint32_t pos = off[l] + atomicAdd(&fill[l], 1u);
+        if (pos < a.list_cap) keys[pos] = key;
+      });
+      mbar_arrive(&sm.l_full[lbuf]);  // release: this thread's list writes
+    }
+  } else {
+    // ---------------------------------------------------------- epilogue
+    const GroupSync gsync{1, kEpiThreads};
+    float *wt = wtile + (size_t)warp * 32 * 33;
+    const uint32_t lane_base = (uint32_t)(32 * (warp % 4)) << 16;
+    const uint32_t mt = warp / 4;
+    for (uint32_t j = 0; j < my_wins; j++) {
+      const uint32_t tb = j % a.tb, lbuf = j % a.lb;
+      if (tid == 0) {
+        uint32_t stop = *((volatile uint32_t *)&sm.abort);
+        if (!stop && !mbar_wait_bounded(&sm.t_full[tb], (j / a.tb) & 1u, kWaitTimeoutNs)) stop = 1;
+        if (!stop && !mbar_wait_bounded(&sm.l_full[lbuf], (j / a.lb) & 1u, kWaitTimeoutNs)) stop = 1;
+        if (stop && !*((volatile uint32_t *)&sm.abort)) {
+          atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
+          sm.abort = 1;
+        }
+        sm.stop_epi = stop;
+      }
+      gsync();
+      if (sm.stop_epi) break;
+      mbar_try_wait(&sm.t_full[tb], (j / a.tb) & 1u);
+      mbar_try_wait(&sm.l_full[lbuf], (j / a.lb) & 1u);
+      tc_fence_after();
+      const uint32_t *off = lists + (size_t)lbuf * list_words;
+      const uint32_t *keys = off + 2 * (kBWin + 1);
+      const uint32_t w = w_begin + j;
+      const uint32_t my_ad_w = 32 * warp + lane;  // this lane's ad within the window
+      const uint32_t ad = w * kBWin + my_ad_w;
+      const bool valid = ad < a.n_ads;
+      for (uint32_t b0 = 0; b0 < a.Bp; b0 += 32) {
+        // wide terms of the warp's 32 ads for users b0 .. b0+31 (lane = user)
+        for (int i = 0; i < 32; i++) {
+          const uint32_t l = 32 * warp + i;
+          const uint32_t k0 = off[l], k1 = min(off[l + 1], a.list_cap);
+          float acc = 0.f;
+          for (uint32_t q = k0; q < k1; q++)
+            acc += __ldg(a.wT + (uint64_t)keys[q] * a.Bp + b0 + lane);
+          wt[i * 33 + lane] = acc;
+        }
+        __syncwarp();
+        uint32_t r[32];
+        tmem_ld32(tmem + lane_base + tb * tcols + mt * a.Bp + b0, r);
+        tmem_ld_wait();
+#pragma unroll
+        for (int jj = 0; jj < 32; jj++) {
+          const uint32_t b = b0 + jj;
+          if (b >= a.B || !valid) continue;
+          const float wide = wt[lane * 33 + jj];
+          const float score = __uint_as_float(r[jj]) + wide;
+          if (a.has_filter[b] &&
+              !((a.filters[(uint64_t)b * a.words + (ad >> 6)] >> (ad & 63)) & 1ull))
+            continue;
+          const unsigned long long key = make_key(score, ad);
+          if (key < sm.thr_u[b]) continue;
+          const uint32_t pos = atomicAdd(&sm.cnt_u[b], 1u);
+          if (pos < a.cap_u) {
+            CandEntry e;
+            e.key = key;
+            e.wide = wide;
+            e.pad = 0;
+            a.cand[((uint64_t)blockIdx.x * a.B + b) * a.cap_u + pos] = e;
+          } else {
+            atomicOr(&a.ctrl->flags, DEVERR_OVERFLOW);
+          }
+        }
+        __syncwarp();
+      }
+      tc_fence_before();
+      gsync();
+      if (tid == 0) {
+        mbar_arrive(&sm.t_empty[tb]);
+        mbar_arrive(&sm.l_empty[lbuf]);
+      }
+      // keep each user's buffer below capacity: exact top-m by radix select
+      for (uint32_t b = warp; b < a.B; b += kEpiWarps) {
+        const uint32_t n = sm.cnt_u[b];
+        if (n + kBWin <= a.cap_u) continue;
+        CandEntry *buf = a.cand + ((uint64_t)blockIdx.x * a.B + b) * a.cap_u;
+        const uint32_t nn = min(n, a.cap_u);
+        const uint64_t T = warp_radix_select(buf, nn, a.m, reinterpret_cast<uint32_t *>(wt));
+        uint32_t kept = 0;
+        for (uint32_t b0 = 0; b0 < nn; b0 += 32) {
+          const uint32_t i = b0 + lane;
+          CandEntry e;
+          e.key = 0;
+          if (i < nn) e = buf[i];
+          const bool kp = i < nn && e.key >= T;
+          const uint32_t bal = __ballot_sync(0xffffffffu, kp);
+          __syncwarp();
+          if (kp) buf[kept + __popc(bal & ((1u << lane) - 1u))] = e;
+          kept += __popc(bal);
+          __syncwarp();
+        }
+        if (lane == 0) {
+          sm.cnt_u[b] = kept;
+          sm.thr_u[b] = T;
+        }
+        __syncwarp();
+      }
+      gsync();
+    }
+    gsync();
+    // final trim to at most m candidates per user (the merge reads grid * m)
+    if (!sm.stop_epi) {
+      for (uint32_t b = warp; b < a.B; b += kEpiWarps) {
+        const uint32_t n = min(sm.cnt_u[b], a.cap_u);
+        if (n <= a.m) continue;
+        CandEntry *buf = a.cand + ((uint64_t)blockIdx.x * a.B + b) * a.cap_u;
+        const uint64_t T = warp_radix_select(buf, n, a.m, reinterpret_cast<uint32_t *>(wt));
+        uint32_t kept = 0;
+        for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+          const uint32_t i = b0 + lane;
+          CandEntry e;
+          e.key = 0;
+          if (i < n) e = buf[i];
+          const bool kp = i < n && e.key >= T;
+          const uint32_t bal = __ballot_sync(0xffffffffu, kp);
+          __syncwarp();
+          if (kp) buf[kept + __popc(bal & ((1u << lane) - 1u))] = e;
+          kept += __popc(bal);
+          __syncwarp();
+        }
+        if (lane == 0) {
+          sm.cnt_u[b] = kept;
+          sm.thr_u[b] = T > sm.thr_u[b] ? T : sm.thr_u[b];
+        }
+        __syncwarp();
+      }
+    }
+    gsync();
+    for (uint32_t b = tid; b < a.B; b += kEpiThreads) {
+      a.cand_n[(uint64_t)blockIdx.x * a.B + b] = min(sm.cnt_u[b], a.cap_u);
+      a.cand_thr[(uint64_t)blockIdx.x * a.B + b] = sm.thr_u[b];
+    }
+  }
+  // Drain before teardown (matters only after an abort): the last issued
+  // tile loads must have landed and the last MMAs retired before the
+  // shared memory and TMEM are released.
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t ni = sm.n_issued, nm = sm.n_mma;
+    bool ok = mbar_wait_bounded(&sm.u_full, 0, kWaitTimeoutNs);
+    for (uint32_t j = ni > a.sa ? ni - a.sa : 0; ok && j < ni; j++)
+      ok = mbar_wait_bounded(&sm.a_full[j % a.sa], (j / a.sa) & 1u, kWaitTimeoutNs);
+    if (ok && nm) ok = mbar_wait_bounded(&sm.t_full[(nm - 1) % a.tb], ((nm - 1) / a.tb) & 1u, kWaitTimeoutNs);
+    if (!ok) atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kMmaWarp) tmem_dealloc(tmem, ncols);
+}
+
+// Per user: the best R*K of the CTAs' candidate buffers (exact if no CTA's
+// buffer threshold exceeds the selected cut), rescored in FP32, best K.
+constexpr int kMergeThreads = 1024;
+constexpr uint32_t kMergeCap = 32768;  // approximate candidates gathered per user
+
+__global__ void __launch_bounds__(kMergeThreads) k_batch_merge(
+    const CandEntry *__restrict__ cand, const uint32_t *__restrict__ cand_n,
+    const unsigned long long *__restrict__ cand_thr, uint32_t grid, uint32_t B, uint32_t cap_u,
+    const uint32_t *__restrict__ kscan, const uint32_t *__restrict__ kout, uint32_t kmax,
+    const float *__restrict__ emb, uint32_t d, const float *__restrict__ h_u,
+    uint64_t *__restrict__ scratch /* [B][kMergeCap + 8192] */, uint32_t *__restrict__ out_ids,
+    float *__restrict__ out_scores, uint32_t *__restrict__ status /* [B] */) {
+  extern __shared__ __align__(16) uint64_t s_v[];  // 8192 keys
+  __shared__ uint32_t s_hist[256], s_misc[8], s_cnt;
+  __shared__ uint32_t s_base[1024];
+  __shared__ float s_h[128];
+  const uint32_t b = blockIdx.x;
+  const uint32_t ks = kscan[b], ko = kout[b];
+  uint64_t *keys = scratch + (uint64_t)b * (kMergeCap + 8192);  // gathered approximate keys
+  uint32_t inexact = 0;
+  // 1. gather this user's candidates into scratch (bounded by 8192: with the
+  //    per-CTA thresholds far fewer survive; beyond that the request is flagged)
+  if (threadIdx.x == 0) s_cnt = 0;
+  for (uint32_t i = threadIdx.x; i < d; i += kMergeThreads) s_h[i] = h_u[(uint64_t)b * d + i];
+  __syncthreads();
+  // count first, then copy (entries of all CTAs, in CTA order)
+  uint32_t total = 0;
+  for (uint32_t c0 = 0; c0 < grid; c0 += kMergeThreads) {
+    const uint32_t c = c0 + threadIdx.x;
+    const uint32_t n = c < grid ? cand_n[(uint64_t)c * B + b] : 0u;
+    // block-wide exclusive scan of n (simple two-level)
+    uint32_t incl = n;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_base[wp] = incl;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      uint32_t x = s_base[threadIdx.x], in2 = x;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, in2, o);
+        if (threadIdx.x >= o) in2 += v;
+      }
+      s_base[threadIdx.x] = in2 - x;
+      if (threadIdx.x == 31) s_misc[4] = in2;
+    }
+    __syncthreads();
+    const uint32_t start = total + s_base[wp] + incl - n;
+    if (c < grid) {
+      const CandEntry *src = cand + ((uint64_t)c * B + b) * cap_u;
+      for (uint32_t i = 0; i < n; i++)
+        if (start + i < kMergeCap) keys[start + i] = src[i].key;
+    }
+    total += s_misc[4];
+    __syncthreads();
+  }
+  if (total > kMergeCap) {
+    inexact = 1;
+    total = kMergeCap;
+  }
+  // 2. the best ks of them by approximate score (T = 0: all of them)
+  uint64_t T = 0;
+  if (total > ks) T = cta_radix_select<kMergeThreads>(keys, total, ks, s_hist, s_misc);
+  // Exactness: CTA c holds every one of its candidates with key >= its
+  // threshold, so the union's best ks are the inventory's best ks when no
+  // threshold lies above the selected cut T.
+  for (uint32_t c = threadIdx.x; c < grid; c += kMergeThreads)
+    if (cand_thr[(uint64_t)c * B + b] > T) inexact = 1;
+  if (inexact) atomicOr(&status[b], 1u);
+  // 3. FP32 rescoring of the survivors: gather (id, wide) into shared
+  //    memory, then one warp per candidate (coalesced FP32 row read).
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  uint64_t *resc = keys + kMergeCap;
+  for (uint32_t c = 0; c < grid; c++) {
+    const uint32_t n = cand_n[(uint64_t)c * B + b];
+    const CandEntry *src = cand + ((uint64_t)c * B + b) * cap_u;
+    for (uint32_t i = threadIdx.x; i < n; i += kMergeThreads) {
+      const CandEntry e = src[i];
+      if (e.key < T || e.key == 0ull) continue;
+      const uint32_t pos = atomicAdd(&s_cnt, 1u);
+      if (pos < 8192) s_v[pos] = ((uint64_t)__float_as_uint(e.wide) << 32) | key_id(e.key);
+    }
+  }
+  __syncthreads();
+  const uint32_t nres = min(s_cnt, 8192u);
+  {
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (uint32_t i = wp; i < nres; i += kMergeThreads / 32) {
+      const uint64_t e = s_v[i];
+      const uint32_t id = (uint32_t)e;
+      const float *row = emb + (uint64_t)id * d;
+      float dot = 0.f;
+      for (uint32_t t = lane; t < d; t += 32) dot = fmaf(s_h[t], __ldg(row + t), dot);
+      for (int o = 16; o; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+      if (lane == 0) resc[i] = make_key(dot + __uint_as_float((uint32_t)(e >> 32)), id);
+    }
+  }
+  __syncthreads();
+  // 4. best ko, sorted
+  uint64_t T2 = 0;
+  if (nres > ko) T2 = cta_radix_select<kMergeThreads>(resc, nres, ko, s_hist, s_misc);
+  if (threadIdx.x == 0) s_cnt = 0;
+  __syncthreads();
+  const uint32_t take = min(nres, ko);
+  uint32_t p2 = 1;
+  while (p2 < take) p2 <<= 1;
+  for (uint32_t i = threadIdx.x; i < nres; i += kMergeThreads) {
+    const uint64_t x = resc[i];
+    if (x >= T2) {
+      const uint32_t pos = atomicAdd(&s_cnt, 1u);
+      if (pos < p2) s_v[pos] = x;
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = take + threadIdx.x; i < p2; i += kMergeThreads) s_v[i] = 0ull;
+  // bitonic sort, descending
+  for (uint32_t size = 2; size <= p2; size <<= 1)
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < p2 / 2; i += kMergeThreads) {
+        const uint32_t lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+        const bool desc = (lo & size) == 0;
+        const uint64_t x = s_v[lo], y = s_v[hi];
+        if ((x < y) == desc) {
+          s_v[lo] = y;
+          s_v[hi] = x;
+        }
+      }
+    }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < kmax; i += kMergeThreads) {
+    const uint64_t x = i < take ? s_v[i] : 0ull;
+    out_ids[(uint64_t)b * kmax + i] = i < take ? key_id(x) : 0xFFFFFFFFu;
+    out_scores[(uint64_t)b * kmax + i] = i < take ? key_score(x) : -INFINITY;
+  }
+}
+
+}  // namespace ebr
+
+// =====================================================================
+// Host side of the batched path
+// =====================================================================
+namespace ebr {
+
+struct BatchPlan {
+  uint32_t Bp, m, cap_u, sa, lb, tb, list_cap;
+  size_t smem;
+};
+
+// Shared-memory layout of k_batch_window for B users: the users' tile, `sa`
+// ad stages, `lb` per-ad key lists and the epilogue transpose tiles.
+// Preference: two list buffers (list building overlaps the epilogue, the
+// slowest role), then two ad stages.
+static bool plan_smem(const ebr_index *ix, uint32_t B, BatchPlan *p) {
+  p->Bp = (B + 31) / 32 * 32;
+  p->list_cap = ix->max_win_slots;
+  p->tb = (4 * p->Bp <= 512) ? 2 : 1;
+  const uint32_t kb_n = ix->d / 64;
+  const size_t u_bytes = (size_t)kb_n * p->Bp * 128;
+  const size_t a_stage = 2ull * kb_n * 16384;
+  const size_t list_bytes = (2ull * (kBWin + 1) + p->list_cap) * 4;
+  const size_t wtile = (size_t)kEpiWarps * 32 * 33 * 4;
+  const size_t budget = 220 * 1024;
+  const uint32_t order[4][2] = {{2, 2}, {1, 2}, {2, 1}, {1, 1}};  // {sa, lb}
+  for (const auto &o : order) {
+    const size_t need = 1024 + u_bytes + o[0] * a_stage + o[1] * list_bytes + wtile;
+    if (need <= budget) {
+      p->sa = o[0];
+      p->lb = o[1];
+      p->smem = need;
+      return true;
+    }
+  }
+  return false;
+}
+
+bool batch_qualifies(const ebr_index *ix, const ebr_cross *cross, const ebr_query *q,
+                     uint32_t batch) {
+  if (ix->dtype != EBR_BF16 || (ix->d != 64 && ix->d != 128) || batch < 2 ||
+      batch > (uint32_t)kMaxUsers || !cross || cross->n_keys != ix->n_keys ||
+      ix->max_win_slots == 0 || ix->n_win == 0)
+    return false;
+  for (uint32_t b = 0; b < batch; b++) {
+    if (!q[b].user_vals || (q[b].flags & EBR_QF_KEY_MAJOR)) return false;
+    if ((uint64_t)q[b].k * ix->rescore_mult > 8192) return false;
+  }
+  BatchPlan p;
+  return plan_smem(ix, batch, &p);
+}
+
+static bool plan_batch(const ebr_index *ix, uint32_t B, uint32_t kscan_max, int grid,
+                       BatchPlan *p) {
+  if (!plan_smem(ix, B, p)) return false;
+  const uint32_t per_cta = (kscan_max + grid - 1) / grid;
+  p->m = std::max<uint32_t>(64, (2 * per_cta + 32 + 31) / 32 * 32);
+  p->cap_u = 2 * p->m + kBWin;
+  return (uint64_t)grid * p->m <= kMergeCap;
+}
+
+static int stage(void *dst, const void *src, size_t bytes, int io, cudaStream_t st) {
+  if (!bytes) return EBR_OK;
+  EBR_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes,
+                               io == EBR_IO_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                               st));
+  return EBR_OK;
+}
+
+int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint32_t B,
+                uint32_t *out_ids, float *out_scores, uint32_t kmax, int io, cudaStream_t st) {
+  BatchWs &w = ix->bws;
+  const uint32_t d = ix->d, fu = cross->f_u, words = (ix->n_ads + 63) / 64;
+  std::vector<uint32_t> kk(2 * B), hasf(B, 0);
+  uint32_t kscan_max = 1;
+  for (uint32_t b = 0; b < B; b++) {
+    kk[b] = std::min<uint32_t>(q[b].k * ix->rescore_mult, ix->n_ads);
+    kk[B + b] = q[b].k;
+    kscan_max = std::max(kscan_max, kk[b]);
+    hasf[b] = q[b].filter ? 1u : 0u;
+  }
+  const int grid = std::max(1, std::min<int>(ix->num_sms, (int)ix->n_win));
+  BatchPlan pl;
+  if (!plan_batch(ix, B, kscan_max, grid, &pl)) {
+    set_error("batched scan: window lists of %u slots do not fit shared memory", ix->max_win_slots);
+    return EBR_EINVAL;
+  }
+  const uint32_t Bp = pl.Bp;
+  EBR_TRY(dev_reserve(w.users_f32, (size_t)Bp * d * 4));
+  EBR_TRY(dev_reserve(w.users_bf16, (size_t)Bp * d * 2));
+  EBR_TRY(dev_reserve(w.user_vals, (size_t)B * fu * 4));
+  EBR_TRY(dev_reserve(w.wT, (size_t)ix->n_keys * Bp * 4));
+  EBR_TRY(dev_reserve(w.filters, (size_t)B * words * 8));
+  EBR_TRY(dev_reserve(w.has_filter, (size_t)B * 4));
+  EBR_TRY(dev_reserve(w.kk, (size_t)2 * B * 4));
+  EBR_TRY(dev_reserve(w.status, (size_t)B * 4 + 64));
+  EBR_TRY(dev_reserve(w.cand, (size_t)grid * B * pl.cap_u * sizeof(CandEntry)));
+  EBR_TRY(dev_reserve(w.cand_n, (size_t)grid * B * 4));
+  EBR_TRY(dev_reserve(w.cand_thr, (size_t)grid * B * 8));
+  EBR_TRY(dev_reserve(w.scratch, (size_t)B * (kMergeCap + 8192) * 8));
+  EBR_TRY(dev_reserve(w.out, (size_t)B * kmax * 8 + 256));
+  Ctrl *ctrl = (Ctrl *)ix->ws.ctrl.p;
+  if (!ctrl) {
+    EBR_TRY(dev_reserve(ix->ws.ctrl, 256));
+    ctrl = (Ctrl *)ix->ws.ctrl.p;
+  }
+  EBR_CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
+  // request inputs
+  EBR_CUDA_TRY(cudaMemsetAsync(w.users_f32.p, 0, (size_t)Bp * d * 4, st));
+  for (uint32_t b = 0; b < B; b++) {
+    EBR_TRY(stage((float *)w.users_f32.p + (size_t)b * d, q[b].h_u, d * 4, io, st));
+    EBR_TRY(stage((uint32_t *)w.user_vals.p + (size_t)b * fu, q[b].user_vals, fu * 4, io, st));
+    if (q[b].filter)
+      EBR_TRY(stage((uint64_t *)w.filters.p + (size_t)b * words, q[b].filter, words * 8, io, st));
+  }
+  EBR_CUDA_TRY(cudaMemcpyAsync(w.has_filter.p, hasf.data(), B * 4, cudaMemcpyHostToDevice, st));
+  EBR_CUDA_TRY(cudaMemcpyAsync(w.kk.p, kk.data(), 2 * B * 4, cudaMemcpyHostToDevice, st));
+  EBR_CUDA_TRY(cudaMemsetAsync(w.status.p, 0, B * 4, st));
+  EBR_TRY(launch_quantize((const float *)w.users_f32.p, (uint64_t)Bp * d, EBR_BF16, w.users_bf16.p,
+                          st));
+  EBR_TRY(expand_transposed(cross, (const uint32_t *)w.user_vals.p, B, Bp, (float *)w.wT.p,
+                            &ctrl->flags, st));
+  ix->launches += 2;
+  // tensor maps
+  if (!w.tmap_ready) {
+    EBR_TRY(make_tmap_bf16(reinterpret_cast<CUtensorMap *>(w.tmap_bytes), ix->emb_q.p, ix->n_ads,
+                           d, 128));
+    w.tmap_ready = true;
+  }
+  BatchArgs a;
+  memset(&a, 0, sizeof(a));
+  memcpy(&a.ta, w.tmap_bytes, sizeof(CUtensorMap));
+  EBR_TRY(make_tmap_bf16(&a.tu, w.users_bf16.p, Bp, d, Bp));
+  for (int g = 0; g < kGroups; g++) {
+    a.wkey[g] = ix->wkey[g];
+    a.wvals[g] = ix->wvals[g];
+    a.win_ptr[g] = ix->win_ptr[g];
+  }
+  a.wT = (const float *)w.wT.p;
+  a.filters = (const uint64_t *)w.filters.p;
+  a.has_filter = (const uint32_t *)w.has_filter.p;
+  a.n_ads = ix->n_ads;
+  a.n_win = ix->n_win;
+  a.B = B;
+  a.Bp = Bp;
+  a.d = d;
+  a.m = pl.m;
+  a.cap_u = pl.cap_u;
+  a.list_cap = pl.list_cap;
+  a.words = words;
+  a.sa = pl.sa;
+  a.lb = pl.lb;
+  a.tb = pl.tb;
+  a.cand = (CandEntry *)w.cand.p;
+  a.cand_n = (uint32_t *)w.cand_n.p;
+  a.cand_thr = (unsigned long long *)w.cand_thr.p;
+  a.ctrl = ctrl;
+  EBR_CUDA_TRY(cudaFuncSetAttribute(k_batch_window, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)pl.smem));
+  k_batch_window<<<grid, kBatchThreads, pl.smem, st>>>(a);
+  EBR_CUDA_TRY(cudaGetLastError());
+  uint32_t *d_ids = out_ids;
+  float *d_scores = out_scores;
+  if (io == EBR_IO_HOST) {
+    d_ids = (uint32_t *)w.out.p;
+    d_scores = (float *)((char *)w.out.p + (((size_t)B * kmax * 4 + 255) / 256 * 256));
+  }
+  EBR_CUDA_TRY(cudaFuncSetAttribute(k_batch_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    8192 * 8));
+  k_batch_merge<<<B, kMergeThreads, 8192 * 8, st>>>(
+      (const CandEntry *)w.cand.p, (const uint32_t *)w.cand_n.p,
+      (const unsigned long long *)w.cand_thr.p, (uint32_t)grid, B, pl.cap_u,
+      (const uint32_t *)w.kk.p, (const uint32_t *)w.kk.p + B, kmax, (const float *)ix->emb_f32.p, d,
+      (const float *)w.users_f32.p, (uint64_t *)w.scratch.p, d_ids, d_scores,
+      (uint32_t *)w.status.p);
+  EBR_CUDA_TRY(cudaGetLastError());
+  ix->launches += 2;
+  ix->batched += B;
+  // status: flags and users whose per-CTA buffers could not prove exactness
+  std::vector<uint32_t> status(B);
+  Ctrl hc;
+  EBR_CUDA_TRY(cudaMemcpyAsync(status.data(), w.status.p, B * 4, cudaMemcpyDeviceToHost, st));
+  EBR_CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  EBR_CUDA_TRY(cudaStreamSynchronize(st));
+  EBR_TRY(check_device_flags(hc.flags, "ebr_score_topk (batched)"));
+  for (uint32_t b = 0; b < B; b++) {
+    if (!status[b]) continue;
+    // exact fallback for this user: the single-request scan
+    ebr_query dq = q[b];
+    dq.h_u = (const float *)w.users_f32.p + (size_t)b * d;
+    dq.user_vals = (const uint32_t *)w.user_vals.p + (size_t)b * fu;
+    dq.filter = q[b].filter ? (const uint64_t *)w.filters.p + (size_t)b * words : nullptr;
+    EBR_TRY(ws_prepare_one(ix, ix->n_keys, 8192));
+    EBR_TRY(query_one(ix, cross, dq, d_ids + (size_t)b * kmax, d_scores + (size_t)b * kmax, kmax,
+                      st));
+    ix->fallbacks += 1;
+    EBR_CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    EBR_CUDA_TRY(cudaStreamSynchronize(st));
+    EBR_TRY(check_device_flags(hc.flags, "ebr_score_topk (single-request recompute)"));
+  }
+  if (io == EBR_IO_HOST) {
+    EBR_CUDA_TRY(cudaMemcpyAsync(out_ids, d_ids, (size_t)B * kmax * 4, cudaMemcpyDeviceToHost, st));
+    EBR_CUDA_TRY(
+        cudaMemcpyAsync(out_scores, d_scores, (size_t)B * kmax * 4, cudaMemcpyDeviceToHost, st));
+  }
+  EBR_CUDA_TRY(cudaStreamSynchronize(st));
+  return EBR_OK;
+}
+
+}  // namespace ebr

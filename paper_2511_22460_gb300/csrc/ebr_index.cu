@@ -172,9 +172,9 @@ __global__ void k_wm_emit(const uint64_t *__restrict__ skey, const uint32_t *__r
 // Also: the most 32-unit work chunks any window has (a unit is one 4-slot
 // word in groups >= 2, one block in groups 0 and 1).
 __global__ void k_win_bytes(WinPtrs wp, uint32_t n_win, unsigned int *out_max) {
-  uint32_t mx = 0, mc = 0;
+  uint32_t mx = 0, mc = 0, ms = 0;
   for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < n_win; w += gridDim.x * blockDim.x) {
-    uint64_t total = 0, chunks = 0;
+    uint64_t total = 0, chunks = 0, slots = 0;
     for (int g = 0; g < kGroups; g++) {
       const uint64_t lo = wp.p[g][w], hi = wp.p[g][w + 1];
       if (hi == lo) continue;
@@ -182,12 +182,15 @@ __global__ void k_win_bytes(WinPtrs wp, uint32_t n_win, unsigned int *out_max) {
       const uint64_t v0 = (lo << g) & ~15ull, v1 = ((hi << g) + 15) & ~15ull;
       total += (k1 - k0) + (v1 - v0);
       chunks += (((hi - lo) << (g >= 2 ? g - 2 : 0)) + 31) >> 5;
+      slots += (hi - lo) << g;
     }
     mx = max(mx, (uint32_t)min(total, (uint64_t)0xFFFFFFFFu));
     mc = max(mc, (uint32_t)min(chunks, (uint64_t)0xFFFFFFFFu));
+    ms = max(ms, (uint32_t)min(slots, (uint64_t)0xFFFFFFFFu));
   }
   atomicMax(out_max, mx);
   atomicMax(out_max + 1, mc);
+  atomicMax(out_max + 2, ms);
 }
 
 inline int grid_for(uint64_t n, int threads = 256, int cap = 1 << 16) {
@@ -447,14 +450,15 @@ static int build_impl(const ebr_index_desc *desc, ebr_index *ix, cudaStream_t st
       {
         WinPtrs wp;
         for (int g = 0; g < kGroups; g++) wp.p[g] = ix->win_ptr[g];
-        BCUDA(cudaMemsetAsync(flags.p, 0, 8, st));
+        BCUDA(cudaMemsetAsync(flags.p, 0, 12, st));
         k_win_bytes<<<grid_for(n_win), 256, 0, st>>>(wp, n_win, (unsigned int *)flags.p);
         BCUDA(cudaGetLastError());
-        uint32_t mm[2] = {0, 0};
-        BCUDA(cudaMemcpyAsync(mm, flags.p, 8, cudaMemcpyDeviceToHost, st));
+        uint32_t mm[3] = {0, 0, 0};
+        BCUDA(cudaMemcpyAsync(mm, flags.p, 12, cudaMemcpyDeviceToHost, st));
         BCUDA(cudaStreamSynchronize(st));
         ix->max_win_bytes = mm[0];
         ix->max_win_chunks = mm[1];
+        ix->max_win_slots = mm[2];
       }
       BCUDA(cudaEventRecord(e1, st));
       BCUDA(cudaEventSynchronize(e1));
@@ -508,6 +512,11 @@ extern "C" void ebr_index_free(ebr_index *ix) {
   Workspace &w = ix->ws;
   for (DevBuf *b : {&w.wide, &w.w_dense, &w.lens, &w.scan, &w.work, &w.cub_tmp, &w.cand,
                     &w.ctrl, &w.io_in, &w.io_out, &w.hist})
+    dev_free(*b);
+  BatchWs &bw = ix->bws;
+  for (DevBuf *b : {&bw.users_f32, &bw.users_bf16, &bw.user_vals, &bw.wT, &bw.filters,
+                    &bw.has_filter, &bw.kk, &bw.status, &bw.cand, &bw.cand_n, &bw.cand_thr,
+                    &bw.scratch, &bw.out})
     dev_free(*b);
   if (w.host_ctrl) cudaFreeHost(w.host_ctrl);
   for (auto *v : {&ix->prof_pending, &ix->prof_pool})

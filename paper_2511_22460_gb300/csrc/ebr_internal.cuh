@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "ebr.h"
+#include <cuda.h>
 
 namespace ebr {
 
@@ -84,6 +85,14 @@ struct Ctrl {
   unsigned int pad;
 };
 
+// Scratch of the batched (tensor-core) path.
+struct BatchWs {
+  DevBuf users_f32, users_bf16, user_vals, wT, filters, has_filter, kk, status;
+  DevBuf cand, cand_n, cand_thr, scratch, out;
+  bool tmap_ready = false;
+  alignas(64) unsigned char tmap_bytes[128];  // CUtensorMap of the BF16 table
+};
+
 }  // namespace ebr
 
 struct ebr_index {
@@ -109,17 +118,21 @@ struct ebr_index {
   uint32_t max_win_bytes = 0;   // largest 16-byte-widened window segment total
   uint32_t max_win_chunks = 0;  // most 32-unit work chunks in one window
   uint32_t max_keys_per_ad = 0; // most distinct keys any ad belongs to
+  uint32_t max_win_slots = 0;   // most value slots (real + padding) in one window
   ebr::DevBuf emb_f32;    // float [N][d]
   ebr::DevBuf emb_q;      // bf16 / e4m3 [N][d]
   ebr::DevBuf emb_scale;  // float [N] (FP8)
   float build_ms = 0.f;
   int num_sms = 0;
   ebr::Workspace ws;
+  ebr::BatchWs bws;
   // profiling (ebr_profile_enable)
   bool prof = false;
   std::vector<std::array<cudaEvent_t, 5>> prof_pending, prof_pool;
   ebr_profile prof_acc = {};
   uint64_t launches = 0, lib_launches = 0;  // counted on every call
+  uint64_t batched = 0;    // requests served by the batched scan
+  uint64_t fallbacks = 0;  // batched requests recomputed by the single-request scan
 };
 
 struct ebr_cross {
@@ -145,4 +158,15 @@ constexpr size_t kHistWords = 256 + 65536;  // candidate-score histogram (coarse
 // Launchers implemented in ebr_query.cu, used by the serving loop.
 int query_one(const ebr_index *ix, const ebr_cross *cross, const ebr_query &q, uint32_t *ids,
               float *scores, uint32_t kmax, cudaStream_t st);
+int ws_prepare_one(ebr_index *ix, uint32_t n_q, uint32_t kcap);
+int launch_quantize(const float *x, uint64_t n, ebr_dtype dt, void *out, cudaStream_t st);
+// Query expansion for a batch straight into user-minor layout wT[key][Bp].
+int expand_transposed(const ebr_cross *c, const uint32_t *users, uint32_t batch, uint32_t Bp,
+                      float *wT, uint32_t *flags, cudaStream_t st);
+// Batched tensor-core path; returns EBR_EINVAL (nothing launched) when the
+// batch does not qualify, so the caller can fall back to per-request scans.
+bool batch_qualifies(const ebr_index *ix, const ebr_cross *cross, const ebr_query *q,
+                     uint32_t batch);
+int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint32_t batch,
+                uint32_t *out_ids, float *out_scores, uint32_t kmax, int io, cudaStream_t st);
 }

@@ -682,7 +682,11 @@ static int launch_scan(const ebr_index *ix, const ScanArgs &a, cudaStream_t st) 
 }
 
 // ----------------------------------------------------------- workspace
+int ws_prepare_one(ebr_index *ix, uint32_t n_q, uint32_t kcap);
 static int ws_prepare(ebr_index *ix, uint32_t n_q, uint32_t kcap) {
+  return ws_prepare_one(ix, n_q, kcap);
+}
+int ws_prepare_one(ebr_index *ix, uint32_t n_q, uint32_t kcap) {
   Workspace &w = ix->ws;
   EBR_TRY(dev_reserve(w.wide, (size_t)ix->n_ads * 4));
   EBR_TRY(dev_reserve(w.w_dense, (size_t)ix->n_keys * 4));
@@ -730,6 +734,57 @@ static int run_wide(ebr_index *ix, const uint32_t *q_key, const float *q_w, uint
   EBR_CUDA_TRY(cudaGetLastError());
   k_wide_scatter<<<ix->num_sms * 8, kWideThreads, 0, st>>>(iv, (const WorkEntry *)w.work.p,
                                                            ctrl, (float *)w.wide.p);
+  EBR_CUDA_TRY(cudaGetLastError());
+  return EBR_OK;
+}
+
+// w_hat transposed: wT[key][b] for b < Bp (zero for padding users b >= batch).
+__global__ void k_expand_T(CrossView cv, const uint32_t *__restrict__ users, uint32_t batch,
+                           uint32_t Bp, float *__restrict__ wT, uint32_t *__restrict__ flags) {
+  extern __shared__ uint32_t s_off2[];
+  for (uint32_t j = threadIdx.x; j <= cv.f_a; j += blockDim.x) s_off2[j] = cv.key_off[j];
+  __syncthreads();
+  const uint64_t total = (uint64_t)cv.n_keys * Bp;
+  uint32_t bad = 0;
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t key = (uint32_t)(t / Bp), b = (uint32_t)(t % Bp);
+    float acc = 0.f;
+    if (b < batch) {
+      uint32_t lo = 0, hi = cv.f_a;
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_off2[mid] <= key) lo = mid; else hi = mid;
+      }
+      const uint32_t j = lo, v = key - s_off2[j];
+      for (uint32_t q = cv.pair_ptr[j]; q < cv.pair_ptr[j + 1]; q++) {
+        const uint32_t p = cv.pair_of[q];
+        const uint32_t i = cv.pair_user[p];
+        const uint32_t u = users[(uint64_t)b * cv.f_u + i];
+        if (u >= cv.vocab_u[i]) { bad |= DEVERR_BAD_USER; continue; }
+        float w;
+        if (cv.hashed) {
+          const uint64_t x = ((uint64_t)p << 40) | ((uint64_t)u << 20) | (uint64_t)v;
+          w = cv.table[splitmix64(x) & ((1ull << cv.hash_bits) - 1ull)];
+        } else {
+          const uint64_t off = ((uint64_t)cv.w_hi[p] << 32) | cv.w_lo[p];
+          w = cv.table[off + (uint64_t)u * cv.vocab_a[j] + v];
+        }
+        acc += w;
+      }
+    }
+    wT[t] = acc;
+  }
+  if (bad) atomicOr(flags, bad);
+}
+
+int expand_transposed(const ebr_cross *c, const uint32_t *users, uint32_t batch, uint32_t Bp,
+                      float *wT, uint32_t *flags, cudaStream_t st) {
+  CrossView cv = cross_view(c);
+  const uint64_t total = (uint64_t)cv.n_keys * Bp;
+  uint64_t blocks = (total + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  k_expand_T<<<(int)blocks, 256, (c->f_a + 1) * 4, st>>>(cv, users, batch, Bp, wT, flags);
   EBR_CUDA_TRY(cudaGetLastError());
   return EBR_OK;
 }
@@ -1091,6 +1146,11 @@ extern "C" int ebr_score_topk(const ebr_index *cix, const ebr_cross *cross, cons
     d_ids = (uint32_t *)w.io_out.p;
     d_scores = (float *)((char *)w.io_out.p + ids_bytes);
   }
+  if (batch > 1 && batch_qualifies(ix, cross, q, batch)) {
+    rc = query_batch(ix, cross, q, batch, out_ids, out_scores, kmax, io, st);
+    cudaSetDevice(prev);
+    return rc;
+  }
   uint32_t flags_acc = 0;
   for (uint32_t b = 0; b < batch && rc == EBR_OK; b++) {
     ebr_query dq = q[b];
@@ -1258,6 +1318,8 @@ extern "C" int ebr_profile_read(ebr_index *ix, ebr_profile *out) {
   *out = ix->prof_acc;
   out->launches = ix->launches;
   out->lib_launches = ix->lib_launches;
+  out->batched = ix->batched;
+  out->recomputed = ix->fallbacks;
   return EBR_OK;
 }
 

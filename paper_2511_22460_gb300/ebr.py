@@ -62,7 +62,7 @@ class QueryC(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("calls", u64), ("launches", u64), ("lib_launches", u64),
                 ("ms_expand", C.c_double), ("ms_wide", C.c_double), ("ms_scan", C.c_double),
-                ("ms_final", C.c_double)]
+                ("ms_final", C.c_double), ("batched", u64), ("recomputed", u64)]
 
 
 def _sig(name, res, args):

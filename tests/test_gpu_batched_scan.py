@@ -1,0 +1,115 @@
+"""GPU parity of the batched tensor-core scan (many users per pass over the
+inventory, BF16 deep term on tcgen05, FP32 rescoring) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+from gpu_util import bitmap_to_mask, check_topk, recall, ref_scores  # noqa: E402
+from paper_2511_22460_gb300 import ebr  # noqa: E402
+from paper_2511_22460_gb300.datagen import make_filters, make_workload  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _run(name, n, B, ks, seed, filt=None, io=ebr.IO_DEVICE, **kw):
+    w = make_workload(name, n_ads=n, seed=seed, batch=B, **kw)
+    pk, pa = w.postings(shuffle=True)
+    ix = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype="bf16")
+    cross = ebr.cross_from_workload(w)
+    kmax = max(ks)
+    host = io == ebr.IO_HOST
+    conv = (lambda a: np.ascontiguousarray(a)) if host else dev
+    qs = [ebr.Query(h_u=conv(w.h_u[b]), k=ks[b], user_vals=conv(w.users[b]),
+                    filter=None if filt is None or filt[b] is None else conv(filt[b]))
+          for b in range(B)]
+    if host:
+        ids = np.empty((B, kmax), np.uint32)
+        sc = np.empty((B, kmax), np.float32)
+    else:
+        ids = torch.empty((B, kmax), dtype=torch.int32, device=DEV)
+        sc = torch.empty((B, kmax), dtype=torch.float32, device=DEV)
+    before = ix.profile_read()
+    b0, r0 = before.batched, before.recomputed
+    ebr.score_topk(ix, cross, qs, ids, sc, io=io)
+    after = ix.profile_read()
+    if not host:
+        ids = ids.cpu().numpy().view(np.uint32)
+        sc = sc.cpu().numpy()
+    return w, (pk, pa), ids, sc, after.batched - b0, after.recomputed - r0
+
+
+def _check_all(w, post, ids, sc, ks, filt=None, users=None):
+    for b in (range(len(ks)) if users is None else users):
+        ref, tol = ref_scores(w, b, post)
+        mask = None
+        if filt is not None and filt[b] is not None:
+            mask = bitmap_to_mask(filt[b], w.n_ads)
+        assert recall(ids[b], ref, tol, ks[b], mask) == 1.0, "user %d" % b
+        check_topk(ids[b], sc[b], ref, tol, ks[b], mask)
+
+
+@pytest.mark.parametrize("name,n,B", [("serve_bf16_5m", 60_001, 64),
+                                      ("batch256_bf16_5m", 40_000, 40),
+                                      ("serve_bf16_5m", 20_000, 2)])
+def test_batched_topk_matches_oracle(name, n, B):
+    ks = [100] * B
+    w, post, ids, sc, nb, nr = _run(name, n, B, ks, seed=11)
+    assert nb == B, "the batched path did not run"
+    _check_all(w, post, ids, sc, ks, users=range(0, B, max(1, B // 8)))
+
+
+def test_batched_mixed_k_filters_and_host_io():
+    B, n = 33, 50_000
+    rng = np.random.default_rng(5)
+    ks = [int(x) for x in rng.choice([1, 100, 500, 1000], size=B)]
+    fl = make_filters(rng, n, B, (0.001, 1.0))
+    filt = [fl[b] if b % 3 else None for b in range(B)]
+    filt[1] = np.zeros_like(fl[1])  # a filter that admits no ad
+    w, post, ids, sc, nb, nr = _run("serve_bf16_5m", n, B, ks, seed=12, filt=filt, io=ebr.IO_HOST)
+    assert nb == B
+    users = [b for b in range(B) if b != 1][::3] + [2, 4]
+    _check_all(w, post, ids, sc, ks, filt, users)
+    assert np.all(ids[1] == 0xFFFFFFFF) and np.all(np.isneginf(sc[1]))
+
+
+def test_batched_equals_single_request_path():
+    """The same users through the batched scan and one at a time give the
+    same ids (FP32 rescoring makes both exact up to score ties)."""
+    B, n, k = 16, 30_000, 200
+    w, post, ids, sc, nb, _ = _run("serve_bf16_5m", n, B, [k] * B, seed=13)
+    assert nb == B
+    pk, pa = post
+    ix = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype="bf16")
+    cross = ebr.cross_from_workload(w)
+    for b in range(0, B, 5):
+        i1 = torch.empty((1, k), dtype=torch.int32, device=DEV)
+        s1 = torch.empty((1, k), dtype=torch.float32, device=DEV)
+        ebr.score_topk(ix, cross, [ebr.Query(h_u=dev(w.h_u[b]), k=k, user_vals=dev(w.users[b]))],
+                       i1, s1)
+        ref, tol = ref_scores(w, b, post)
+        a = set(ids[b].tolist())
+        c = set(i1.cpu().numpy().view(np.uint32)[0].tolist())
+        for x in a ^ c:  # any difference is a tie within tolerance at the K-th score
+            kth = np.sort(ref)[::-1][k - 1]
+            assert abs(ref[x] - kth) <= 2 * tol[x]
+
+
+def test_batched_tiny_inventory_and_k_above_n():
+    """Fewer ads than one window and K larger than the inventory."""
+    B, n = 4, 200
+    ks = [300, 50, 200, 1]
+    w, post, ids, sc, nb, _ = _run("serve_bf16_5m", n, B, ks, seed=14)
+    assert nb == B
+    for b in range(B):
+        ref, tol = ref_scores(w, b, post)
+        take = check_topk(ids[b], sc[b], ref, tol, ks[b])
+        assert take == min(ks[b], n)
