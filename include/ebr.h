@@ -110,6 +110,10 @@ typedef struct {
   float build_ms;               /* device time of the index build (Algorithm 1 only) */
   float window_view_ms;         /* device time of the window-major view (below) */
   uint64_t window_view_bytes;   /* its size: per-block keys + value bytes + window offsets */
+  uint32_t n_windows;           /* windows of 256 consecutive ads: ceil(n_ads / 256) */
+  uint32_t max_keys_per_ad;     /* most distinct keys of one ad */
+  uint32_t max_window_slots;    /* most value slots (real + padding) in one window */
+  uint32_t max_window_chunks;   /* most 32-slot work chunks in one window */
 } ebr_index_info;
 int ebr_index_get_info(const ebr_index *ix, ebr_index_info *out);
 

@@ -162,20 +162,26 @@ extern "C" int ebr_debug_gemm_bf16(const uint16_t *A, uint32_t n, const uint16_t
 // Batched scan: B users against every ad, one pass over the inventory
 // =====================================================================
 // Per window of 256 ads (one persistent CTA per SM, contiguous windows):
-//   producer warp   -- tensor TMA of the window's BF16 rows (two 128-row
-//                      M-tiles) into a stage ring; the users' BF16 vectors
-//                      are loaded once;
-//   MMA warp        -- tcgen05.mma: deep[256 ads x Bp users] in TMEM (Eq. 1);
+//   producer warp   -- tensor TMA of the window's BF16 ad rows into a stage
+//                      ring; the users' BF16 vectors are loaded once;
+//   MMA warp        -- tcgen05.mma with the users as the M side and the
+//                      window's ads as N = 256: deep[user][ad] (Eq. 1) lands
+//                      in TMEM with one user per TMEM lane;
 //   list warps (4)  -- walk the window's blocks in the window-major view of
-//                      the compressed list and build, per ad, the list of its
-//                      keys (the window's slice of L, transposed);
-//   epilogue (8)    -- warp w owns ads 32w .. 32w+31; for each group of 32
-//                      users: lanes = users sum w^T[key][user] over each ad's
-//                      keys (coalesced rows of the expanded weights), the
-//                      32x32 tile is transposed through shared memory, added
-//                      to the TMEM deep scores of the warp's rows, filtered,
-//                      and each user's candidates above its running threshold
-//                      go to this CTA's per-user buffer (top-m kept exactly).
+//                      the compressed list and lay out, per run of 32 ads, a
+//                      key table T[r][i] = r-th key of ad i (the window's
+//                      slice of L, transposed; short ads padded with a zero
+//                      row of w^T);
+//   epilogue (8)    -- thread = user (its TMEM lane), runs of 32 ads per
+//                      warp: wide[i] += w^T[T[r][i]][user] for every row r
+//                      (32 independent coalesced 128-byte loads per step,
+//                      accumulators in registers), added to the 32 deep
+//                      scores of one TMEM load, filtered, and each user's
+//                      candidates above its running threshold go to this
+//                      CTA's per-user buffer (top-m kept exactly).
+// Fewer than 128 users are replicated across the 128 TMEM lanes so that all
+// eight epilogue warps have work: with Bq users (32, 64 or 128) per replica,
+// warp w serves users 32(w%4) mod Bq .. +31 on a run of Bq ads.
 namespace ebr {
 
 constexpr int kBWin = 256;
@@ -184,6 +190,9 @@ constexpr int kEpiThreads = kEpiWarps * 32, kListThreads = kListWarps * 32;
 constexpr int kMmaWarp = kEpiWarps + kListWarps, kProdWarpB = kMmaWarp + 1;
 constexpr int kBatchThreads = (kProdWarpB + 1) * 32;  // 448
 constexpr int kMaxUsers = 256;
+// List buffer: run_off[8], run_rows[8], fill[256], then the run tables.
+constexpr uint32_t kListHdr = 8 + 8 + kBWin;
+constexpr uint32_t kMaxBatchKeysPerAd = 64;  // longest key list the batched tables hold
 
 struct CandEntry {
   unsigned long long key;  // approximate score | id
@@ -193,14 +202,16 @@ struct CandEntry {
 
 struct BatchArgs {
   CUtensorMap ta;  // ad rows, BF16 [N][d], box {64, 128}
-  CUtensorMap tu;  // users, BF16 [Bp][d], box {64, Bp}
+  CUtensorMap tu;  // users, BF16 [Bq][d], box {64, min(Bq, 128)}
   const uint32_t *wkey[kGroups];
   const uint8_t *wvals[kGroups];
   const uint32_t *win_ptr[kGroups];
-  const float *wT;             // [n_keys][Bp] expanded weights, user-minor
+  const uint16_t *ad_nkeys;    // [N] distinct keys of each ad
+  const float *wT;             // [n_keys + 1][Bq] expanded weights, user-minor; last row 0
   const uint64_t *filters;     // [B][words] (rows of users without a filter are unused)
   const uint32_t *has_filter;  // [B]
-  uint32_t n_ads, n_win, B, Bp, d, m, cap_u, list_cap, words;
+  uint32_t n_ads, n_win, B, Bq, d, m, cap_u, list_cap, words;
+  uint32_t zero_row;           // n_keys * Bq: offset of the zero row of wT
   uint32_t sa, lb, tb;         // A stages, list buffers, TMEM buffers
   CandEntry *cand;             // [grid][B][cap_u]
   uint32_t *cand_n;            // [grid][B]
@@ -219,31 +230,43 @@ struct BatchSmem {
 __device__ __forceinline__ uint32_t ushift(uint32_t g) { return g >= 2 ? g - 2 : 0; }
 
 // Walk the real slots of window w: f(ad_in_window, key).  `t`/`nt`: this
-// thread's index in the walking group.
+// thread's index in the walking group.  Eight units per thread are loaded
+// before any is used, so each thread keeps that many loads in flight.
 template <typename F>
 __device__ __forceinline__ void walk_window(const BatchArgs &a, uint32_t w, int t, int nt, F f) {
+  constexpr int kU = 8;
 #pragma unroll 1
   for (uint32_t g = 0; g < (uint32_t)kGroups; g++) {
     const uint32_t lo = __ldg(a.win_ptr[g] + w), hi = __ldg(a.win_ptr[g] + w + 1);
     const uint32_t us = ushift(g);
     const uint32_t units = (hi - lo) << us;
-    for (uint32_t u = t; u < units; u += nt) {
-      const uint32_t bk = lo + (u >> us), wi = u & ((1u << us) - 1u);
-      const uint32_t key = __ldg(a.wkey[g] + bk);
-      uint32_t word, ns;
-      if (g >= 2) {
-        word = __ldg(reinterpret_cast<const uint32_t *>(a.wvals[g]) + (((uint64_t)bk << us) + wi));
-        ns = 4;
-      } else if (g == 1) {
-        word = __ldg(reinterpret_cast<const unsigned short *>(a.wvals[1]) + bk);
-        ns = 2;
-      } else {
-        word = __ldg(a.wvals[0] + bk);
-        ns = 1;
+    const uint32_t ns = g >= 2 ? 4u : (g == 1 ? 2u : 1u);
+#pragma unroll 1
+    for (uint32_t u0 = t; u0 < units; u0 += kU * nt) {
+      uint32_t key[kU], word[kU], first[kU];
+#pragma unroll
+      for (int e = 0; e < kU; e++) {
+        const uint32_t u = u0 + e * nt;
+        const bool v = u < units;
+        const uint32_t bk = lo + (v ? (u >> us) : 0u), wi = u & ((1u << us) - 1u);
+        key[e] = v ? __ldg(a.wkey[g] + bk) : 0u;
+        if (!v)
+          word[e] = 0u;
+        else if (g >= 2)
+          word[e] = __ldg(reinterpret_cast<const uint32_t *>(a.wvals[g]) + (((uint64_t)bk << us) + wi));
+        else if (g == 1)
+          word[e] = __ldg(reinterpret_cast<const unsigned short *>(a.wvals[1]) + bk);
+        else
+          word[e] = __ldg(a.wvals[0] + bk);
+        first[e] = (v && wi == 0) ? 1u : 0u;
       }
-      for (uint32_t s = 0; s < ns; s++) {
-        const uint32_t l = (word >> (8 * s)) & 255u;
-        if ((s == 0 && wi == 0) || l != 0) f(l, key);
+#pragma unroll
+      for (int e = 0; e < kU; e++) {
+        if (u0 + e * nt >= units) break;
+        for (uint32_t s = 0; s < ns; s++) {
+          const uint32_t l = (word[e] >> (8 * s)) & 255u;
+          if ((s == 0 && first[e]) || l != 0) f(l, key[e]);
+        }
       }
     }
   }
@@ -299,6 +322,26 @@ __device__ uint64_t warp_radix_select(const CandEntry *buf, uint32_t n, uint32_t
   return prefix;
 }
 
+// Stable in-place compaction of buf[0..n) to the entries with key >= T;
+// returns how many were kept.
+__device__ uint32_t warp_compact(CandEntry *buf, uint32_t n, uint64_t T) {
+  const int lane = threadIdx.x & 31;
+  uint32_t kept = 0;
+  for (uint32_t b0 = 0; b0 < n; b0 += 32) {
+    const uint32_t i = b0 + lane;
+    CandEntry e;
+    e.key = 0;
+    if (i < n) e = buf[i];
+    const bool kp = i < n && e.key >= T;
+    const uint32_t bal = __ballot_sync(0xffffffffu, kp);
+    __syncwarp();
+    if (kp) buf[kept + __popc(bal & ((1u << lane) - 1u))] = e;
+    kept += __popc(bal);
+    __syncwarp();
+  }
+  return kept;
+}
+
 __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ BatchSmem sm;
@@ -306,19 +349,20 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t kb_n = a.d / 64;
-  const uint32_t a_stage = 2u * kb_n * 16384u;  // two 128-row M-tiles
-  uint8_t *su = smem;                             // kb_n x [Bp x 128 B]
-  uint8_t *sa = su + (size_t)kb_n * a.Bp * 128;   // sa stages
+  const uint32_t n_mt = a.Bq > 128 ? 2u : 1u;     // 128-user M-tiles
+  const uint32_t u_tile = kb_n * 16384u;           // one M-tile: kb_n x [128 rows x 128 B]
+  const uint32_t a_stage = kb_n * 32768u;          // kb_n x [256 ad rows x 128 B]
+  uint8_t *su = smem;                              // n_mt user tiles
+  uint8_t *sa = su + (size_t)n_mt * u_tile;        // sa ad stages
   uint32_t *lists = reinterpret_cast<uint32_t *>(sa + (size_t)a.sa * a_stage);
-  const uint32_t list_words = 2 * (kBWin + 1) + a.list_cap;  // off[257], fill[257], keys
-  float *wtile = reinterpret_cast<float *>(lists + (size_t)a.lb * list_words);  // [8][32][33]
+  const uint32_t list_words = kListHdr + a.list_cap;
+  uint32_t *whist = lists + (size_t)a.lb * list_words;  // [8][256] radix histograms
 
   const uint32_t w_begin = (uint32_t)(((uint64_t)a.n_win * blockIdx.x) / gridDim.x);
   const uint32_t w_end = (uint32_t)(((uint64_t)a.n_win * (blockIdx.x + 1)) / gridDim.x);
   const uint32_t my_wins = w_end - w_begin;
-  const uint32_t tcols = 2u * a.Bp;  // TMEM columns per window (two M-tiles)
-  uint32_t ncols = 32;
-  while (ncols < tcols * a.tb) ncols <<= 1;
+  const uint32_t tcols = 256u * n_mt;  // TMEM columns per window
+  const uint32_t ncols = 512;
 
   for (uint32_t b = tid; b < a.B; b += kBatchThreads) {
     sm.cnt_u[b] = 0;
@@ -352,9 +396,15 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
   if (warp == kProdWarpB) {
     // ---------------------------------------------------------- producer
     if (lane == 0) {
-      mbar_arrive_expect_tx(&sm.u_full, kb_n * a.Bp * 128u);
-      for (uint32_t kb = 0; kb < kb_n; kb++)
-        tma_load_2d(su + (size_t)kb * a.Bp * 128, &a.tu, (int)(kb * 64), 0, &sm.u_full);
+      const uint64_t pol = l2_evict_first_policy();
+      // users: M-tile rows r hold user r mod Bq (replicas when Bq < 128)
+      const uint32_t box_u = a.Bq < 128 ? a.Bq : 128u;
+      mbar_arrive_expect_tx(&sm.u_full, n_mt * u_tile);
+      for (uint32_t mt = 0; mt < n_mt; mt++)
+        for (uint32_t r0 = 0; r0 < 128; r0 += box_u)
+          for (uint32_t kb = 0; kb < kb_n; kb++)
+            tma_load_2d(su + mt * u_tile + kb * 16384u + r0 * 128u, &a.tu, (int)(kb * 64),
+                        (int)(n_mt > 1 ? mt * 128 : 0), &sm.u_full);
       for (uint32_t j = 0; j < my_wins; j++) {
         const uint32_t s = j % a.sa;
         if (j >= a.sa && !mbar_wait_bounded(&sm.a_empty[s], ((j / a.sa) - 1) & 1u, kWaitTimeoutNs)) {
@@ -366,10 +416,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
         const int row0 = (int)((w_begin + j) * kBWin);
         uint8_t *dst = sa + (size_t)s * a_stage;
         mbar_arrive_expect_tx(&sm.a_full[s], a_stage);
-        for (uint32_t mt = 0; mt < 2; mt++)
-          for (uint32_t kb = 0; kb < kb_n; kb++)
-            tma_load_2d(dst + (mt * kb_n + kb) * 16384, &a.ta, (int)(kb * 64), row0 + (int)mt * 128,
-                        &sm.a_full[s]);
+        for (uint32_t kb = 0; kb < kb_n; kb++)
+          for (uint32_t h = 0; h < 2; h++)
+            tma_load_2d_hint(dst + kb * 32768u + h * 16384u, &a.ta, (int)(kb * 64),
+                             row0 + (int)h * 128, &sm.a_full[s], pol);
         sm.n_issued = j + 1;
       }
     }
@@ -377,7 +427,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
     // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
       bool ok = mbar_wait_bounded(&sm.u_full, 0, kWaitTimeoutNs);
-      const uint32_t idesc = idesc_bf16_f32(128, a.Bp);
+      const uint32_t idesc = idesc_bf16_f32(128, 256);
       for (uint32_t j = 0; ok && j < my_wins; j++) {
         const uint32_t s = j % a.sa, tb = j % a.tb;
         ok = mbar_wait_bounded(&sm.a_full[s], (j / a.sa) & 1u, kWaitTimeoutNs);
@@ -385,13 +435,13 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
         if (!ok || *((volatile uint32_t *)&sm.abort)) break;
         tc_fence_after();
         const uint8_t *as = sa + (size_t)s * a_stage;
-        for (uint32_t mt = 0; mt < 2; mt++) {
-          const uint32_t dcol = tmem + tb * tcols + mt * a.Bp;
+        for (uint32_t mt = 0; mt < n_mt; mt++) {
+          const uint32_t dcol = tmem + tb * tcols + mt * 256u;
           for (uint32_t k = 0; k < a.d / 16; k++) {
             const uint32_t kb = k / 4, kk = k % 4;
-            const uint64_t ad = sdesc_k_sw128(smem_u32(as + (mt * kb_n + kb) * 16384 + kk * 32));
-            const uint64_t bd = sdesc_k_sw128(smem_u32(su + (size_t)kb * a.Bp * 128 + kk * 32));
-            umma_bf16(dcol, ad, bd, idesc, k > 0 ? 1u : 0u);
+            const uint64_t ud = sdesc_k_sw128(smem_u32(su + mt * u_tile + kb * 16384u + kk * 32));
+            const uint64_t ad = sdesc_k_sw128(smem_u32(as + kb * 32768u + kk * 32));
+            umma_bf16(dcol, ud, ad, idesc, k > 0 ? 1u : 0u);
           }
         }
         umma_commit(&sm.a_empty[s]);
@@ -405,6 +455,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
     }
   } else if (warp >= kEpiWarps) {
     // ---------------------------------------------------------- list builders
+    // Per window: off[l] = first slot of ad l (exclusive scan of the ads' key
+    // counts), then one walk of the window's blocks drops each key into its
+    // ad's slot range.
     const int lt = tid - kEpiThreads;
     for (uint32_t j = 0; j < my_wins; j++) {
       const uint32_t lbuf = j % a.lb;
@@ -421,49 +474,75 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
       named_sync(2, kListThreads);
       if (sm.stop_list) break;
       if (j >= a.lb) mbar_try_wait(&sm.l_empty[lbuf], ((j / a.lb) - 1) & 1u);
-      uint32_t *off = lists + (size_t)lbuf * list_words;
-      uint32_t *fill = off + (kBWin + 1);
-      uint32_t *keys = fill + (kBWin + 1);
-      for (int i = lt; i < 2 * (kBWin + 1); i += kListThreads) off[i] = 0;
-      named_sync(2, kListThreads);
+      uint32_t *run_off = lists + (size_t)lbuf * list_words;
+      uint32_t *run_rows = run_off + 8;
+      uint32_t *fill = run_off + 16;
+      uint32_t *tab = run_off + kListHdr;
       const uint32_t w = w_begin + j;
-      walk_window(a, w, lt, kListThreads, [&](uint32_t l, uint32_t) { atomicAdd(&fill[l], 1u); });
-      named_sync(2, kListThreads);
-      if (lt < 32) {  // exclusive scan of 256 counts -> off[0..256]
-        uint32_t c[8], tot = 0;
+      // rows of each run = most keys of its 32 ads; thread lt owns ads lt, lt + 128
+      uint32_t nk[2];
 #pragma unroll
-        for (int e = 0; e < 8; e++) {
-          c[e] = fill[8 * lt + e];
-          tot += c[e];
-        }
-        uint32_t incl = tot;
+      for (int h = 0; h < 2; h++) {
+        const uint32_t ad = w * kBWin + lt + 128 * h;
+        nk[h] = ad < a.n_ads ? (uint32_t)__ldg(a.ad_nkeys + ad) : 0u;
+        fill[lt + 128 * h] = 0;
+        uint32_t mx = nk[h];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lt >= o) incl += v;
-        }
-        uint32_t run = incl - tot;
-#pragma unroll
-        for (int e = 0; e < 8; e++) {
-          off[8 * lt + e] = run;
-          fill[8 * lt + e] = 0;
-          run += c[e];
-        }
-        if (lt == 31) off[kBWin] = run;
+        for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) run_rows[warp - kEpiWarps + 4 * h] = mx;
       }
       named_sync(2, kListThreads);
+      uint32_t ro[2], rr[2];
+      {
+        uint32_t acc = 0;
+        const uint32_t r0 = (lt >> 5), r1 = r0 + 4;
+        for (uint32_t r = 0; r < 8; r++) {
+          const uint32_t rows = run_rows[r];
+          if (r == r0) { ro[0] = acc; rr[0] = rows; }
+          if (r == r1) { ro[1] = acc; rr[1] = rows; }
+          if (lt == 0) run_off[r] = acc;
+          acc += rows * 32u;
+        }
+      }
+      // padding entries (rows nk .. rows-1) point at the zero row
+#pragma unroll
+      for (int h = 0; h < 2; h++)
+        for (uint32_t r = nk[h]; r < rr[h]; r++) {
+          const uint32_t pos = ro[h] + r * 32u + (uint32_t)lane;
+          if (pos < a.list_cap) tab[pos] = a.zero_row;
+        }
+      named_sync(2, kListThreads);
       walk_window(a, w, lt, kListThreads, [&](uint32_t l, uint32_t key) {
-        const uint32_t pos = off[l] + atomicAdd(&fill[l], 1u);
-        if (pos < a.list_cap) keys[pos] = key;
+        const uint32_t rank = atomicAdd(&fill[l], 1u);
+        const uint32_t pos = run_off[l >> 5] + rank * 32u + (l & 31u);
+        if (rank < run_rows[l >> 5] && pos < a.list_cap) tab[pos] = key * a.Bq;
       });
       mbar_arrive(&sm.l_full[lbuf]);  // release: this thread's list writes
     }
   } else {
     // ---------------------------------------------------------- epilogue
     const GroupSync gsync{1, kEpiThreads};
-    float *wt = wtile + (size_t)warp * 32 * 33;
-    const uint32_t lane_base = (uint32_t)(32 * (warp % 4)) << 16;
-    const uint32_t mt = warp / 4;
+    const uint32_t q = warp % 4;                  // TMEM lane quadrant of this warp
+    uint32_t *hist = whist + warp * 256;
+    uint32_t mt, user, ad_lo, n_ads_w;
+    if (n_mt > 1) {  // 256 users: warp w serves M-tile w/4, all 256 ads
+      mt = warp / 4;
+      user = mt * 128 + 32 * q + lane;
+      ad_lo = 0;
+      n_ads_w = 256;
+    } else {  // Bq users replicated 128/Bq times; warps split the window's ads
+      const uint32_t rep = 128 / a.Bq;
+      mt = 0;
+      user = (32 * q) % a.Bq + lane;
+      ad_lo = ((warp / 4) * rep + (32 * q) / a.Bq) * a.Bq;
+      n_ads_w = a.Bq;
+    }
+    const uint32_t tl = tmem + ((32u * q) << 16) + mt * 256u;
+    const bool user_ok = user < a.B;
+    const bool filt = user_ok && a.has_filter[user];
+    const uint64_t *frow = a.filters + (uint64_t)(user_ok ? user : 0u) * a.words;
+    const float *wcol = a.wT + user;
+    CandEntry *ubuf = a.cand + ((uint64_t)blockIdx.x * a.B + (user_ok ? user : 0u)) * a.cap_u;
     for (uint32_t j = 0; j < my_wins; j++) {
       const uint32_t tb = j % a.tb, lbuf = j % a.lb;
       if (tid == 0) {
@@ -481,49 +560,53 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
       mbar_try_wait(&sm.t_full[tb], (j / a.tb) & 1u);
       mbar_try_wait(&sm.l_full[lbuf], (j / a.lb) & 1u);
       tc_fence_after();
-      const uint32_t *off = lists + (size_t)lbuf * list_words;
-      const uint32_t *keys = off + 2 * (kBWin + 1);
-      const uint32_t w = w_begin + j;
-      const uint32_t my_ad_w = 32 * warp + lane;  // this lane's ad within the window
-      const uint32_t ad = w * kBWin + my_ad_w;
-      const bool valid = ad < a.n_ads;
-      for (uint32_t b0 = 0; b0 < a.Bp; b0 += 32) {
-        // wide terms of the warp's 32 ads for users b0 .. b0+31 (lane = user)
-        for (int i = 0; i < 32; i++) {
-          const uint32_t l = 32 * warp + i;
-          const uint32_t k0 = off[l], k1 = min(off[l + 1], a.list_cap);
-          float acc = 0.f;
-          for (uint32_t q = k0; q < k1; q++)
-            acc += __ldg(a.wT + (uint64_t)keys[q] * a.Bp + b0 + lane);
-          wt[i * 33 + lane] = acc;
-        }
-        __syncwarp();
-        uint32_t r[32];
-        tmem_ld32(tmem + lane_base + tb * tcols + mt * a.Bp + b0, r);
-        tmem_ld_wait();
+      const uint32_t *run_off = lists + (size_t)lbuf * list_words;
+      const uint32_t *tab = run_off + kListHdr;
+      const uint32_t wbase = (w_begin + j) * kBWin;
+      const unsigned long long thr0 = user_ok ? sm.thr_u[user] : ~0ull;
+      for (uint32_t c = 0; c < n_ads_w; c += 32) {
+        const uint32_t a0 = ad_lo + c;  // first window-local ad of this run
+        const uint32_t run = a0 >> 5;
+        const uint32_t rows = run_off[8 + run];
+        const uint4 *t4 = reinterpret_cast<const uint4 *>(tab + run_off[run]);
+        float acc[32];
 #pragma unroll
-        for (int jj = 0; jj < 32; jj++) {
-          const uint32_t b = b0 + jj;
-          if (b >= a.B || !valid) continue;
-          const float wide = wt[lane * 33 + jj];
-          const float score = __uint_as_float(r[jj]) + wide;
-          if (a.has_filter[b] &&
-              !((a.filters[(uint64_t)b * a.words + (ad >> 6)] >> (ad & 63)) & 1ull))
-            continue;
-          const unsigned long long key = make_key(score, ad);
-          if (key < sm.thr_u[b]) continue;
-          const uint32_t pos = atomicAdd(&sm.cnt_u[b], 1u);
-          if (pos < a.cap_u) {
-            CandEntry e;
-            e.key = key;
-            e.wide = wide;
-            e.pad = 0;
-            a.cand[((uint64_t)blockIdx.x * a.B + b) * a.cap_u + pos] = e;
-          } else {
-            atomicOr(&a.ctrl->flags, DEVERR_OVERFLOW);
+        for (int i = 0; i < 32; i++) acc[i] = 0.f;
+        for (uint32_t r = 0; r < rows; r++) {
+#pragma unroll
+          for (int i4 = 0; i4 < 8; i4++) {
+            const uint4 k = t4[r * 8 + i4];
+            acc[4 * i4 + 0] += __ldg(wcol + k.x);
+            acc[4 * i4 + 1] += __ldg(wcol + k.y);
+            acc[4 * i4 + 2] += __ldg(wcol + k.z);
+            acc[4 * i4 + 3] += __ldg(wcol + k.w);
           }
         }
-        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          uint32_t dv[16];  // deep scores of 16 ads, one TMEM load
+          tmem_ld16(tl + tb * tcols + a0 + 16 * h, dv);
+          tmem_ld_wait();
+#pragma unroll
+          for (int ii = 0; ii < 16; ii++) {
+            const int i = 16 * h + ii;
+            const uint32_t ad = wbase + a0 + i;
+            if (!user_ok || ad >= a.n_ads) continue;
+            const unsigned long long key = make_key(__uint_as_float(dv[ii]) + acc[i], ad);
+            if (key < thr0) continue;
+            if (filt && !((__ldg(frow + (ad >> 6)) >> (ad & 63)) & 1ull)) continue;
+            const uint32_t pos = atomicAdd(&sm.cnt_u[user], 1u);
+            if (pos < a.cap_u) {
+              CandEntry ce;
+              ce.key = key;
+              ce.wide = acc[i];
+              ce.pad = 0;
+              ubuf[pos] = ce;
+            } else {
+              atomicOr(&a.ctrl->flags, DEVERR_OVERFLOW);
+            }
+          }
+        }
       }
       tc_fence_before();
       gsync();
@@ -537,20 +620,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
         if (n + kBWin <= a.cap_u) continue;
         CandEntry *buf = a.cand + ((uint64_t)blockIdx.x * a.B + b) * a.cap_u;
         const uint32_t nn = min(n, a.cap_u);
-        const uint64_t T = warp_radix_select(buf, nn, a.m, reinterpret_cast<uint32_t *>(wt));
-        uint32_t kept = 0;
-        for (uint32_t b0 = 0; b0 < nn; b0 += 32) {
-          const uint32_t i = b0 + lane;
-          CandEntry e;
-          e.key = 0;
-          if (i < nn) e = buf[i];
-          const bool kp = i < nn && e.key >= T;
-          const uint32_t bal = __ballot_sync(0xffffffffu, kp);
-          __syncwarp();
-          if (kp) buf[kept + __popc(bal & ((1u << lane) - 1u))] = e;
-          kept += __popc(bal);
-          __syncwarp();
-        }
+        const uint64_t T = warp_radix_select(buf, nn, a.m, hist);
+        const uint32_t kept = warp_compact(buf, nn, T);
         if (lane == 0) {
           sm.cnt_u[b] = kept;
           sm.thr_u[b] = T;
@@ -566,20 +637,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
         const uint32_t n = min(sm.cnt_u[b], a.cap_u);
         if (n <= a.m) continue;
         CandEntry *buf = a.cand + ((uint64_t)blockIdx.x * a.B + b) * a.cap_u;
-        const uint64_t T = warp_radix_select(buf, n, a.m, reinterpret_cast<uint32_t *>(wt));
-        uint32_t kept = 0;
-        for (uint32_t b0 = 0; b0 < n; b0 += 32) {
-          const uint32_t i = b0 + lane;
-          CandEntry e;
-          e.key = 0;
-          if (i < n) e = buf[i];
-          const bool kp = i < n && e.key >= T;
-          const uint32_t bal = __ballot_sync(0xffffffffu, kp);
-          __syncwarp();
-          if (kp) buf[kept + __popc(bal & ((1u << lane) - 1u))] = e;
-          kept += __popc(bal);
-          __syncwarp();
-        }
+        const uint64_t T = warp_radix_select(buf, n, a.m, hist);
+        const uint32_t kept = warp_compact(buf, n, T);
         if (lane == 0) {
           sm.cnt_u[b] = kept;
           sm.thr_u[b] = T > sm.thr_u[b] ? T : sm.thr_u[b];
@@ -759,27 +818,35 @@ __global__ void __launch_bounds__(kMergeThreads) k_batch_merge(
 namespace ebr {
 
 struct BatchPlan {
-  uint32_t Bp, m, cap_u, sa, lb, tb, list_cap;
+  uint32_t Bq, m, cap_u, sa, lb, tb, list_cap;
   size_t smem;
 };
 
-// Shared-memory layout of k_batch_window for B users: the users' tile, `sa`
-// ad stages, `lb` per-ad key lists and the epilogue transpose tiles.
-// Preference: two list buffers (list building overlaps the epilogue, the
-// slowest role), then two ad stages.
+// Users per TMEM replica: the batch rounded up to 32, 64, 128 or 256.
+static uint32_t users_pow2(uint32_t B) {
+  uint32_t q = 32;
+  while (q < B) q <<= 1;
+  return q;
+}
+
+// Shared-memory layout of k_batch_window: the users' M-tiles, `sa` ad
+// stages, `lb` per-ad key lists and the epilogue's per-warp score tiles.
+// Preference: two list buffers (list building then overlaps the epilogue),
+// then two ad stages.
 static bool plan_smem(const ebr_index *ix, uint32_t B, BatchPlan *p) {
-  p->Bp = (B + 31) / 32 * 32;
-  p->list_cap = ix->max_win_slots;
-  p->tb = (4 * p->Bp <= 512) ? 2 : 1;
+  p->Bq = users_pow2(B);
+  p->list_cap = kBWin * ix->max_keys_per_ad;  // 8 runs x 32 ads x rows
+  const uint32_t n_mt = p->Bq > 128 ? 2 : 1;
+  p->tb = n_mt == 1 ? 2 : 1;
   const uint32_t kb_n = ix->d / 64;
-  const size_t u_bytes = (size_t)kb_n * p->Bp * 128;
-  const size_t a_stage = 2ull * kb_n * 16384;
-  const size_t list_bytes = (2ull * (kBWin + 1) + p->list_cap) * 4;
-  const size_t wtile = (size_t)kEpiWarps * 32 * 33 * 4;
+  const size_t u_bytes = (size_t)n_mt * kb_n * 16384;
+  const size_t a_stage = (size_t)kb_n * 32768;
+  const size_t list_bytes = ((size_t)kListHdr + p->list_cap) * 4;
+  const size_t hist = (size_t)kEpiWarps * 256 * 4;
   const size_t budget = 220 * 1024;
   const uint32_t order[4][2] = {{2, 2}, {1, 2}, {2, 1}, {1, 1}};  // {sa, lb}
   for (const auto &o : order) {
-    const size_t need = 1024 + u_bytes + o[0] * a_stage + o[1] * list_bytes + wtile;
+    const size_t need = 1024 + u_bytes + o[0] * a_stage + o[1] * list_bytes + hist;
     if (need <= budget) {
       p->sa = o[0];
       p->lb = o[1];
@@ -794,7 +861,9 @@ bool batch_qualifies(const ebr_index *ix, const ebr_cross *cross, const ebr_quer
                      uint32_t batch) {
   if (ix->dtype != EBR_BF16 || (ix->d != 64 && ix->d != 128) || batch < 2 ||
       batch > (uint32_t)kMaxUsers || !cross || cross->n_keys != ix->n_keys ||
-      ix->max_win_slots == 0 || ix->n_win == 0)
+      ix->n_win == 0 || !ix->ad_nkeys.p || ix->max_keys_per_ad == 0 ||
+      ix->max_keys_per_ad > kMaxBatchKeysPerAd ||
+      (uint64_t)(ix->n_keys + 1) * users_pow2(batch) >= (1ull << 32))
     return false;
   for (uint32_t b = 0; b < batch; b++) {
     if (!q[b].user_vals || (q[b].flags & EBR_QF_KEY_MAJOR)) return false;
@@ -836,14 +905,15 @@ int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint3
   const int grid = std::max(1, std::min<int>(ix->num_sms, (int)ix->n_win));
   BatchPlan pl;
   if (!plan_batch(ix, B, kscan_max, grid, &pl)) {
-    set_error("batched scan: window lists of %u slots do not fit shared memory", ix->max_win_slots);
+    set_error("batched scan: per-window key tables (%u keys per ad) do not fit shared memory",
+              ix->max_keys_per_ad);
     return EBR_EINVAL;
   }
-  const uint32_t Bp = pl.Bp;
+  const uint32_t Bp = pl.Bq;
   EBR_TRY(dev_reserve(w.users_f32, (size_t)Bp * d * 4));
   EBR_TRY(dev_reserve(w.users_bf16, (size_t)Bp * d * 2));
   EBR_TRY(dev_reserve(w.user_vals, (size_t)B * fu * 4));
-  EBR_TRY(dev_reserve(w.wT, (size_t)ix->n_keys * Bp * 4));
+  EBR_TRY(dev_reserve(w.wT, ((size_t)ix->n_keys + 1) * Bp * 4));
   EBR_TRY(dev_reserve(w.filters, (size_t)B * words * 8));
   EBR_TRY(dev_reserve(w.has_filter, (size_t)B * 4));
   EBR_TRY(dev_reserve(w.kk, (size_t)2 * B * 4));
@@ -874,6 +944,7 @@ int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint3
                           st));
   EBR_TRY(expand_transposed(cross, (const uint32_t *)w.user_vals.p, B, Bp, (float *)w.wT.p,
                             &ctrl->flags, st));
+  EBR_CUDA_TRY(cudaMemsetAsync((float *)w.wT.p + (size_t)ix->n_keys * Bp, 0, (size_t)Bp * 4, st));
   ix->launches += 2;
   // tensor maps
   if (!w.tmap_ready) {
@@ -884,23 +955,25 @@ int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint3
   BatchArgs a;
   memset(&a, 0, sizeof(a));
   memcpy(&a.ta, w.tmap_bytes, sizeof(CUtensorMap));
-  EBR_TRY(make_tmap_bf16(&a.tu, w.users_bf16.p, Bp, d, Bp));
+  EBR_TRY(make_tmap_bf16(&a.tu, w.users_bf16.p, Bp, d, std::min<uint32_t>(Bp, 128)));
   for (int g = 0; g < kGroups; g++) {
     a.wkey[g] = ix->wkey[g];
     a.wvals[g] = ix->wvals[g];
     a.win_ptr[g] = ix->win_ptr[g];
   }
+  a.ad_nkeys = (const uint16_t *)ix->ad_nkeys.p;
   a.wT = (const float *)w.wT.p;
   a.filters = (const uint64_t *)w.filters.p;
   a.has_filter = (const uint32_t *)w.has_filter.p;
   a.n_ads = ix->n_ads;
   a.n_win = ix->n_win;
   a.B = B;
-  a.Bp = Bp;
+  a.Bq = Bp;
   a.d = d;
   a.m = pl.m;
   a.cap_u = pl.cap_u;
   a.list_cap = pl.list_cap;
+  a.zero_row = ix->n_keys * Bp;
   a.words = words;
   a.sa = pl.sa;
   a.lb = pl.lb;

@@ -46,6 +46,10 @@ __global__ void k_keys_per_ad(const uint64_t *__restrict__ x, uint32_t m, uint32
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
     atomicAdd(&cnt[(uint32_t)x[i]], 1u);
 }
+__global__ void k_u32_to_u16(const uint32_t *__restrict__ v, uint32_t n, uint16_t *__restrict__ out) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = (uint16_t)v[i];
+}
 __global__ void k_max_u32(const uint32_t *__restrict__ v, uint32_t n, unsigned int *__restrict__ out) {
   uint32_t mx = 0;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -323,6 +327,13 @@ static int build_impl(const ebr_index_desc *desc, ebr_index *ix, cudaStream_t st
                                                 (unsigned int *)flags.p);
       BCUDA(cudaMemcpyAsync(&ix->max_keys_per_ad, flags.p, 4, cudaMemcpyDeviceToHost, st));
       BCUDA(cudaStreamSynchronize(st));
+      if (ix->max_keys_per_ad <= 65535) {  // per-ad slot counts of the batched scan
+        BTRY(dev_alloc(ix->ad_nkeys, (size_t)n_ads * 2));
+        k_u32_to_u16<<<grid_for(n_ads), 256, 0, st>>>((const uint32_t *)bs.p, n_ads,
+                                                      (uint16_t *)ix->ad_nkeys.p);
+        BCUDA(cudaGetLastError());
+        BCUDA(cudaStreamSynchronize(st));
+      }
       dev_free(bs);
       BTRY(dev_alloc(bs, (size_t)m * 4));
       BTRY(dev_alloc(bid, (size_t)m * 4));
@@ -506,6 +517,7 @@ extern "C" void ebr_index_free(ebr_index *ix) {
   dev_free(ix->mem_wkey);
   dev_free(ix->mem_wvals);
   dev_free(ix->mem_winptr);
+  dev_free(ix->ad_nkeys);
   dev_free(ix->emb_f32);
   dev_free(ix->emb_q);
   dev_free(ix->emb_scale);
@@ -593,6 +605,10 @@ extern "C" int ebr_index_get_info(const ebr_index *ix, ebr_index_info *out) {
   out->build_ms = ix->build_ms;
   out->window_view_ms = ix->wm_build_ms;
   out->window_view_bytes = bytes - 4ull * kGroups * (ix->n_keys + 1) + 4ull * kGroups * (ix->n_win + 1);
+  out->n_windows = ix->n_win;
+  out->max_keys_per_ad = ix->max_keys_per_ad;
+  out->max_window_slots = ix->max_win_slots;
+  out->max_window_chunks = ix->max_win_chunks;
   return EBR_OK;
 }
 

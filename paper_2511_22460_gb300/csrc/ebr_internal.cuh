@@ -119,6 +119,7 @@ struct ebr_index {
   uint32_t max_win_chunks = 0;  // most 32-unit work chunks in one window
   uint32_t max_keys_per_ad = 0; // most distinct keys any ad belongs to
   uint32_t max_win_slots = 0;   // most value slots (real + padding) in one window
+  ebr::DevBuf ad_nkeys;         // uint16 [N]: distinct keys of each ad (empty if any > 65535)
   ebr::DevBuf emb_f32;    // float [N][d]
   ebr::DevBuf emb_q;      // bf16 / e4m3 [N][d]
   ebr::DevBuf emb_scale;  // float [N] (FP8)

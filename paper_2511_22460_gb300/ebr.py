@@ -44,7 +44,9 @@ class IndexInfo(C.Structure):
     _fields_ = [("n_ads", u32), ("n_keys", u32), ("d", u32), ("emb_dtype", i32),
                 ("rescore_mult", u32), ("nnz_unique", u64), ("n_blocks", u64 * 9),
                 ("index_bytes", u64), ("emb_bytes", u64), ("build_ms", C.c_float),
-                ("window_view_ms", C.c_float), ("window_view_bytes", u64)]
+                ("window_view_ms", C.c_float), ("window_view_bytes", u64),
+                ("n_windows", u32), ("max_keys_per_ad", u32), ("max_window_slots", u32),
+                ("max_window_chunks", u32)]
 
 
 class CrossDesc(C.Structure):
