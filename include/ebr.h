@@ -304,6 +304,65 @@ typedef struct {
 int ebr_profile_enable(ebr_index *ix, int on);
 int ebr_profile_read(ebr_index *ix, ebr_profile *out);
 
+/* ------------------------------------------------------------------ serving
+ * Continuous-batching request loop over one index (the serving form of the
+ * method's query, Algorithm 2 plus the dual-tower term of Eq. 1, for many
+ * concurrent users; the paper itself gives no serving design).
+ *
+ * ebr_submit copies a host request into a device-resident slot (the copy
+ * runs on the server's copy stream) and queues it; a worker thread launches
+ * whatever is queued, up to max_batch users, as one batched scan as soon as
+ * one of its two pipelines is free, so a batch is being staged and launched
+ * while the previous one is still on the GPU.  ebr_poll returns the result
+ * once it is visible on the host.
+ *
+ * Admission is by device memory: every slot holds a request's inputs (user
+ * vector, user field values, targeting bitmap) in HBM, and the slots plus the
+ * two pipelines' workspaces must fit `hbm_budget`.  A submit with no free
+ * slot is refused with EBR_ENOMEM (the caller retries after polling).
+ *
+ * The index must not be used by other calls while a server runs on it.
+ */
+typedef struct ebr_server ebr_server;
+typedef struct {
+  uint64_t hbm_budget;        /* device bytes for slots + workspaces (0: half of the free memory) */
+  uint32_t max_batch;         /* users per batched scan, 1..256 (0: 64) */
+  uint32_t max_slots;         /* admitted requests at once, queued + running (0: 4 * max_batch) */
+  uint32_t k_max;             /* largest K a request may ask for (0: 1000) */
+  uint32_t queue_timeout_ms;  /* a request still queued after this long fails with EBR_ETIMEDOUT (0: never) */
+} ebr_server_cfg;
+
+typedef struct {
+  uint64_t submitted, admitted, rejected, completed, failed, batches, batched_requests;
+  double p50_ms, p99_ms, mean_ms;   /* submit -> result visible, over up to the last 65536 requests */
+  uint32_t max_batch, max_slots;    /* effective values after the HBM budget */
+  uint64_t device_bytes;            /* device memory held by slots and workspaces */
+  uint64_t slot_bytes;              /* device bytes of one request slot */
+} ebr_server_stats;
+
+/*
+ * cross: the cross model whose user field values the requests carry
+ * (required: requests are given as raw user fields, expanded on the device).
+ * Returns EBR_ENOMEM if not even one batch of one request fits the budget.
+ */
+int ebr_server_create(ebr_index *ix, const ebr_cross *cross, const ebr_server_cfg *cfg,
+                      ebr_server **out);
+/*
+ * q: HOST pointers (h_u[d], user_vals[f_u], optional filter bitmap of
+ * ceil(N/64) words); q->k in 1..k_max; q_key/q_w are not accepted here.
+ * The request is copied before the call returns.  *ticket identifies it.
+ */
+int ebr_submit(ebr_server *s, const ebr_query *q, uint64_t *ticket);
+/*
+ * EBR_EAGAIN while pending; EBR_OK with ids[k], scores[k] (host) filled and
+ * the ticket retired; the request's error code (ticket retired) if it
+ * failed; EBR_EINVAL for an unknown or already retired ticket.
+ */
+int ebr_poll(ebr_server *s, uint64_t ticket, uint32_t *ids, float *scores);
+int ebr_server_get_stats(ebr_server *s, ebr_server_stats *out);
+/* Stops the worker (requests still pending are dropped) and frees everything. */
+int ebr_server_destroy(ebr_server *s);
+
 #ifdef __cplusplus
 }
 #endif

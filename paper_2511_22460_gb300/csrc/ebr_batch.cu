@@ -890,18 +890,16 @@ static int stage(void *dst, const void *src, size_t bytes, int io, cudaStream_t 
   return EBR_OK;
 }
 
-int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint32_t B,
-                uint32_t *out_ids, float *out_scores, uint32_t kmax, int io, cudaStream_t st) {
-  BatchWs &w = ix->bws;
+// Stages the batch's requests into w, launches expansion, the window scan and
+// the merge on st, and queues the copies of the per-user status and the
+// control block to w's pinned mirror.  Nothing here waits for the device.
+int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint32_t B,
+                 uint32_t *d_ids, float *d_scores, uint32_t kmax, int io, BatchWs &w,
+                 cudaStream_t st) {
   const uint32_t d = ix->d, fu = cross->f_u, words = (ix->n_ads + 63) / 64;
-  std::vector<uint32_t> kk(2 * B), hasf(B, 0);
   uint32_t kscan_max = 1;
-  for (uint32_t b = 0; b < B; b++) {
-    kk[b] = std::min<uint32_t>(q[b].k * ix->rescore_mult, ix->n_ads);
-    kk[B + b] = q[b].k;
-    kscan_max = std::max(kscan_max, kk[b]);
-    hasf[b] = q[b].filter ? 1u : 0u;
-  }
+  for (uint32_t b = 0; b < B; b++)
+    kscan_max = std::max(kscan_max, std::min<uint32_t>(q[b].k * ix->rescore_mult, ix->n_ads));
   const int grid = std::max(1, std::min<int>(ix->num_sms, (int)ix->n_win));
   BatchPlan pl;
   if (!plan_batch(ix, B, kscan_max, grid, &pl)) {
@@ -915,20 +913,38 @@ int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint3
   EBR_TRY(dev_reserve(w.user_vals, (size_t)B * fu * 4));
   EBR_TRY(dev_reserve(w.wT, ((size_t)ix->n_keys + 1) * Bp * 4));
   EBR_TRY(dev_reserve(w.filters, (size_t)B * words * 8));
-  EBR_TRY(dev_reserve(w.has_filter, (size_t)B * 4));
-  EBR_TRY(dev_reserve(w.kk, (size_t)2 * B * 4));
-  EBR_TRY(dev_reserve(w.status, (size_t)B * 4 + 64));
+  EBR_TRY(dev_reserve(w.small, (size_t)3 * B * 4 + 256));
   EBR_TRY(dev_reserve(w.cand, (size_t)grid * B * pl.cap_u * sizeof(CandEntry)));
   EBR_TRY(dev_reserve(w.cand_n, (size_t)grid * B * 4));
   EBR_TRY(dev_reserve(w.cand_thr, (size_t)grid * B * 8));
   EBR_TRY(dev_reserve(w.scratch, (size_t)B * (kMergeCap + 8192) * 8));
-  EBR_TRY(dev_reserve(w.out, (size_t)B * kmax * 8 + 256));
-  Ctrl *ctrl = (Ctrl *)ix->ws.ctrl.p;
-  if (!ctrl) {
-    EBR_TRY(dev_reserve(ix->ws.ctrl, 256));
-    ctrl = (Ctrl *)ix->ws.ctrl.p;
+  EBR_TRY(dev_reserve(w.ctrl, sizeof(Ctrl)));
+  const size_t host_need = (size_t)4 * B * 4;
+  if (w.host_bytes < host_need) {
+    if (w.host) cudaFreeHost(w.host);
+    w.host = nullptr;
+    w.host_bytes = 0;
+    if (cudaMallocHost(&w.host, host_need) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("batched scan: pinned host allocation of %zu bytes failed", host_need);
+      return EBR_ENOMEM;
+    }
+    w.host_bytes = host_need;
   }
+  // pinned host mirror: [kscan B][kout B][has_filter B] in, then [status B] out
+  uint32_t *h_in = reinterpret_cast<uint32_t *>(w.host);
+  for (uint32_t b = 0; b < B; b++) {
+    h_in[b] = std::min<uint32_t>(q[b].k * ix->rescore_mult, ix->n_ads);
+    h_in[B + b] = q[b].k;
+    h_in[2 * B + b] = q[b].filter ? 1u : 0u;
+  }
+  uint32_t *kk = (uint32_t *)w.small.p;
+  uint32_t *has_filter = kk + 2 * B;
+  uint32_t *status = (uint32_t *)((char *)w.small.p + (((size_t)3 * B * 4 + 127) / 128 * 128));
+  Ctrl *ctrl = (Ctrl *)w.ctrl.p;
   EBR_CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
+  EBR_CUDA_TRY(cudaMemcpyAsync(kk, h_in, (size_t)3 * B * 4, cudaMemcpyHostToDevice, st));
+  EBR_CUDA_TRY(cudaMemsetAsync(status, 0, B * 4, st));
   // request inputs
   EBR_CUDA_TRY(cudaMemsetAsync(w.users_f32.p, 0, (size_t)Bp * d * 4, st));
   for (uint32_t b = 0; b < B; b++) {
@@ -937,20 +953,17 @@ int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint3
     if (q[b].filter)
       EBR_TRY(stage((uint64_t *)w.filters.p + (size_t)b * words, q[b].filter, words * 8, io, st));
   }
-  EBR_CUDA_TRY(cudaMemcpyAsync(w.has_filter.p, hasf.data(), B * 4, cudaMemcpyHostToDevice, st));
-  EBR_CUDA_TRY(cudaMemcpyAsync(w.kk.p, kk.data(), 2 * B * 4, cudaMemcpyHostToDevice, st));
-  EBR_CUDA_TRY(cudaMemsetAsync(w.status.p, 0, B * 4, st));
   EBR_TRY(launch_quantize((const float *)w.users_f32.p, (uint64_t)Bp * d, EBR_BF16, w.users_bf16.p,
                           st));
   EBR_TRY(expand_transposed(cross, (const uint32_t *)w.user_vals.p, B, Bp, (float *)w.wT.p,
                             &ctrl->flags, st));
   EBR_CUDA_TRY(cudaMemsetAsync((float *)w.wT.p + (size_t)ix->n_keys * Bp, 0, (size_t)Bp * 4, st));
-  ix->launches += 2;
   // tensor maps
-  if (!w.tmap_ready) {
+  if (!w.tmap_ready || w.tmap_for != ix->emb_q.p) {
     EBR_TRY(make_tmap_bf16(reinterpret_cast<CUtensorMap *>(w.tmap_bytes), ix->emb_q.p, ix->n_ads,
                            d, 128));
     w.tmap_ready = true;
+    w.tmap_for = ix->emb_q.p;
   }
   BatchArgs a;
   memset(&a, 0, sizeof(a));
@@ -964,7 +977,7 @@ int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint3
   a.ad_nkeys = (const uint16_t *)ix->ad_nkeys.p;
   a.wT = (const float *)w.wT.p;
   a.filters = (const uint64_t *)w.filters.p;
-  a.has_filter = (const uint32_t *)w.has_filter.p;
+  a.has_filter = has_filter;
   a.n_ads = ix->n_ads;
   a.n_win = ix->n_win;
   a.B = B;
@@ -986,33 +999,35 @@ int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint3
                                     (int)pl.smem));
   k_batch_window<<<grid, kBatchThreads, pl.smem, st>>>(a);
   EBR_CUDA_TRY(cudaGetLastError());
-  uint32_t *d_ids = out_ids;
-  float *d_scores = out_scores;
-  if (io == EBR_IO_HOST) {
-    d_ids = (uint32_t *)w.out.p;
-    d_scores = (float *)((char *)w.out.p + (((size_t)B * kmax * 4 + 255) / 256 * 256));
-  }
   EBR_CUDA_TRY(cudaFuncSetAttribute(k_batch_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     8192 * 8));
   k_batch_merge<<<B, kMergeThreads, 8192 * 8, st>>>(
       (const CandEntry *)w.cand.p, (const uint32_t *)w.cand_n.p,
-      (const unsigned long long *)w.cand_thr.p, (uint32_t)grid, B, pl.cap_u,
-      (const uint32_t *)w.kk.p, (const uint32_t *)w.kk.p + B, kmax, (const float *)ix->emb_f32.p, d,
-      (const float *)w.users_f32.p, (uint64_t *)w.scratch.p, d_ids, d_scores,
-      (uint32_t *)w.status.p);
+      (const unsigned long long *)w.cand_thr.p, (uint32_t)grid, B, pl.cap_u, kk, kk + B, kmax,
+      (const float *)ix->emb_f32.p, d, (const float *)w.users_f32.p, (uint64_t *)w.scratch.p,
+      d_ids, d_scores, status);
   EBR_CUDA_TRY(cudaGetLastError());
-  ix->launches += 2;
+  ix->launches += 4;
   ix->batched += B;
-  // status: flags and users whose per-CTA buffers could not prove exactness
-  std::vector<uint32_t> status(B);
+  // status and flags back to the pinned mirror
+  uint32_t *h_status = h_in + 3 * B;
+  EBR_CUDA_TRY(cudaMemcpyAsync(h_status, status, B * 4, cudaMemcpyDeviceToHost, st));
+  return EBR_OK;
+}
+
+// Waits for a batch started by batch_launch, checks the device flags and
+// recomputes on the single-request scan every user whose candidate buffers
+// could not prove exactness (outputs rewritten in place on st).
+int batch_finish(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint32_t B,
+                 uint32_t *d_ids, float *d_scores, uint32_t kmax, BatchWs &w, cudaStream_t st) {
+  const uint32_t d = ix->d, fu = cross->f_u, words = (ix->n_ads + 63) / 64;
   Ctrl hc;
-  EBR_CUDA_TRY(cudaMemcpyAsync(status.data(), w.status.p, B * 4, cudaMemcpyDeviceToHost, st));
-  EBR_CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  EBR_CUDA_TRY(cudaMemcpyAsync(&hc, w.ctrl.p, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
   EBR_CUDA_TRY(cudaStreamSynchronize(st));
   EBR_TRY(check_device_flags(hc.flags, "ebr_score_topk (batched)"));
+  const uint32_t *h_status = reinterpret_cast<const uint32_t *>(w.host) + 3 * B;
   for (uint32_t b = 0; b < B; b++) {
-    if (!status[b]) continue;
-    // exact fallback for this user: the single-request scan
+    if (!h_status[b]) continue;
     ebr_query dq = q[b];
     dq.h_u = (const float *)w.users_f32.p + (size_t)b * d;
     dq.user_vals = (const uint32_t *)w.user_vals.p + (size_t)b * fu;
@@ -1021,16 +1036,41 @@ int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint3
     EBR_TRY(query_one(ix, cross, dq, d_ids + (size_t)b * kmax, d_scores + (size_t)b * kmax, kmax,
                       st));
     ix->fallbacks += 1;
-    EBR_CUDA_TRY(cudaMemcpyAsync(&hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    EBR_CUDA_TRY(cudaMemcpyAsync(&hc, ix->ws.ctrl.p, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     EBR_CUDA_TRY(cudaStreamSynchronize(st));
     EBR_TRY(check_device_flags(hc.flags, "ebr_score_topk (single-request recompute)"));
   }
+  return EBR_OK;
+}
+
+void batch_ws_free(BatchWs &w) {
+  for (DevBuf *b : {&w.users_f32, &w.users_bf16, &w.user_vals, &w.wT, &w.filters, &w.small,
+                    &w.cand, &w.cand_n, &w.cand_thr, &w.scratch, &w.res, &w.ctrl})
+    dev_free(*b);
+  if (w.host) cudaFreeHost(w.host);
+  w.host = nullptr;
+  w.host_bytes = 0;
+  w.tmap_ready = false;
+}
+
+int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint32_t B,
+                uint32_t *out_ids, float *out_scores, uint32_t kmax, int io, cudaStream_t st) {
+  BatchWs &w = ix->bws;
+  uint32_t *d_ids = out_ids;
+  float *d_scores = out_scores;
+  if (io == EBR_IO_HOST) {
+    EBR_TRY(dev_reserve(w.res, (size_t)B * kmax * 8 + 256));
+    d_ids = (uint32_t *)w.res.p;
+    d_scores = (float *)((char *)w.res.p + (((size_t)B * kmax * 4 + 255) / 256 * 256));
+  }
+  EBR_TRY(batch_launch(ix, cross, q, B, d_ids, d_scores, kmax, io, w, st));
+  EBR_TRY(batch_finish(ix, cross, q, B, d_ids, d_scores, kmax, w, st));
   if (io == EBR_IO_HOST) {
     EBR_CUDA_TRY(cudaMemcpyAsync(out_ids, d_ids, (size_t)B * kmax * 4, cudaMemcpyDeviceToHost, st));
     EBR_CUDA_TRY(
         cudaMemcpyAsync(out_scores, d_scores, (size_t)B * kmax * 4, cudaMemcpyDeviceToHost, st));
+    EBR_CUDA_TRY(cudaStreamSynchronize(st));
   }
-  EBR_CUDA_TRY(cudaStreamSynchronize(st));
   return EBR_OK;
 }
 

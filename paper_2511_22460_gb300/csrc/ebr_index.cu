@@ -525,11 +525,7 @@ extern "C" void ebr_index_free(ebr_index *ix) {
   for (DevBuf *b : {&w.wide, &w.w_dense, &w.lens, &w.scan, &w.work, &w.cub_tmp, &w.cand,
                     &w.ctrl, &w.io_in, &w.io_out, &w.hist})
     dev_free(*b);
-  BatchWs &bw = ix->bws;
-  for (DevBuf *b : {&bw.users_f32, &bw.users_bf16, &bw.user_vals, &bw.wT, &bw.filters,
-                    &bw.has_filter, &bw.kk, &bw.status, &bw.cand, &bw.cand_n, &bw.cand_thr,
-                    &bw.scratch, &bw.out})
-    dev_free(*b);
+  batch_ws_free(ix->bws);
   if (w.host_ctrl) cudaFreeHost(w.host_ctrl);
   for (auto *v : {&ix->prof_pending, &ix->prof_pool})
     for (auto &ev : *v)

@@ -87,11 +87,18 @@ struct Ctrl {
 
 // Scratch of the batched (tensor-core) path.
 struct BatchWs {
-  DevBuf users_f32, users_bf16, user_vals, wT, filters, has_filter, kk, status;
-  DevBuf cand, cand_n, cand_thr, scratch, out;
+  DevBuf users_f32, users_bf16, user_vals, wT, filters;
+  DevBuf small;  // uint32 [kscan B][kout B][has_filter B], then status [B]
+  DevBuf cand, cand_n, cand_thr, scratch;
+  DevBuf res;    // device staging of host-bound results
+  DevBuf ctrl;   // Ctrl of this batch
+  void *host = nullptr;  // pinned mirror of `small`
+  size_t host_bytes = 0;
   bool tmap_ready = false;
+  const void *tmap_for = nullptr;
   alignas(64) unsigned char tmap_bytes[128];  // CUtensorMap of the BF16 table
 };
+void batch_ws_free(BatchWs &w);
 
 }  // namespace ebr
 
@@ -145,7 +152,7 @@ struct ebr_cross {
   ebr::DevBuf meta;        // packed uint32 metadata (see ebr_query.cu)
   uint64_t w_len = 0;
   // host copies
-  std::string host_meta;   // bytes of the packed metadata
+  std::vector<uint32_t> vocab_u_host;  // user field vocabularies (request checks)
 };
 
 namespace ebr {
@@ -170,4 +177,12 @@ bool batch_qualifies(const ebr_index *ix, const ebr_cross *cross, const ebr_quer
                      uint32_t batch);
 int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint32_t batch,
                 uint32_t *out_ids, float *out_scores, uint32_t kmax, int io, cudaStream_t st);
+// The same in two halves, for callers that keep several batches in flight:
+// batch_launch queues everything on st (w must stay untouched until
+// batch_finish returns); batch_finish waits, checks and recomputes.
+int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint32_t B,
+                 uint32_t *d_ids, float *d_scores, uint32_t kmax, int io, BatchWs &w,
+                 cudaStream_t st);
+int batch_finish(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint32_t B,
+                 uint32_t *d_ids, float *d_scores, uint32_t kmax, BatchWs &w, cudaStream_t st);
 }

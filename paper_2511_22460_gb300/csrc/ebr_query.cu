@@ -990,6 +990,7 @@ extern "C" int ebr_cross_create(const ebr_cross_desc *d, ebr_cross **out) {
   c->kind = d->kind;
   c->hash_bits = d->hash_bits;
   c->w_len = d->w_len;
+  c->vocab_u_host.assign(d->vocab_u, d->vocab_u + d->f_u);
   int rc = dev_alloc(c->table, d->w_len * 4);
   if (rc == EBR_OK) rc = dev_alloc(c->meta, m.size() * 4);
   cudaStream_t st = (cudaStream_t)d->stream;

@@ -1,0 +1,584 @@
+// Continuous-batching request loop (ebr_server_*, ebr_submit, ebr_poll).
+//
+// Requests arrive on any host thread and are copied into device-resident
+// slots on a copy stream.  One worker thread owns the GPU side: it keeps two
+// pipelines (workspace + stream each) and, whenever one is free and requests
+// are queued, launches all of them (up to max_batch) as one batched scan;
+// otherwise it finishes the oldest pipeline in flight and publishes its
+// results.  Requests that arrive while a batch is on the GPU therefore join
+// the next batch, which is staged and launched before the running one is
+// finished.  Admission is by device memory: the slots and both workspaces are
+// allocated up front from the HBM budget, and a submit finding no free slot
+// is refused.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "ebr_internal.cuh"
+
+namespace ebr {
+
+namespace {
+
+enum SlotState { kFree = 0, kQueued, kRunning, kDone, kFailed };
+
+struct Slot {
+  SlotState state = kFree;
+  uint64_t ticket = 0;
+  uint32_t k = 0;
+  bool has_filter = false;
+  double t_submit = 0.0;
+  int rc = EBR_OK;
+  std::string err;
+  float *d_hu = nullptr;
+  uint32_t *d_uv = nullptr;
+  uint64_t *d_filter = nullptr;
+  float *h_hu = nullptr;
+  uint32_t *h_uv = nullptr;
+  uint64_t *h_filter = nullptr;
+  uint32_t *h_ids = nullptr;
+  float *h_scores = nullptr;
+  cudaEvent_t copied = nullptr;
+};
+
+struct Pipe {
+  BatchWs ws;
+  cudaStream_t st = nullptr;
+  DevBuf out;                  // ids [max_batch][k_max] then scores
+  uint32_t *h_ids = nullptr;   // pinned copies of the outputs
+  float *h_scores = nullptr;
+  std::vector<int> slots;
+  std::vector<ebr_query> qs;
+  uint32_t kmax = 0;
+  bool busy = false;
+  bool single = false;  // ran on the single-request scan (already complete)
+};
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+// Device bytes one batched call of B users may reserve in its workspace.
+static size_t batch_ws_bytes(const ebr_index *ix, const ebr_cross *cross, uint32_t B,
+                             uint32_t kscan) {
+  uint32_t Bq = 32;
+  while (Bq < B) Bq <<= 1;
+  const uint64_t grid = std::max(1, std::min<int>(ix->num_sms, (int)ix->n_win));
+  const uint64_t per_cta = (kscan + grid - 1) / grid;
+  const uint64_t m = std::max<uint64_t>(64, (2 * per_cta + 32 + 31) / 32 * 32);
+  const uint64_t cap_u = 2 * m + 256;
+  const uint64_t words = (ix->n_ads + 63) / 64;
+  size_t t = 0;
+  t += round256((size_t)Bq * ix->d * 4) + round256((size_t)Bq * ix->d * 2);
+  t += round256((size_t)B * cross->f_u * 4) + round256(((size_t)ix->n_keys + 1) * Bq * 4);
+  t += round256((size_t)B * words * 8) + round256((size_t)3 * B * 4 + 256);
+  t += round256(grid * B * cap_u * 16) + round256(grid * B * 4) + round256(grid * B * 8);
+  t += round256((size_t)B * (32768 + 8192) * 8) + 256;
+  return t;
+}
+
+}  // namespace ebr
+
+using namespace ebr;
+
+struct ebr_server {
+  ebr_index *ix = nullptr;
+  const ebr_cross *cross = nullptr;
+  int device = 0;
+  uint32_t max_batch = 64, max_slots = 256, k_max = 1000, timeout_ms = 0;
+  uint32_t words = 0;
+  bool batched_ok = false;
+  std::vector<Slot> slots;
+  std::vector<int> free_slots;
+  std::deque<int> queue;
+  std::unordered_map<uint64_t, int> by_ticket;
+  uint64_t next_ticket = 1;
+  Pipe pipes[2];
+  cudaStream_t copy_st = nullptr;
+  DevBuf slot_mem;
+  void *slot_host = nullptr;
+  uint64_t device_bytes = 0, slot_bytes = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread worker;
+  bool stop = false;
+  ebr_server_stats st = {};
+  std::vector<float> lat;  // ring of latencies (ms)
+  uint64_t lat_n = 0;
+};
+
+namespace ebr {
+namespace {
+
+void fail_slots(ebr_server *s, const std::vector<int> &ids, int rc, const std::string &msg) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (int i : ids) {
+    Slot &sl = s->slots[i];
+    sl.state = kFailed;
+    sl.rc = rc;
+    sl.err = msg;
+    s->st.failed += 1;
+  }
+}
+
+// Launch the queued requests `take` on pipe p (stream-ordered, no waiting);
+// requests that cannot take the batched path run one by one, synchronously.
+int pipe_launch(ebr_server *s, int p, const std::vector<int> &take) {
+  Pipe &P = s->pipes[p];
+  P.slots = take;
+  P.qs.assign(take.size(), ebr_query{});
+  P.kmax = 0;
+  for (size_t i = 0; i < take.size(); i++) {
+    Slot &sl = s->slots[take[i]];
+    ebr_query &q = P.qs[i];
+    q.h_u = sl.d_hu;
+    q.user_vals = sl.d_uv;
+    q.filter = sl.has_filter ? sl.d_filter : nullptr;
+    q.k = sl.k;
+    P.kmax = std::max(P.kmax, sl.k);
+    EBR_CUDA_TRY(cudaStreamWaitEvent(P.st, sl.copied, 0));
+  }
+  const uint32_t B = (uint32_t)take.size();
+  uint32_t *d_ids = (uint32_t *)P.out.p;
+  float *d_scores = (float *)((char *)P.out.p + round256((size_t)s->max_batch * s->k_max * 4));
+  if (s->batched_ok && batch_qualifies(s->ix, s->cross, P.qs.data(), B)) {
+    EBR_TRY(batch_launch(s->ix, s->cross, P.qs.data(), B, d_ids, d_scores, P.kmax, EBR_IO_DEVICE,
+                         P.ws, P.st));
+    P.single = false;
+    P.busy = true;
+    return EBR_OK;
+  }
+  // one request (or an index the batched scan does not take): the
+  // single-request scan, each checked before the next
+  P.single = true;
+  EBR_TRY(ws_prepare_one(s->ix, s->ix->n_keys, 8192));
+  for (uint32_t b = 0; b < B; b++) {
+    EBR_TRY(query_one(s->ix, s->cross, P.qs[b], d_ids + (size_t)b * P.kmax,
+                      d_scores + (size_t)b * P.kmax, P.kmax, P.st));
+    Ctrl hc;
+    EBR_CUDA_TRY(cudaMemcpyAsync(&hc, s->ix->ws.ctrl.p, sizeof(Ctrl), cudaMemcpyDeviceToHost, P.st));
+    EBR_CUDA_TRY(cudaStreamSynchronize(P.st));
+    EBR_TRY(check_device_flags(hc.flags, "ebr_server (single-request scan)"));
+  }
+  P.busy = true;
+  return EBR_OK;
+}
+
+int pipe_finish(ebr_server *s, int p) {
+  Pipe &P = s->pipes[p];
+  const uint32_t B = (uint32_t)P.slots.size();
+  uint32_t *d_ids = (uint32_t *)P.out.p;
+  float *d_scores = (float *)((char *)P.out.p + round256((size_t)s->max_batch * s->k_max * 4));
+  if (!P.single)
+    EBR_TRY(batch_finish(s->ix, s->cross, P.qs.data(), B, d_ids, d_scores, P.kmax, P.ws, P.st));
+  EBR_CUDA_TRY(cudaMemcpyAsync(P.h_ids, d_ids, (size_t)B * P.kmax * 4, cudaMemcpyDeviceToHost, P.st));
+  EBR_CUDA_TRY(
+      cudaMemcpyAsync(P.h_scores, d_scores, (size_t)B * P.kmax * 4, cudaMemcpyDeviceToHost, P.st));
+  EBR_CUDA_TRY(cudaStreamSynchronize(P.st));
+  const double t = now_s();
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (uint32_t b = 0; b < B; b++) {
+    Slot &sl = s->slots[P.slots[b]];
+    memcpy(sl.h_ids, P.h_ids + (size_t)b * P.kmax, sl.k * 4);
+    memcpy(sl.h_scores, P.h_scores + (size_t)b * P.kmax, sl.k * 4);
+    sl.state = kDone;
+    const float ms = (float)((t - sl.t_submit) * 1e3);
+    s->lat[s->lat_n % s->lat.size()] = ms;
+    s->lat_n += 1;
+    s->st.completed += 1;
+  }
+  s->st.batches += 1;
+  s->st.batched_requests += B;
+  return EBR_OK;
+}
+
+void worker_main(ebr_server *s) {
+  cudaSetDevice(s->device);
+  std::deque<int> inflight;  // pipes in launch order
+  for (;;) {
+    int lp = -1;
+    std::vector<int> take;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->stop) break;
+      if (s->timeout_ms && !s->queue.empty()) {  // shed requests that waited too long
+        const double t = now_s();
+        std::deque<int> keep;
+        for (int i : s->queue) {
+          Slot &sl = s->slots[i];
+          if ((t - sl.t_submit) * 1e3 > s->timeout_ms) {
+            sl.state = kFailed;
+            sl.rc = EBR_ETIMEDOUT;
+            sl.err = "ebr_server: request waited longer than queue_timeout_ms";
+            s->st.failed += 1;
+          } else {
+            keep.push_back(i);
+          }
+        }
+        s->queue.swap(keep);
+      }
+      for (int p = 0; p < 2 && lp < 0; p++)
+        if (!s->pipes[p].busy) lp = p;
+      if (lp >= 0 && !s->queue.empty()) {
+        while (!s->queue.empty() && take.size() < s->max_batch) {
+          const int i = s->queue.front();
+          s->queue.pop_front();
+          s->slots[i].state = kRunning;
+          take.push_back(i);
+        }
+      } else if (inflight.empty()) {
+        s->cv.wait_for(lk, std::chrono::milliseconds(2));
+        continue;
+      }
+    }
+    if (!take.empty()) {
+      const int rc = pipe_launch(s, lp, take);
+      if (rc != EBR_OK) {
+        s->pipes[lp].busy = false;
+        fail_slots(s, take, rc, ebr_last_error());
+      } else {
+        inflight.push_back(lp);
+      }
+      continue;
+    }
+    const int p = inflight.front();
+    inflight.pop_front();
+    const int rc = pipe_finish(s, p);
+    if (rc != EBR_OK) fail_slots(s, s->pipes[p].slots, rc, ebr_last_error());
+    s->pipes[p].busy = false;
+  }
+  while (!inflight.empty()) {  // let launched work drain before teardown
+    cudaStreamSynchronize(s->pipes[inflight.front()].st);
+    inflight.pop_front();
+  }
+}
+
+void server_free(ebr_server *s) {
+  for (Pipe &P : s->pipes) {
+    batch_ws_free(P.ws);
+    dev_free(P.out);
+    if (P.h_ids) cudaFreeHost(P.h_ids);
+    if (P.h_scores) cudaFreeHost(P.h_scores);
+    if (P.st) cudaStreamDestroy(P.st);
+  }
+  for (Slot &sl : s->slots)
+    if (sl.copied) cudaEventDestroy(sl.copied);
+  dev_free(s->slot_mem);
+  if (s->slot_host) cudaFreeHost(s->slot_host);
+  if (s->copy_st) cudaStreamDestroy(s->copy_st);
+  delete s;
+}
+
+// Reserve every buffer a batch of B users with K up to kmax can touch, so
+// that serving allocates nothing after creation.
+int pipe_reserve(ebr_server *s, Pipe &P) {
+  ebr_index *ix = s->ix;
+  const uint32_t B = s->max_batch, d = ix->d, fu = s->cross->f_u;
+  uint32_t Bq = 32;
+  while (Bq < B) Bq <<= 1;
+  const uint32_t kscan = std::min<uint32_t>(s->k_max * ix->rescore_mult, ix->n_ads);
+  const int grid = std::max(1, std::min<int>(ix->num_sms, (int)ix->n_win));
+  const uint64_t per_cta = (kscan + grid - 1) / grid;
+  const uint64_t m = std::max<uint64_t>(64, (2 * per_cta + 32 + 31) / 32 * 32);
+  const uint64_t cap_u = 2 * m + 256;
+  const size_t words = s->words;
+  EBR_TRY(dev_reserve(P.ws.users_f32, (size_t)Bq * d * 4));
+  EBR_TRY(dev_reserve(P.ws.users_bf16, (size_t)Bq * d * 2));
+  EBR_TRY(dev_reserve(P.ws.user_vals, (size_t)B * fu * 4));
+  EBR_TRY(dev_reserve(P.ws.wT, ((size_t)ix->n_keys + 1) * Bq * 4));
+  EBR_TRY(dev_reserve(P.ws.filters, (size_t)B * words * 8));
+  EBR_TRY(dev_reserve(P.ws.small, (size_t)3 * B * 4 + 256));
+  EBR_TRY(dev_reserve(P.ws.cand, (size_t)grid * B * cap_u * 16));
+  EBR_TRY(dev_reserve(P.ws.cand_n, (size_t)grid * B * 4));
+  EBR_TRY(dev_reserve(P.ws.cand_thr, (size_t)grid * B * 8));
+  EBR_TRY(dev_reserve(P.ws.scratch, (size_t)B * (32768 + 8192) * 8));
+  EBR_TRY(dev_reserve(P.ws.ctrl, sizeof(Ctrl)));
+  const size_t ob = round256((size_t)B * s->k_max * 4);
+  EBR_TRY(dev_reserve(P.out, 2 * ob));
+  if (cudaMallocHost((void **)&P.h_ids, (size_t)B * s->k_max * 4) != cudaSuccess ||
+      cudaMallocHost((void **)&P.h_scores, (size_t)B * s->k_max * 4) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("ebr_server_create: pinned host allocation failed");
+    return EBR_ENOMEM;
+  }
+  EBR_CUDA_TRY(cudaStreamCreateWithFlags(&P.st, cudaStreamNonBlocking));
+  return EBR_OK;
+}
+
+}  // namespace
+}  // namespace ebr
+
+extern "C" int ebr_server_create(ebr_index *ix, const ebr_cross *cross, const ebr_server_cfg *cfg,
+                                 ebr_server **out) {
+  clear_error();
+  if (!ix || !cross || !out) {
+    set_error("ebr_server_create: null argument");
+    return EBR_EINVAL;
+  }
+  if (cross->n_keys != ix->n_keys) {
+    set_error("ebr_server_create: cross model has %u keys, index has %u", cross->n_keys,
+              ix->n_keys);
+    return EBR_EINVAL;
+  }
+  ebr_server_cfg c = cfg ? *cfg : ebr_server_cfg{};
+  if (c.max_batch == 0) c.max_batch = 64;
+  if (c.k_max == 0) c.k_max = 1000;
+  if (c.max_batch > 256 || c.k_max > 8192 ||
+      (ix->dtype != EBR_F32 && (uint64_t)c.k_max * ix->rescore_mult > 8192)) {
+    set_error("ebr_server_create: max_batch must be <= 256 and k_max <= 8192 (R*k_max <= 8192 "
+              "for BF16/FP8 indexes)");
+    return EBR_EINVAL;
+  }
+  int prev = 0;
+  cudaGetDevice(&prev);
+  EBR_CUDA_TRY(cudaSetDevice(ix->device));
+  ebr_server *s = new ebr_server();
+  s->ix = ix;
+  s->cross = cross;
+  s->device = ix->device;
+  s->k_max = c.k_max;
+  s->timeout_ms = c.queue_timeout_ms;
+  s->words = (ix->n_ads + 63) / 64;
+  // admission budget: slots + two pipelines must fit
+  uint64_t budget = c.hbm_budget;
+  if (budget == 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    budget = fr / 2;
+  }
+  s->slot_bytes = round256((size_t)s->words * 8) + round256((size_t)ix->d * 4) +
+                  round256((size_t)cross->f_u * 4);
+  const uint32_t kscan = std::min<uint32_t>(c.k_max * ix->rescore_mult, ix->n_ads);
+  uint32_t mb = c.max_batch;
+  auto pipes_bytes = [&](uint32_t B) {
+    return 2 * (batch_ws_bytes(ix, cross, B, kscan) + 2 * round256((size_t)B * c.k_max * 4));
+  };
+  while (mb > 1 && pipes_bytes(mb) + (uint64_t)mb * s->slot_bytes > budget) mb >>= 1;
+  if (pipes_bytes(mb) + (uint64_t)mb * s->slot_bytes > budget) {
+    set_error("ebr_server_create: HBM budget of %llu bytes holds no batch (one request needs "
+              "%llu)",
+              (unsigned long long)budget,
+              (unsigned long long)(pipes_bytes(1) + s->slot_bytes));
+    delete s;
+    cudaSetDevice(prev);
+    return EBR_ENOMEM;
+  }
+  s->max_batch = mb;
+  uint64_t n_slots = (budget - pipes_bytes(mb)) / s->slot_bytes;
+  const uint32_t want = c.max_slots ? c.max_slots : 4 * mb;
+  n_slots = std::min<uint64_t>(n_slots, want);
+  s->max_slots = (uint32_t)std::max<uint64_t>(n_slots, 1);
+  s->batched_ok = ix->dtype == EBR_BF16;
+  s->lat.assign(65536, 0.f);
+  // slots: device memory and pinned host staging
+  int rc = dev_alloc(s->slot_mem, (size_t)s->max_slots * s->slot_bytes);
+  const size_t host_slot = round256((size_t)s->words * 8) + round256((size_t)ix->d * 4) +
+                           round256((size_t)cross->f_u * 4) + 2 * round256((size_t)c.k_max * 4);
+  if (rc == EBR_OK && cudaMallocHost(&s->slot_host, (size_t)s->max_slots * host_slot) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("ebr_server_create: pinned host allocation failed");
+    rc = EBR_ENOMEM;
+  }
+  if (rc == EBR_OK && cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking) != cudaSuccess) {
+    set_error("ebr_server_create: stream creation failed");
+    rc = EBR_ECUDA;
+  }
+  if (rc == EBR_OK) {
+    s->slots.resize(s->max_slots);
+    for (uint32_t i = 0; i < s->max_slots; i++) {
+      Slot &sl = s->slots[i];
+      char *dp = (char *)s->slot_mem.p + (size_t)i * s->slot_bytes;
+      sl.d_filter = (uint64_t *)dp;
+      sl.d_hu = (float *)(dp + round256((size_t)s->words * 8));
+      sl.d_uv = (uint32_t *)(dp + round256((size_t)s->words * 8) + round256((size_t)ix->d * 4));
+      char *hp = (char *)s->slot_host + (size_t)i * host_slot;
+      sl.h_filter = (uint64_t *)hp;
+      hp += round256((size_t)s->words * 8);
+      sl.h_hu = (float *)hp;
+      hp += round256((size_t)ix->d * 4);
+      sl.h_uv = (uint32_t *)hp;
+      hp += round256((size_t)cross->f_u * 4);
+      sl.h_ids = (uint32_t *)hp;
+      hp += round256((size_t)c.k_max * 4);
+      sl.h_scores = (float *)hp;
+      if (cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming) != cudaSuccess) {
+        set_error("ebr_server_create: event creation failed");
+        rc = EBR_ECUDA;
+        break;
+      }
+      s->free_slots.push_back((int)(s->max_slots - 1 - i));
+    }
+  }
+  for (int p = 0; p < 2 && rc == EBR_OK; p++) rc = pipe_reserve(s, s->pipes[p]);
+  if (rc != EBR_OK) {
+    server_free(s);
+    cudaSetDevice(prev);
+    return rc;
+  }
+  s->device_bytes = (uint64_t)s->max_slots * s->slot_bytes + pipes_bytes(mb);
+  s->worker = std::thread(worker_main, s);
+  cudaSetDevice(prev);
+  *out = s;
+  return EBR_OK;
+}
+
+extern "C" int ebr_submit(ebr_server *s, const ebr_query *q, uint64_t *ticket) {
+  clear_error();
+  if (!s || !q || !ticket || !q->h_u || !q->user_vals) {
+    set_error("ebr_submit: needs a server, h_u and user_vals (host pointers) and a ticket");
+    return EBR_EINVAL;
+  }
+  if (q->k == 0 || q->k > s->k_max || q->q_key || q->q_w) {
+    set_error("ebr_submit: k must be 1..%u; q_key/q_w are not accepted", s->k_max);
+    return EBR_EINVAL;
+  }
+  for (uint32_t f = 0; f < s->cross->f_u; f++)
+    if (q->user_vals[f] >= s->cross->vocab_u_host[f]) {
+      set_error("ebr_submit: user field %u value %u outside its vocabulary of %u", f,
+                q->user_vals[f], s->cross->vocab_u_host[f]);
+      return EBR_EINVAL;
+    }
+  int i = -1;
+  uint64_t t = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->st.submitted += 1;
+    if (s->free_slots.empty()) {
+      s->st.rejected += 1;
+      set_error("ebr_submit: admission refused, all %u device slots are in use", s->max_slots);
+      return EBR_ENOMEM;
+    }
+    i = s->free_slots.back();
+    s->free_slots.pop_back();
+    t = s->next_ticket++;
+  }
+  Slot &sl = s->slots[i];
+  sl.ticket = t;
+  sl.k = q->k;
+  sl.has_filter = q->filter != nullptr;
+  sl.rc = EBR_OK;
+  sl.err.clear();
+  sl.t_submit = now_s();
+  const ebr_index *ix = s->ix;
+  memcpy(sl.h_hu, q->h_u, (size_t)ix->d * 4);
+  memcpy(sl.h_uv, q->user_vals, (size_t)s->cross->f_u * 4);
+  if (sl.has_filter) memcpy(sl.h_filter, q->filter, (size_t)s->words * 8);
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  cudaError_t e = cudaMemcpyAsync(sl.d_hu, sl.h_hu, (size_t)ix->d * 4, cudaMemcpyHostToDevice,
+                                  s->copy_st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(sl.d_uv, sl.h_uv, (size_t)s->cross->f_u * 4, cudaMemcpyHostToDevice,
+                        s->copy_st);
+  if (e == cudaSuccess && sl.has_filter)
+    e = cudaMemcpyAsync(sl.d_filter, sl.h_filter, (size_t)s->words * 8, cudaMemcpyHostToDevice,
+                        s->copy_st);
+  if (e == cudaSuccess) e = cudaEventRecord(sl.copied, s->copy_st);
+  cudaSetDevice(prev);
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (e != cudaSuccess) {
+    sl.state = kFree;
+    s->free_slots.push_back(i);
+    set_error("ebr_submit: %s", cudaGetErrorString(e));
+    return EBR_ECUDA;
+  }
+  sl.state = kQueued;
+  s->by_ticket[t] = i;
+  s->queue.push_back(i);
+  s->st.admitted += 1;
+  *ticket = t;
+  s->cv.notify_one();
+  return EBR_OK;
+}
+
+extern "C" int ebr_poll(ebr_server *s, uint64_t ticket, uint32_t *ids, float *scores) {
+  clear_error();
+  if (!s) {
+    set_error("ebr_poll: null server");
+    return EBR_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->by_ticket.find(ticket);
+  if (it == s->by_ticket.end()) {
+    set_error("ebr_poll: unknown or retired ticket %llu", (unsigned long long)ticket);
+    return EBR_EINVAL;
+  }
+  Slot &sl = s->slots[it->second];
+  if (sl.state == kQueued || sl.state == kRunning) return EBR_EAGAIN;
+  int rc = EBR_OK;
+  if (sl.state == kDone) {
+    if (!ids || !scores) {
+      set_error("ebr_poll: null output buffer");
+      return EBR_EINVAL;
+    }
+    memcpy(ids, sl.h_ids, (size_t)sl.k * 4);
+    memcpy(scores, sl.h_scores, (size_t)sl.k * 4);
+  } else {
+    rc = sl.rc;
+    set_error("%s", sl.err.c_str());
+  }
+  sl.state = kFree;
+  s->free_slots.push_back(it->second);
+  s->by_ticket.erase(it);
+  return rc;
+}
+
+extern "C" int ebr_server_get_stats(ebr_server *s, ebr_server_stats *out) {
+  clear_error();
+  if (!s || !out) {
+    set_error("ebr_server_get_stats: null argument");
+    return EBR_EINVAL;
+  }
+  std::vector<float> l;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->st;
+    const size_t n = (size_t)std::min<uint64_t>(s->lat_n, s->lat.size());
+    l.assign(s->lat.begin(), s->lat.begin() + n);
+  }
+  out->max_batch = s->max_batch;
+  out->max_slots = s->max_slots;
+  out->device_bytes = s->device_bytes;
+  out->slot_bytes = s->slot_bytes;
+  out->p50_ms = out->p99_ms = out->mean_ms = 0.0;
+  if (!l.empty()) {
+    double sum = 0;
+    for (float x : l) sum += x;
+    out->mean_ms = sum / l.size();
+    std::sort(l.begin(), l.end());
+    out->p50_ms = l[(size_t)(0.50 * (l.size() - 1) + 0.5)];
+    out->p99_ms = l[(size_t)(0.99 * (l.size() - 1) + 0.5)];
+  }
+  return EBR_OK;
+}
+
+extern "C" int ebr_server_destroy(ebr_server *s) {
+  clear_error();
+  if (!s) return EBR_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  if (s->copy_st) cudaStreamSynchronize(s->copy_st);
+  server_free(s);
+  cudaSetDevice(prev);
+  return EBR_OK;
+}

@@ -61,6 +61,19 @@ class QueryC(C.Structure):
                 ("filter", vp), ("k", u32), ("flags", u32)]
 
 
+class ServerCfg(C.Structure):
+    _fields_ = [("hbm_budget", u64), ("max_batch", u32), ("max_slots", u32), ("k_max", u32),
+                ("queue_timeout_ms", u32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", u64), ("admitted", u64), ("rejected", u64), ("completed", u64),
+                ("failed", u64), ("batches", u64), ("batched_requests", u64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("max_batch", u32), ("max_slots", u32), ("device_bytes", u64),
+                ("slot_bytes", u64)]
+
+
 class Profile(C.Structure):
     _fields_ = [("calls", u64), ("launches", u64), ("lib_launches", u64),
                 ("ms_expand", C.c_double), ("ms_wide", C.c_double), ("ms_scan", C.c_double),
@@ -94,6 +107,11 @@ ebr_scan_topk_noalloc = _sig("ebr_scan_topk_noalloc", i32,
 ebr_debug_gemm_bf16 = _sig("ebr_debug_gemm_bf16", i32, [vp, u32, vp, u32, u32, vp, vp])
 ebr_profile_enable = _sig("ebr_profile_enable", i32, [vp, i32])
 ebr_profile_read = _sig("ebr_profile_read", i32, [vp, C.POINTER(Profile)])
+ebr_server_create = _sig("ebr_server_create", i32, [vp, vp, vp, C.POINTER(vp)])
+ebr_submit = _sig("ebr_submit", i32, [vp, C.POINTER(QueryC), C.POINTER(u64)])
+ebr_poll = _sig("ebr_poll", i32, [vp, u64, vp, vp])
+ebr_server_get_stats = _sig("ebr_server_get_stats", i32, [vp, vp])
+ebr_server_destroy = _sig("ebr_server_destroy", i32, [vp])
 
 
 class EbrError(RuntimeError):
@@ -303,3 +321,65 @@ def debug_gemm_bf16(A, U, out, stream=None):
     """out[n][B] = A[n][d] @ U[B][d]^T on the tensor cores (BF16 in, FP32 out)."""
     _check(ebr_debug_gemm_bf16(ptr(A), int(A.shape[0]), ptr(U), int(U.shape[0]), int(A.shape[1]),
                                ptr(out), stream_ptr(stream)), "ebr_debug_gemm_bf16")
+
+
+class Server:
+    """Continuous-batching request loop (ebr_server_create / ebr_submit / ebr_poll).
+
+    Requests are host arrays; results come back as host arrays."""
+
+    def __init__(self, index: Index, cross: Cross, hbm_budget=0, max_batch=0, max_slots=0,
+                 k_max=0, queue_timeout_ms=0):
+        cfg = ServerCfg(int(hbm_budget), int(max_batch), int(max_slots), int(k_max),
+                        int(queue_timeout_ms))
+        h = vp()
+        _check(ebr_server_create(index.h, cross.h, C.byref(cfg), C.byref(h)), "ebr_server_create")
+        self.h = h.value
+        self._keep = (index, cross)
+
+    def submit(self, h_u, user_vals, k, filter=None):
+        """Ticket of the admitted request, or None when admission is refused."""
+        q = QueryC(ptr(h_u), ptr(user_vals), 0, None, None, ptr(filter), int(k), 0)
+        t = u64()
+        rc = ebr_submit(self.h, C.byref(q), C.byref(t))
+        if rc == EBR_ENOMEM:
+            return None
+        _check(rc, "ebr_submit")
+        return t.value
+
+    def poll(self, ticket, k):
+        """(ids, scores) once done, None while pending; raises on a failed request."""
+        ids = np.empty(k, np.uint32)
+        sc = np.empty(k, np.float32)
+        rc = ebr_poll(self.h, int(ticket), ids.ctypes.data, sc.ctypes.data)
+        if rc == EBR_EAGAIN:
+            return None
+        _check(rc, "ebr_poll")
+        return ids, sc
+
+    def wait(self, ticket, k, timeout_s=60.0):
+        import time
+        t0 = time.monotonic()
+        while True:
+            r = self.poll(ticket, k)
+            if r is not None:
+                return r
+            if time.monotonic() - t0 > timeout_s:
+                raise TimeoutError("request %d not done after %.0f s" % (ticket, timeout_s))
+            time.sleep(0.0002)
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        _check(ebr_server_get_stats(self.h, C.byref(st)), "ebr_server_get_stats")
+        return st
+
+    def close(self):
+        if self.h:
+            ebr_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

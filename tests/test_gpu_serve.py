@@ -1,0 +1,150 @@
+"""GPU tests of the continuous-batching request loop: each result is the same
+alone and in a mix of concurrent requests (and matches the FP64 oracle),
+admission by the HBM budget, ticket semantics and the per-request path."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from gpu_util import bitmap_to_mask, check_topk, recall, ref_scores  # noqa: E402
+from paper_2511_22460_gb300 import ebr  # noqa: E402
+from paper_2511_22460_gb300.datagen import make_filters, make_workload  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(n, B, dtype="bf16", seed=21):
+    w = make_workload("serve_bf16_5m", n_ads=n, seed=seed, batch=B)
+    pk, pa = w.postings(shuffle=True)
+    ix = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype=dtype)
+    cross = ebr.cross_from_workload(w)
+    return w, (pk, pa), ix, cross
+
+
+def _same_result(a, b, ref, tol, k, mask=None):
+    """Two results of one request agree: equal id sets except for ties within
+    tolerance at the K-th oracle score, scores within tolerance."""
+    ids_a, sc_a = a
+    ids_b, sc_b = b
+    elig = np.ones(ref.size, bool) if mask is None else mask
+    take = min(k, int(elig.sum()))
+    r = np.where(elig, ref, -np.inf)
+    kth = np.sort(r)[::-1][take - 1]
+    diff = set(ids_a[:take].tolist()) ^ set(ids_b[:take].tolist())
+    for x in diff:
+        assert abs(ref[x] - kth) <= 2 * tol[x], "id %d differs and is not a tie" % x
+    common = np.intersect1d(ids_a[:take], ids_b[:take])
+    pa = {int(i): s for i, s in zip(ids_a[:take], sc_a[:take])}
+    pb = {int(i): s for i, s in zip(ids_b[:take], sc_b[:take])}
+    for i in common:
+        assert abs(float(pa[int(i)]) - float(pb[int(i)])) <= 2 * tol[i]
+
+
+def test_alone_and_in_a_mix_give_the_same_result():
+    n, B = 60_000, 40
+    w, post, ix, cross = _setup(n, B)
+    rng = np.random.default_rng(3)
+    ks = [int(x) for x in rng.choice([100, 500, 1000], size=B)]
+    fl = make_filters(rng, n, B, (0.01, 1.0))
+    filt = [fl[b] if b % 2 else None for b in range(B)]
+    srv = ebr.Server(ix, cross, max_batch=64, k_max=1000)
+    try:
+        probe = [0, 7, 13, 30]
+        alone = {}
+        for b in probe:  # one at a time: the single-request scan
+            t = srv.submit(w.h_u[b], w.users[b], ks[b], filt[b])
+            alone[b] = srv.wait(t, ks[b])
+        # all at once: batched scans mixing users with different K and filters
+        tickets = [srv.submit(w.h_u[b], w.users[b], ks[b], filt[b]) for b in range(B)]
+        assert all(t is not None for t in tickets)
+        mixed = {b: srv.wait(t, ks[b]) for b, t in enumerate(tickets)}
+        st = srv.stats()
+        assert st.completed == B + len(probe) and st.failed == 0
+        assert st.batches < B + len(probe), "requests were never batched"
+        for b in probe + [1, 2, 5, 39]:
+            ref, tol = ref_scores(w, b, post)
+            mask = None if filt[b] is None else bitmap_to_mask(filt[b], n)
+            ids, sc = mixed[b]
+            assert recall(ids, ref, tol, ks[b], mask) == 1.0
+            check_topk(ids, sc, ref, tol, ks[b], mask)
+            if b in alone:
+                _same_result(alone[b], mixed[b], ref, tol, ks[b], mask)
+    finally:
+        srv.close()
+
+
+def test_admission_by_hbm_budget_and_slot_reuse():
+    n = 20_000
+    w, post, ix, cross = _setup(n, 12)
+    # the budget decides: far too small -> no server at all
+    with pytest.raises(ebr.EbrError) as e:
+        ebr.Server(ix, cross, hbm_budget=1 << 20, max_batch=8, k_max=100)
+    assert e.value.code == ebr.EBR_ENOMEM
+    # measure what 8-user pipelines and one slot cost, then allow 8 slots
+    probe = ebr.Server(ix, cross, max_batch=8, max_slots=16, k_max=100)
+    st = probe.stats()
+    pipes = st.device_bytes - st.max_slots * st.slot_bytes
+    probe.close()
+    budget = pipes + 8 * st.slot_bytes + st.slot_bytes // 2
+    srv = ebr.Server(ix, cross, hbm_budget=budget, max_batch=8, k_max=100)
+    try:
+        st = srv.stats()
+        assert st.max_slots == 8 and st.max_batch == 8
+        assert st.device_bytes <= budget
+        tickets = [srv.submit(w.h_u[b], w.users[b], 50) for b in range(8)]
+        assert all(t is not None for t in tickets)
+        assert srv.submit(w.h_u[8], w.users[8], 50) is None  # refused: no free slot
+        assert srv.stats().rejected == 1
+        ids, sc = srv.wait(tickets[0], 50)
+        t9 = srv.submit(w.h_u[8], w.users[8], 50)  # the retired slot is reused
+        assert t9 is not None
+        res9 = srv.wait(t9, 50)
+        for t in tickets[1:]:
+            srv.wait(t, 50)
+        ref, tol = ref_scores(w, 8, post)
+        check_topk(res9[0], res9[1], ref, tol, 50)
+        # tickets are retired by the poll that returns them
+        with pytest.raises(ebr.EbrError) as e:
+            srv.poll(tickets[0], 50)
+        assert e.value.code == ebr.EBR_EINVAL
+    finally:
+        srv.close()
+
+
+def test_submit_rejects_bad_requests():
+    w, post, ix, cross = _setup(5_000, 2)
+    srv = ebr.Server(ix, cross, max_batch=4, k_max=100)
+    try:
+        for k in (0, 101):
+            with pytest.raises(ebr.EbrError) as e:
+                srv.submit(w.h_u[0], w.users[0], k)
+            assert e.value.code == ebr.EBR_EINVAL
+        bad = w.users[1].copy()
+        bad[0] = 1 << 30  # a user value outside its vocabulary: refused at submit
+        with pytest.raises(ebr.EbrError) as e:
+            srv.submit(w.h_u[1], bad, 10)
+        assert e.value.code == ebr.EBR_EINVAL
+        t = srv.submit(w.h_u[0], w.users[0], 10)  # the server still serves
+        ids, sc = srv.wait(t, 10)
+        ref, tol = ref_scores(w, 0, post)
+        check_topk(ids, sc, ref, tol, 10)
+    finally:
+        srv.close()
+
+
+def test_fp32_index_server_matches_oracle():
+    n, B = 30_000, 10
+    w, post, ix, cross = _setup(n, B, dtype="f32")
+    srv = ebr.Server(ix, cross, max_batch=16, k_max=500)
+    try:
+        tickets = [srv.submit(w.h_u[b], w.users[b], 200) for b in range(B)]
+        res = [srv.wait(t, 200) for t in tickets]
+        for b in (0, 4, 9):
+            ref, tol = ref_scores(w, b, post)
+            check_topk(res[b][0], res[b][1], ref, tol, 200)
+        st = srv.stats()
+        assert st.completed == B and st.p99_ms >= st.p50_ms > 0
+    finally:
+        srv.close()
