@@ -232,10 +232,136 @@ def run_gpu(args, rank, world, local_rank):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
+    del ix, h_u, users, flush
+    if world == 1 and not args.no_serve:
+        out["serving"] = run_serving(args, device=local_rank)
     return out
 
 
 KERNEL_REV = "fused-v1"
+
+
+def run_serving(args, device=0):
+    """Serving form (the 5,000,000-ad BF16 d=64 serving workload): open-loop
+    Poisson arrivals through ebr_submit/ebr_poll at each offered rate, each
+    request with its own user, K in {100, 500, 1000} and targeting bitmap;
+    p50/p99 from submit to result visible; then the plain per-request FP32 path
+    on the same inventory through ebr_score_topk with host buffers."""
+    import torch
+
+    import oracle
+    from paper_2511_22460_gb300 import ebr
+    from paper_2511_22460_gb300.datagen import poisson_arrivals
+
+    t_gen = time.perf_counter()
+    pool = args.serve_pool
+    w = make_workload("serve_bf16_5m", seed=args.seed, batch=pool)
+    pk, pa = w.postings()
+    gen_s = time.perf_counter() - t_gen
+    ix = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype="bf16", device=device)
+    cross = ebr.cross_from_workload(w, device=device)
+    ks = [int(x) for x in w.ks]
+    reqs = [(np.ascontiguousarray(w.h_u[b]), np.ascontiguousarray(w.users[b]), ks[b],
+             np.ascontiguousarray(w.filters[b])) for b in range(pool)]
+    srv = ebr.Server(ix, cross, max_batch=args.serve_batch, max_slots=4096, k_max=1000)
+    check_ids = {0: None, 1: None}
+
+    def drive(rate, duration, keep):
+        # one thread: submit every request whose arrival time has passed, then
+        # retire whatever the server reports finished (no lock, no GIL contention)
+        arr = poisson_arrivals(rate, duration, seed=args.seed + int(rate))
+        outstanding = {}
+        n_done = rejected = failed = 0
+        last = 0.0
+        i = 0
+        t0 = time.perf_counter()
+        while i < len(arr) or outstanding:
+            now = time.perf_counter() - t0
+            busy = False
+            while i < len(arr) and arr[i] <= now:
+                b = i % pool
+                h, u, k, f = reqs[b]
+                t = srv.submit(h, u, k, f)
+                if t is None:
+                    rejected += 1
+                else:
+                    outstanding[t] = b
+                i += 1
+                busy = True
+            for t in srv.completed():
+                b = outstanding.pop(int(t))
+                busy = True
+                try:
+                    r = srv.poll(int(t), ks[b])
+                except ebr.EbrError:
+                    failed += 1
+                    continue
+                if keep and b in check_ids and check_ids[b] is None:
+                    check_ids[b] = r
+                n_done += 1
+                last = time.perf_counter()
+            if not busy:
+                time.sleep(2e-5)
+        span = max(last, t0 + duration) - t0
+        return len(arr), n_done, rejected + failed, span
+
+    drive(2000.0, 0.3, False)  # warm-up
+    rows = []
+    for rate in args.serve_rates:
+        srv.reset_stats()
+        offered, n_done, rejected, span = drive(rate, args.serve_seconds, rate == args.serve_rates[0])
+        st = srv.stats()
+        rows.append({"offered_req_s": rate, "submitted": offered, "completed": n_done,
+                     "rejected": rejected, "req_per_s": n_done / span,
+                     "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
+                     "mean_batch": st.batched_requests / max(st.batches, 1)})
+    srv_stats = srv.stats()
+    srv.close()
+    # recall of served results against the FP64 oracle (two requests)
+    oc = oracle.Cross.from_workload(w)
+    recalls = []
+    for b, r in check_ids.items():
+        if r is None:
+            continue
+        s = oracle.score_query(w, b, oc, (pk, pa))
+        _, cond = oracle.scores_brute(oc, w.h_u[b], w.emb, w.ad_vals, w.users[b], with_cond=True)
+        tol = oracle.tolerance(s, cond, 1e-5)
+        bits = np.unpackbits(w.filters[b].view(np.uint8), bitorder="little")[:w.n_ads].astype(bool)
+        sm = np.where(bits, s, -np.inf)
+        k = ks[b]
+        kth = np.sort(sm)[::-1][min(k, int(bits.sum())) - 1]
+        ids = r[0][:k].astype(np.int64)
+        hit = sum(1 for a in ids if 0 <= a < w.n_ads and bits[a] and s[a] >= kth - tol[a])
+        recalls.append(hit / min(k, int(bits.sum())))
+    # the plain per-request FP32 path on the same inventory, host buffers
+    del ix
+    ix32 = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype="f32", device=device)
+    ids = np.empty(1000, np.uint32)
+    sc = np.empty(1000, np.float32)
+    for i in range(3):
+        h, u, k, f = reqs[i]
+        ebr.score_topk(ix32, cross, [ebr.Query(h_u=h, k=k, user_vals=u, filter=f)], ids, sc,
+                       io=ebr.IO_HOST)
+    n32 = args.serve_fp32_requests
+    t0 = time.perf_counter()
+    for i in range(n32):
+        h, u, k, f = reqs[i % pool]
+        ebr.score_topk(ix32, cross, [ebr.Query(h_u=h, k=k, user_vals=u, filter=f)], ids, sc,
+                       io=ebr.IO_HOST)
+    fp32_rps = n32 / (time.perf_counter() - t0)
+    del ix32
+    torch.cuda.synchronize()
+    best = max(rows, key=lambda r: r["req_per_s"])
+    return {"workload": "serve_bf16_5m", "n_ads": w.n_ads, "d": w.recipe.d,
+            "emb_dtype": "bf16 + FP32 rescoring (R=4)", "ad_fields": w.recipe.f_a,
+            "cross_pairs": int(len(w.pairs)), "k_choices": [100, 500, 1000],
+            "filter_fraction": "U[0.01, 1] per request", "request_pool": pool,
+            "max_batch": srv_stats.max_batch, "rates": rows,
+            "max_req_per_s": best["req_per_s"],
+            "recall_after_rescoring": recalls,
+            "fp32_per_request_req_per_s": fp32_rps,
+            "speedup_vs_fp32_per_request": best["req_per_s"] / fp32_rps,
+            "datagen_s": round(gen_s, 1)}
 
 
 def cpu_baseline(w, budget_s=15.0):
@@ -293,6 +419,12 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[2000, 5000, 10000, 20000])
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-batch", type=int, default=128)
+    ap.add_argument("--serve-pool", type=int, default=64)
+    ap.add_argument("--serve-fp32-requests", type=int, default=30)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))

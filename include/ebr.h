@@ -338,6 +338,7 @@ typedef struct {
   uint32_t max_batch, max_slots;    /* effective values after the HBM budget */
   uint64_t device_bytes;            /* device memory held by slots and workspaces */
   uint64_t slot_bytes;              /* device bytes of one request slot */
+  double launch_ms, finish_ms;      /* worker host time staging+launching / waiting+publishing */
 } ebr_server_stats;
 
 /*
@@ -360,6 +361,14 @@ int ebr_submit(ebr_server *s, const ebr_query *q, uint64_t *ticket);
  */
 int ebr_poll(ebr_server *s, uint64_t ticket, uint32_t *ids, float *scores);
 int ebr_server_get_stats(ebr_server *s, ebr_server_stats *out);
+/* Clears the counters and the latency record (e.g. after a warm-up). */
+int ebr_server_reset_stats(ebr_server *s);
+/*
+ * Tickets of requests that finished (done or failed) since the previous
+ * call, up to cap of them (the rest are kept for the next call); lets a
+ * client poll only what is ready.
+ */
+int ebr_server_completed(ebr_server *s, uint64_t *tickets, uint32_t cap, uint32_t *n);
 /* Stops the worker (requests still pending are dropped) and frees everything. */
 int ebr_server_destroy(ebr_server *s);
 

@@ -913,7 +913,7 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   EBR_TRY(dev_reserve(w.user_vals, (size_t)B * fu * 4));
   EBR_TRY(dev_reserve(w.wT, ((size_t)ix->n_keys + 1) * Bp * 4));
   EBR_TRY(dev_reserve(w.filters, (size_t)B * words * 8));
-  EBR_TRY(dev_reserve(w.small, (size_t)3 * B * 4 + 256));
+  EBR_TRY(dev_reserve(w.small, small_bytes(B)));
   EBR_TRY(dev_reserve(w.cand, (size_t)grid * B * pl.cap_u * sizeof(CandEntry)));
   EBR_TRY(dev_reserve(w.cand_n, (size_t)grid * B * 4));
   EBR_TRY(dev_reserve(w.cand_thr, (size_t)grid * B * 8));
@@ -940,7 +940,7 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   }
   uint32_t *kk = (uint32_t *)w.small.p;
   uint32_t *has_filter = kk + 2 * B;
-  uint32_t *status = (uint32_t *)((char *)w.small.p + (((size_t)3 * B * 4 + 127) / 128 * 128));
+  uint32_t *status = (uint32_t *)((char *)w.small.p + small_status_off(B));
   Ctrl *ctrl = (Ctrl *)w.ctrl.p;
   EBR_CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
   EBR_CUDA_TRY(cudaMemcpyAsync(kk, h_in, (size_t)3 * B * 4, cudaMemcpyHostToDevice, st));

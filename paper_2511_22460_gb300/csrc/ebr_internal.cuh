@@ -99,6 +99,10 @@ struct BatchWs {
   alignas(64) unsigned char tmap_bytes[128];  // CUtensorMap of the BF16 table
 };
 void batch_ws_free(BatchWs &w);
+// Layout of BatchWs::small for B users: [kscan B][kout B][has_filter B], then
+// the per-user status words from a 128-byte boundary.
+inline size_t small_status_off(uint32_t B) { return ((size_t)3 * B * 4 + 127) / 128 * 128; }
+inline size_t small_bytes(uint32_t B) { return small_status_off(B) + (size_t)B * 4; }
 
 }  // namespace ebr
 

@@ -83,7 +83,7 @@ static size_t batch_ws_bytes(const ebr_index *ix, const ebr_cross *cross, uint32
   size_t t = 0;
   t += round256((size_t)Bq * ix->d * 4) + round256((size_t)Bq * ix->d * 2);
   t += round256((size_t)B * cross->f_u * 4) + round256(((size_t)ix->n_keys + 1) * Bq * 4);
-  t += round256((size_t)B * words * 8) + round256((size_t)3 * B * 4 + 256);
+  t += round256((size_t)B * words * 8) + round256(small_bytes(B));
   t += round256(grid * B * cap_u * 16) + round256(grid * B * 4) + round256(grid * B * 8);
   t += round256((size_t)B * (32768 + 8192) * 8) + 256;
   return t;
@@ -117,6 +117,7 @@ struct ebr_server {
   ebr_server_stats st = {};
   std::vector<float> lat;  // ring of latencies (ms)
   uint64_t lat_n = 0;
+  std::deque<uint64_t> finished;  // tickets not yet reported by ebr_server_completed
 };
 
 namespace ebr {
@@ -130,6 +131,7 @@ void fail_slots(ebr_server *s, const std::vector<int> &ids, int rc, const std::s
     sl.rc = rc;
     sl.err = msg;
     s->st.failed += 1;
+    s->finished.push_back(sl.ticket);
   }
 }
 
@@ -194,6 +196,7 @@ int pipe_finish(ebr_server *s, int p) {
     memcpy(sl.h_ids, P.h_ids + (size_t)b * P.kmax, sl.k * 4);
     memcpy(sl.h_scores, P.h_scores + (size_t)b * P.kmax, sl.k * 4);
     sl.state = kDone;
+    s->finished.push_back(sl.ticket);
     const float ms = (float)((t - sl.t_submit) * 1e3);
     s->lat[s->lat_n % s->lat.size()] = ms;
     s->lat_n += 1;
@@ -223,6 +226,7 @@ void worker_main(ebr_server *s) {
             sl.rc = EBR_ETIMEDOUT;
             sl.err = "ebr_server: request waited longer than queue_timeout_ms";
             s->st.failed += 1;
+            s->finished.push_back(sl.ticket);
           } else {
             keep.push_back(i);
           }
@@ -244,7 +248,12 @@ void worker_main(ebr_server *s) {
       }
     }
     if (!take.empty()) {
+      const double tl0 = now_s();
       const int rc = pipe_launch(s, lp, take);
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->st.launch_ms += (now_s() - tl0) * 1e3;
+      }
       if (rc != EBR_OK) {
         s->pipes[lp].busy = false;
         fail_slots(s, take, rc, ebr_last_error());
@@ -255,7 +264,12 @@ void worker_main(ebr_server *s) {
     }
     const int p = inflight.front();
     inflight.pop_front();
+    const double tf0 = now_s();
     const int rc = pipe_finish(s, p);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->st.finish_ms += (now_s() - tf0) * 1e3;
+    }
     if (rc != EBR_OK) fail_slots(s, s->pipes[p].slots, rc, ebr_last_error());
     s->pipes[p].busy = false;
   }
@@ -299,7 +313,7 @@ int pipe_reserve(ebr_server *s, Pipe &P) {
   EBR_TRY(dev_reserve(P.ws.user_vals, (size_t)B * fu * 4));
   EBR_TRY(dev_reserve(P.ws.wT, ((size_t)ix->n_keys + 1) * Bq * 4));
   EBR_TRY(dev_reserve(P.ws.filters, (size_t)B * words * 8));
-  EBR_TRY(dev_reserve(P.ws.small, (size_t)3 * B * 4 + 256));
+  EBR_TRY(dev_reserve(P.ws.small, small_bytes(B)));
   EBR_TRY(dev_reserve(P.ws.cand, (size_t)grid * B * cap_u * 16));
   EBR_TRY(dev_reserve(P.ws.cand_n, (size_t)grid * B * 4));
   EBR_TRY(dev_reserve(P.ws.cand_thr, (size_t)grid * B * 8));
@@ -562,6 +576,34 @@ extern "C" int ebr_server_get_stats(ebr_server *s, ebr_server_stats *out) {
     out->p50_ms = l[(size_t)(0.50 * (l.size() - 1) + 0.5)];
     out->p99_ms = l[(size_t)(0.99 * (l.size() - 1) + 0.5)];
   }
+  return EBR_OK;
+}
+
+extern "C" int ebr_server_reset_stats(ebr_server *s) {
+  clear_error();
+  if (!s) {
+    set_error("ebr_server_reset_stats: null server");
+    return EBR_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->st = ebr_server_stats{};
+  s->lat_n = 0;
+  return EBR_OK;
+}
+
+extern "C" int ebr_server_completed(ebr_server *s, uint64_t *tickets, uint32_t cap, uint32_t *n) {
+  clear_error();
+  if (!s || !n || (cap && !tickets)) {
+    set_error("ebr_server_completed: null argument");
+    return EBR_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  uint32_t c = 0;
+  while (c < cap && !s->finished.empty()) {
+    tickets[c++] = s->finished.front();
+    s->finished.pop_front();
+  }
+  *n = c;
   return EBR_OK;
 }
 

@@ -71,7 +71,7 @@ class ServerStats(C.Structure):
                 ("failed", u64), ("batches", u64), ("batched_requests", u64),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
                 ("max_batch", u32), ("max_slots", u32), ("device_bytes", u64),
-                ("slot_bytes", u64)]
+                ("slot_bytes", u64), ("launch_ms", C.c_double), ("finish_ms", C.c_double)]
 
 
 class Profile(C.Structure):
@@ -112,6 +112,8 @@ ebr_submit = _sig("ebr_submit", i32, [vp, C.POINTER(QueryC), C.POINTER(u64)])
 ebr_poll = _sig("ebr_poll", i32, [vp, u64, vp, vp])
 ebr_server_get_stats = _sig("ebr_server_get_stats", i32, [vp, vp])
 ebr_server_destroy = _sig("ebr_server_destroy", i32, [vp])
+ebr_server_reset_stats = _sig("ebr_server_reset_stats", i32, [vp])
+ebr_server_completed = _sig("ebr_server_completed", i32, [vp, vp, u32, C.POINTER(u32)])
 
 
 class EbrError(RuntimeError):
@@ -372,6 +374,17 @@ class Server:
         st = ServerStats()
         _check(ebr_server_get_stats(self.h, C.byref(st)), "ebr_server_get_stats")
         return st
+
+    def reset_stats(self):
+        _check(ebr_server_reset_stats(self.h), "ebr_server_reset_stats")
+
+    def completed(self, cap=4096):
+        """Tickets finished since the previous call (done or failed)."""
+        buf = np.empty(cap, np.uint64)
+        n = u32()
+        _check(ebr_server_completed(self.h, buf.ctypes.data, cap, C.byref(n)),
+               "ebr_server_completed")
+        return buf[:n.value]
 
     def close(self):
         if self.h:

@@ -59,7 +59,9 @@ def _check_all(w, post, ids, sc, ks, filt=None, users=None):
 
 @pytest.mark.parametrize("name,n,B", [("serve_bf16_5m", 60_001, 64),
                                       ("batch256_bf16_5m", 40_000, 40),
-                                      ("serve_bf16_5m", 20_000, 2)])
+                                      ("serve_bf16_5m", 20_000, 2),
+                                      ("serve_bf16_5m", 30_000, 128),
+                                      ("batch256_bf16_5m", 25_000, 200)])
 def test_batched_topk_matches_oracle(name, n, B):
     ks = [100] * B
     w, post, ids, sc, nb, nr = _run(name, n, B, ks, seed=11)
