@@ -50,14 +50,36 @@ def _peaks():
 
 def _config(w, extra=None):
     r = w.recipe
+    emb_mb = r.n_ads * r.d * {"f32": 4, "bf16": 2, "fp8e4m3": 1}[r.emb_dtype] / 2**20
     cfg = {"workload": r.name, "n_ads": r.n_ads, "d": r.d, "emb_dtype": r.emb_dtype,
            "user_fields": r.f_u, "ad_fields": r.f_a, "cross_pairs": int(len(w.pairs)),
            "weights": "hashed 2^24 FP32" if r.weights == "hashed" else "dense per pair",
            "k": int(w.ks[0]), "n_keys": w.n_keys, "postings": w.nnz,
-           "l2": "flushed between steps (256 MiB write); embedding table 512 MB > L2"}
+           "l2": "flushed between steps (256 MiB write); embedding table %.0f MiB" % emb_mb}
+    if r.batch > 1:
+        cfg.update({"batch": r.batch, "k_per_user": sorted(set(int(x) for x in w.ks)),
+                    "rescore_mult": r.rescore_mult})
     if extra:
         cfg.update(extra)
     return cfg
+
+
+def max_over_ranks(x, device):
+    """Largest value of x over the ranks of the default process group (x itself
+    when there is none): the job is as slow as its slowest replica."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, total_ms):
+    """Units per second of the whole job: every rank processed units_per_rank
+    in at most total_ms (the max over ranks)."""
+    return units_per_rank * world / (total_ms / 1e3)
 
 
 class ClockSampler:
@@ -117,7 +139,9 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     st = torch.cuda.current_stream()
-    w = make_workload(args.workload, seed=args.seed)
+    w = _workload(args)
+    if w.recipe.batch > 1:
+        return run_gpu_batched(args, w, rank, world, local_rank)
     pk, pa = w.postings()
     ix = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype=w.recipe.emb_dtype,
                          device=local_rank)
@@ -161,13 +185,9 @@ def run_gpu(args, rank, world, local_rank):
     times = [a.elapsed_time(b) for a, b in evs]
     prof = ix.profile_read()
     ix.profile_enable(False)
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(times)), dev)
     ms_step = total_ms / args.steps
-    value = w.n_ads * args.steps * world / (total_ms / 1e3)
+    value = whole_job_rate(w.n_ads * args.steps, world, total_ms)
 
     # End to end through the C ABI with host buffers (request in, K results out).
     hk_ids = np.empty(k, np.uint32)
@@ -233,12 +253,131 @@ def run_gpu(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
     del ix, h_u, users, flush
-    if world == 1 and not args.no_serve:
+    if world == 1 and not args.no_serve and args.workload == WORKLOAD:
         out["serving"] = run_serving(args, device=local_rank)
     return out
 
 
 KERNEL_REV = "fused-v1"
+
+# FP32 add throughput of the CUDA cores: 152 SMs x 128 FP32 lanes x 2.07 GHz
+ALU_ADD_PEAK_T = 152 * 128 * 2.07e9 / 1e12
+
+
+def _workload(args):
+    kw = {}
+    if args.n_ads:
+        kw["n_ads"] = args.n_ads
+    if args.batch:
+        kw["batch"] = args.batch
+    return make_workload(args.workload, seed=args.seed, **kw)
+
+
+def run_gpu_batched(args, w, rank, world, local_rank):
+    """A step is one batched call: every user of the batch against the whole
+    inventory (tensor-core deep term, wide term from the compressed lists,
+    per-user top-K with FP32 rescoring)."""
+    import torch
+
+    from paper_2511_22460_gb300 import ebr
+
+    dev = torch.device("cuda", local_rank)
+    st = torch.cuda.current_stream()
+    pk, pa = w.postings()
+    ix = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype=w.recipe.emb_dtype,
+                         device=local_rank)
+    del pk, pa
+    cross = ebr.cross_from_workload(w, device=local_rank)
+    info = ix.info()
+    B = w.recipe.batch
+    ks = [int(x) for x in w.ks]
+    kmax = max(ks)
+    h_u = torch.from_numpy(w.h_u).to(dev)
+    users = torch.from_numpy(w.users).to(dev)
+    filt = None if w.filters is None else torch.from_numpy(w.filters.view(np.int64)).to(dev)
+    qs = [ebr.Query(h_u=h_u[b], k=ks[b], user_vals=users[b],
+                    filter=None if filt is None else filt[b]) for b in range(B)]
+    ids = torch.empty((B, kmax), dtype=torch.int32, device=dev)
+    sc = torch.empty((B, kmax), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        ebr.score_topk(ix, cross, qs, ids, sc, stream=st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ix.profile_enable(True)
+    p0 = ix.profile_read()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(st)
+        step()
+        evs[i][1].record(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in evs]
+    prof = ix.profile_read()
+    ix.profile_enable(False)
+    total_ms = max_over_ranks(float(sum(times)), dev)
+    ms_step = total_ms / args.steps
+    value = whole_job_rate(w.n_ads * B * args.steps, world, total_ms)
+    # end to end with host buffers: requests in, B x K results out
+    hq = [ebr.Query(h_u=np.ascontiguousarray(w.h_u[b]), k=ks[b],
+                    user_vals=np.ascontiguousarray(w.users[b]),
+                    filter=None if w.filters is None else np.ascontiguousarray(w.filters[b]))
+          for b in range(B)]
+    hids = np.empty((B, kmax), np.uint32)
+    hsc = np.empty((B, kmax), np.float32)
+    e2e_t = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ebr.score_topk(ix, cross, hq, hids, hsc, io=ebr.IO_HOST, stream=st)
+        if i >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_val = w.n_ads * B * len(e2e_t) / sum(e2e_t)
+    h2d = B * (w.recipe.d * 4 + w.recipe.f_u * 4) + (0 if w.filters is None else w.filters.nbytes)
+    calls = max(prof.batch_calls, 1)
+    scan_ms = prof.ms_batch_scan / calls
+    adds = B * info.nnz_unique  # the wide term's FP32 adds of one batched scan
+    achieved = adds / (scan_ms / 1e3) / 1e12
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": w.recipe.emb_dtype, "data": "synthetic",
+        "config": _config(w, {"replicas": world, "units": "user x ad pairs scored"}),
+        "req_per_s": B * 1e3 / ms_step * world,
+        "latency_ms": {"p50": float(np.percentile(times, 50)),
+                       "p99": float(np.percentile(times, 99))},
+        "stage_ms": {"stage_expand": prof.ms_batch_stage / calls, "scan": scan_ms,
+                     "merge_rescore": prof.ms_batch_merge / calls},
+        "recomputed_users": int(prof.recomputed - p0.recomputed),
+        "roofline": {"kernel": "k_batch_window", "bound": "alu", "achieved": achieved,
+                     "peak": ALU_ADD_PEAK_T, "unit": "Tadd/s", "frac": achieved / ALU_ADD_PEAK_T,
+                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
+                     "traffic": None, "algorithmic_ops": adds,
+                     "ops_note": "B x distinct (key, ad) postings FP32 adds of the wide term"},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(B * kmax * 8)},
+        "gpu_launches": int(prof.launches - p0.launches),
+        "gpu_launches_per_step": (prof.launches - p0.launches) / max(args.steps, 1),
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(w, budget_s=args.cpu_budget)
+        out["cpu_baseline"] = cb
+    return out
 
 
 def run_serving(args, device=0):
@@ -384,7 +523,7 @@ def cpu_baseline(w, budget_s=15.0):
 
 
 def run_reference(args):
-    w = make_workload(args.workload, seed=args.seed)
+    w = _workload(args)
     import oracle
     cross = oracle.Cross.from_workload(w)
     pk, pa = w.postings()
@@ -420,6 +559,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--n-ads", type=int, default=0, help="override the workload's inventory size")
+    ap.add_argument("--batch", type=int, default=0, help="override the workload's users per step")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[2000, 5000, 10000, 20000])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-batch", type=int, default=128)

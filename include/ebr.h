@@ -300,6 +300,10 @@ typedef struct {
   uint64_t batched;        /* requests served by the batched tensor-core scan */
   uint64_t recomputed;     /* of those, recomputed by the single-request scan because the
                               batched candidate buffers could not prove exactness */
+  uint64_t batch_calls;    /* batched calls profiled */
+  double ms_batch_stage;   /* staging + expansion into user-minor weights */
+  double ms_batch_scan;    /* k_batch_window: tensor-core deep term + wide term + per-CTA top-m */
+  double ms_batch_merge;   /* k_batch_merge: per-user merge, FP32 rescoring, final K */
 } ebr_profile;
 int ebr_profile_enable(ebr_index *ix, int on);
 int ebr_profile_read(ebr_index *ix, ebr_profile *out);

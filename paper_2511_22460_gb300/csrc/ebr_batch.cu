@@ -900,6 +900,19 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   uint32_t kscan_max = 1;
   for (uint32_t b = 0; b < B; b++)
     kscan_max = std::max(kscan_max, std::min<uint32_t>(q[b].k * ix->rescore_mult, ix->n_ads));
+  // profiling events (ebr_profile_enable): before staging, before the scan,
+  // after the scan, after the merge
+  std::array<cudaEvent_t, 5> ev{};
+  const bool prof = ix->prof;
+  if (prof) {
+    if (!ix->prof_pool.empty()) {
+      ev = ix->prof_pool.back();
+      ix->prof_pool.pop_back();
+    } else {
+      for (auto &e : ev) EBR_CUDA_TRY(cudaEventCreate(&e));
+    }
+    EBR_CUDA_TRY(cudaEventRecord(ev[0], st));
+  }
   const int grid = std::max(1, std::min<int>(ix->num_sms, (int)ix->n_win));
   BatchPlan pl;
   if (!plan_batch(ix, B, kscan_max, grid, &pl)) {
@@ -997,8 +1010,10 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   a.ctrl = ctrl;
   EBR_CUDA_TRY(cudaFuncSetAttribute(k_batch_window, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)pl.smem));
+  if (prof) EBR_CUDA_TRY(cudaEventRecord(ev[1], st));
   k_batch_window<<<grid, kBatchThreads, pl.smem, st>>>(a);
   EBR_CUDA_TRY(cudaGetLastError());
+  if (prof) EBR_CUDA_TRY(cudaEventRecord(ev[2], st));
   EBR_CUDA_TRY(cudaFuncSetAttribute(k_batch_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     8192 * 8));
   k_batch_merge<<<B, kMergeThreads, 8192 * 8, st>>>(
@@ -1007,6 +1022,10 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
       (const float *)ix->emb_f32.p, d, (const float *)w.users_f32.p, (uint64_t *)w.scratch.p,
       d_ids, d_scores, status);
   EBR_CUDA_TRY(cudaGetLastError());
+  if (prof) {
+    EBR_CUDA_TRY(cudaEventRecord(ev[3], st));
+    ix->bprof_pending.push_back(ev);
+  }
   ix->launches += 4;
   ix->batched += B;
   // status and flags back to the pinned mirror

@@ -527,7 +527,7 @@ extern "C" void ebr_index_free(ebr_index *ix) {
     dev_free(*b);
   batch_ws_free(ix->bws);
   if (w.host_ctrl) cudaFreeHost(w.host_ctrl);
-  for (auto *v : {&ix->prof_pending, &ix->prof_pool})
+  for (auto *v : {&ix->prof_pending, &ix->prof_pool, &ix->bprof_pending})
     for (auto &ev : *v)
       for (cudaEvent_t e : ev) cudaEventDestroy(e);
   cudaSetDevice(prev);

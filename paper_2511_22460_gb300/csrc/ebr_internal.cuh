@@ -141,6 +141,7 @@ struct ebr_index {
   // profiling (ebr_profile_enable)
   bool prof = false;
   std::vector<std::array<cudaEvent_t, 5>> prof_pending, prof_pool;
+  std::vector<std::array<cudaEvent_t, 5>> bprof_pending;  // batched calls (same pool)
   ebr_profile prof_acc = {};
   uint64_t launches = 0, lib_launches = 0;  // counted on every call
   uint64_t batched = 0;    // requests served by the batched scan

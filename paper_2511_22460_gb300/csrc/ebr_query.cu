@@ -1316,6 +1316,17 @@ extern "C" int ebr_profile_read(ebr_index *ix, ebr_profile *out) {
     ix->prof_pool.push_back(ev);
   }
   ix->prof_pending.clear();
+  for (auto &ev : ix->bprof_pending) {
+    EBR_CUDA_TRY(cudaEventSynchronize(ev[3]));
+    float t[3];
+    for (int i = 0; i < 3; i++) EBR_CUDA_TRY(cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]));
+    ix->prof_acc.batch_calls += 1;
+    ix->prof_acc.ms_batch_stage += t[0];
+    ix->prof_acc.ms_batch_scan += t[1];
+    ix->prof_acc.ms_batch_merge += t[2];
+    ix->prof_pool.push_back(ev);
+  }
+  ix->bprof_pending.clear();
   *out = ix->prof_acc;
   out->launches = ix->launches;
   out->lib_launches = ix->lib_launches;

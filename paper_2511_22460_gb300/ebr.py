@@ -77,7 +77,9 @@ class ServerStats(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("calls", u64), ("launches", u64), ("lib_launches", u64),
                 ("ms_expand", C.c_double), ("ms_wide", C.c_double), ("ms_scan", C.c_double),
-                ("ms_final", C.c_double), ("batched", u64), ("recomputed", u64)]
+                ("ms_final", C.c_double), ("batched", u64), ("recomputed", u64),
+                ("batch_calls", u64), ("ms_batch_stage", C.c_double),
+                ("ms_batch_scan", C.c_double), ("ms_batch_merge", C.c_double)]
 
 
 def _sig(name, res, args):
