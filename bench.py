@@ -213,6 +213,8 @@ def run_gpu(args, rank, world, local_rank):
     # the fused scan must read the embedding table and the window-major view of
     # the compressed lists (keys + value bytes + window offsets)
     kern_bytes = emb_bytes + info.window_view_bytes
+    if w.recipe.emb_dtype != "f32":
+        kern_bytes += 4 * w.n_ads  # the FP32 wide term, written for the rescoring
     achieved = kern_bytes / (scan_ms / 1e3) / 1e9
     step_bytes = kern_bytes
     traffic = None
@@ -226,7 +228,8 @@ def run_gpu(args, rank, world, local_rank):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": w.recipe.emb_dtype,
+        "data": "synthetic",
         "config": _config(w, {"replicas": world, "build_ms": round(info.build_ms, 3),
                               "window_view_ms": round(info.window_view_ms, 3),
                               "index_bytes": info.index_bytes,
@@ -241,8 +244,9 @@ def run_gpu(args, rank, world, local_rank):
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic,
                      "algorithmic_bytes": kern_bytes,
-                     "bytes_note": "embedding table + window-major view of the compressed "
-                                   "lists, per launch"},
+                     "bytes_note": "embedding table (+ FP8 row scales) + window-major view of "
+                                   "the compressed lists (+ FP32 wide term out when the "
+                                   "table is quantised), per launch"},
         "e2e": {"value": e2e_val, "unit": UNIT,
                 "h2d_bytes_per_step": int(w.recipe.d * 4 + w.recipe.f_u * 4),
                 "d2h_bytes_per_step": int(k * 8)},

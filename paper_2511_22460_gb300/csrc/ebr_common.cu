@@ -34,9 +34,7 @@ int check_device_flags(uint32_t flags, const char *where) {
             (flags & DEVERR_BAD_USER) ? "user value >= vocabulary " : "",
             (flags & DEVERR_OVERFLOW) ? "capacity overflow " : "",
             (flags & DEVERR_BAD_BUILD_KEY) ? "key >= n_keys " : "",
-            (flags & DEVERR_RANGE) ? "a query weight times the most keys of one ad is >= 8192 "
-                                     "(exact window accumulator range; use EBR_QF_KEY_MAJOR) "
-                                   : "");
+            (flags & DEVERR_RANGE) ? "a non-finite query weight " : "");
   return EBR_EDATA;
 }
 

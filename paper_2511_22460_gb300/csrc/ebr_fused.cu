@@ -15,8 +15,8 @@
 //       bulk copies (cp.async.bulk + mbarrier, L2 evict-first);
 //   decoders (2 teams x 5 warps): each team takes every other window; warps
 //       walk the window's blocks in chunks of 32 work units of one size group,
-//       gather w^[key] and add it into one of four exact fixed-point
-//       accumulators of 256 ads (two 32-bit integer atomics per ad slot);
+//       gather w^[key] and add it into one of four fixed-point accumulators
+//       of 256 ads (one 32-bit integer atomic per real ad slot);
 //   scorers (8 warps): one thread per row (two for 128-element rows) forms the
 //       inner product with its rotated copy of h_u held in registers, adds the
 //       window's accumulator (and the FP8 row scale), applies the filter and
@@ -61,7 +61,8 @@ struct FusedArgs {
   float *all_out;   // score-all mode
   float *wide_out;  // if set: the per-ad wide term is written here (FP32 rescoring needs it)
   uint32_t *hist;   // [256 + 65536] candidate-score histogram (zeroed per request)
-  float w_lim;      // |w^| must stay below this (exact accumulator range)
+  const uint32_t *wmax_bits;  // max |w^| over the keys (FP32 bits), set by k_absmax
+  uint32_t max_keys;          // most keys of one ad
 };
 
 template <typename Elt, int D>
@@ -92,19 +93,28 @@ struct SlotDesc {                // one window's staged segments
 
 constexpr int kPrefetch = 4;  // producer reads window offsets this many windows ahead
 
-// The window accumulators hold each ad's wide term exactly, in fixed point
-// with 36 fraction bits split over two 32-bit words (shared-memory integer
-// atomics are fast where FP32 ones are not): w = round(w^ * 2^36) is added as
-// hi = w >> 18 (signed) and lo = w & (2^18 - 1); the term is
-// hi * 2^-18 + lo * 2^-36.  With |w^| * (most keys of one ad) < 2^13 neither
-// word overflows; the decoders flag weights outside that range.
-constexpr float kFixScale = 68719476736.0f;      // 2^36
-constexpr float kHiUnit = 3.814697265625e-06f;   // 2^-18
-constexpr float kLoUnit = 1.4551915228366852e-11f;  // 2^-36
+// The window accumulators hold each ad's wide term in 32-bit fixed point
+// (shared-memory integer atomics are fast where FP32 ones are not, and an
+// integer sum does not depend on the order of the additions): every slot adds
+// round(w^ * 2^F), and the term is the sum times 2^-F.  F is chosen per request
+// as the largest power of two with max|w^| * 2^F * (most keys of one ad) below
+// 2^31, so no sum can overflow; each term is then off by at most 2^-(F+1),
+// about 2^-31 of max|w^| times the key count, far inside the FP32 path's error.
+__device__ __forceinline__ int fix_exponent(uint32_t wmax_bits, uint32_t max_keys) {
+  const float wmax = __uint_as_float(wmax_bits);
+  if (!(wmax > 0.f)) return 0;
+  const float mk = (float)max(max_keys, 1u);
+  const float limit = (2147483647.0f - mk) / mk;  // per-term bound of |w^| * 2^F
+  const float r = limit / wmax;
+  int e = (int)((__float_as_uint(r) >> 23) & 0xFFu) - 127;  // floor(log2 r), r normal
+  if (e > 100) e = 100;
+  if (e < -100) e = -100;
+  return e;
+}
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(127 + e) << 23); }
 
 struct FusedSmem {
-  int acc_hi[kAccBufs][kWin];
-  uint32_t acc_lo[kAccBufs][kWin];
+  int acc[kAccBufs][kWin];
   uint32_t wp[kPrefetch][kGroups];  // producer's ring of window offsets
   uint32_t ctab[kTeams][kMaxChunkTab];  // per team: group << 16 | chunk within the group
   SlotDesc desc[kIdxSlots];
@@ -140,10 +150,9 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
   const uint32_t w_end = (uint32_t)(((uint64_t)a.n_win * (blockIdx.x + 1)) / gridDim.x);
   const uint32_t my_wins = w_end - w_begin;
 
-  for (int i = tid; i < kAccBufs * kWin; i += kFusedThreads) {
-    (&sm.acc_hi[0][0])[i] = 0;
-    (&sm.acc_lo[0][0])[i] = 0u;
-  }
+  for (int i = tid; i < kAccBufs * kWin; i += kFusedThreads) (&sm.acc[0][0])[i] = 0;
+  const int fx_e = fix_exponent(*a.wmax_bits, a.max_keys);
+  const float fx_scale = pow2f(fx_e), fx_unit = pow2f(-fx_e);
   for (int i = tid; i < D; i += kFusedThreads) s_h[i] = a.h_u[i];
   if (tid == 0) {
     sm.n = 0;
@@ -327,13 +336,14 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
         tab[i] = (g << 16) | (i - cb);
       }
       named_sync(2 + team, kTeamThreads);
-      int *acc_hi = sm.acc_hi[b];
-      uint32_t *acc_lo = sm.acc_lo[b];
-      bool range_ok = true;
-      // Branch-free rounds: every chunk's loads are independent of the
-      // others', so the shared-memory reads and w^ gathers of a round overlap.
+      int *acc = sm.acc[b];
+      // Branch-free loads: every chunk's loads are independent of the
+      // others', so the shared-memory reads and w^ gathers of a round overlap;
+      // the additions then branch on the chunk's size group (uniform across
+      // the warp), so a unit issues only the atomics its group can need.
       for (uint32_t c0 = tw; c0 < n_chunks; c0 += kChunksInFlight * kTeamWarps) {
-        uint32_t word[kChunksInFlight], meta[kChunksInFlight], key[kChunksInFlight];
+        uint32_t word[kChunksInFlight], key[kChunksInFlight], gq[kChunksInFlight];
+        bool first[kChunksInFlight], valid[kChunksInFlight];
 #pragma unroll
         for (int q = 0; q < kChunksInFlight; q++) {
           const uint32_t c = c0 + q * kTeamWarps;  // warp-uniform
@@ -351,30 +361,33 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
           const uint32_t w32 = *reinterpret_cast<const uint32_t *>(slot + (off & ~3u));
           const uint32_t sh = 8 * (off & 3u);
           word[q] = g >= 2 ? w32 : ((w32 >> sh) & (g == 1 ? 0xFFFFu : 0xFFu));
-          // meta: slots in the word (1, 2 or 4) | first word of its block << 4
-          meta[q] = v ? ((g >= 2 ? 4u : (g == 1 ? 2u : 1u)) | (wi == 0 ? 16u : 0u)) : 0u;
+          gq[q] = cv ? g : 0xFFu;
+          first[q] = wi == 0;
+          valid[q] = v;
         }
-        float wt[kChunksInFlight];
+        int fx[kChunksInFlight];
 #pragma unroll
         for (int q = 0; q < kChunksInFlight; q++)
-          wt[q] = meta[q] ? __ldg(a.w_hat + key[q]) : 0.f;
+          fx[q] = valid[q] ? __float2int_rn(__ldg(a.w_hat + key[q]) * fx_scale) : 0;
 #pragma unroll
         for (int q = 0; q < kChunksInFlight; q++) {
-          range_ok = range_ok && fabsf(wt[q]) < a.w_lim;
-          const long long fx = __float2ll_rn(wt[q] * kFixScale);
-          const int hi = (int)(fx >> 18);
-          const uint32_t lo = (uint32_t)(fx & 0x3FFFFll);
-          const uint32_t ns = meta[q] & 7u;
+          const uint32_t g = gq[q];
+          const bool add = fx[q] != 0;
+          if (g >= 2 && g < (uint32_t)kGroups) {
 #pragma unroll
-          for (int s2 = 0; s2 < 4; s2++) {
-            const uint32_t l = (word[q] >> (8 * s2)) & 255u;
-            const bool real = (uint32_t)s2 < ns && ((s2 == 0 && (meta[q] & 16u)) || l != 0);
-            if (real && hi != 0) atomicAdd(&acc_hi[l], hi);
-            if (real && lo != 0) atomicAdd(&acc_lo[l], lo);
+            for (int s2 = 0; s2 < 4; s2++) {
+              const uint32_t l = (word[q] >> (8 * s2)) & 255u;
+              if (add && ((s2 == 0 && first[q]) || l != 0)) atomicAdd(&acc[l], fx[q]);
+            }
+          } else if (g == 1) {
+            if (add) atomicAdd(&acc[word[q] & 255u], fx[q]);  // slot 0 of a block is real
+            const uint32_t l = (word[q] >> 8) & 255u;
+            if (add && l != 0) atomicAdd(&acc[l], fx[q]);
+          } else if (g == 0) {
+            if (add) atomicAdd(&acc[word[q] & 255u], fx[q]);
           }
         }
       }
-      if (!range_ok) atomicOr(&a.ctrl->flags, DEVERR_RANGE);
       named_sync(2 + team, kTeamThreads);  // every read of the slot is done
       if (tt == 0) mbar_arrive(&sm.idx_empty[team]);
       mbar_arrive(&sm.acc_full[b]);  // release: this thread's additions into acc[b]
@@ -419,8 +432,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       mbar_try_wait(&sm.full[seq % S], (seq / S) & 1u);
     }
     const uint32_t w = w_begin + j;
-    const int *acc_hi = sm.acc_hi[b];
-    const uint32_t *acc_lo = sm.acc_lo[b];
+    const int *acc = sm.acc[b];
 #pragma unroll
     for (int ps = 0; ps < Sh::kPasses; ps++) {
       const uint32_t rw = ps * Sh::kRowsPerPass + prow;  // row within the window
@@ -449,7 +461,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       const bool leader = valid && qd == 0;
       float score = 0.f;
       if (leader) {
-        const float wide = fmaf((float)acc_lo[rw], kLoUnit, (float)acc_hi[rw] * kHiUnit);
+        const float wide = (float)acc[rw] * fx_unit;
         score = dot;
         if (a.scale) score *= a.scale[ad];
         score += wide;
@@ -478,10 +490,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
     if (tid == 0)
       for (uint32_t q = 0; q < (uint32_t)Sh::kStagesPerWin; q++)
         mbar_arrive(&sm.empty[(j * Sh::kStagesPerWin + q) % S]);
-    for (int i = tid; i < kWin; i += kDotThreads) {  // hand the accumulator back, zeroed
-      sm.acc_hi[b][i] = 0;
-      sm.acc_lo[b][i] = 0u;
-    }
+    for (int i = tid; i < kWin; i += kDotThreads) sm.acc[b][i] = 0;  // hand it back, zeroed
     mbar_arrive(&sm.acc_empty[b]);
     if (!ALL && sm.n + kWin > a.cap) {
       // trim the candidates to the K best: radix select, then a stable
@@ -612,11 +621,25 @@ static int launch_fused_d(const ebr_index *ix, const FusedArgs &a, int max_grid,
   return EBR_EINVAL;
 }
 
+// Largest |w[i]| as FP32 bits (non-negative floats order like their bits);
+// a non-finite weight is flagged.
+__global__ void k_absmax(const float *__restrict__ w, uint32_t n, uint32_t *__restrict__ out,
+                         uint32_t *__restrict__ flags) {
+  uint32_t m = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    m = max(m, __float_as_uint(w[i]) & 0x7FFFFFFFu);
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) {
+    if (m >= 0x7F800000u) atomicOr(flags, DEVERR_RANGE);
+    atomicMax(out, m >= 0x7F800000u ? 0u : m);
+  }
+}
+
 // Whether the fused scan fits shared memory for top-k on this index; if not,
 // dense queries take the key-major path (Algorithm 2) instead.
 bool fused_fits(const ebr_index *ix, uint32_t k) {
   uint32_t slot_bytes = 0;
-  return ix->max_win_chunks <= (uint32_t)kMaxChunkTab && ix->max_keys_per_ad < 8192u &&
+  return ix->max_win_chunks <= (uint32_t)kMaxChunkTab && ix->max_keys_per_ad <= 65536u &&
          fused_fixed_bytes(ix, ix->d, fused_cap(k), &slot_bytes) + 4 * (size_t)kStageBytes <=
              kFusedSmemBudget;
 }
@@ -648,7 +671,13 @@ int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
   a.all_out = all_out;
   a.wide_out = wide_out;
   a.hist = hist;
-  a.w_lim = 8192.0f / (float)std::max<uint32_t>(ix->max_keys_per_ad, 1);
+  a.max_keys = std::max<uint32_t>(ix->max_keys_per_ad, 1);
+  // max |w^| for the accumulators' fixed-point scale (non-finite weights are flagged)
+  a.wmax_bits = &ctrl->pad;
+  EBR_CUDA_TRY(cudaMemsetAsync(&ctrl->pad, 0, sizeof(uint32_t), st));
+  k_absmax<<<std::max<uint32_t>(1, std::min<uint32_t>(64, (ix->n_keys + 1023) / 1024)), 256, 0,
+             st>>>(w_hat, ix->n_keys, &ctrl->pad, &ctrl->flags);
+  EBR_CUDA_TRY(cudaGetLastError());
   if (all_out) {
     if (ix->dtype == EBR_F32) return launch_fused_d<float, true>(ix, a, max_grid, st);
     if (ix->dtype == EBR_BF16) return launch_fused_d<Bf16Tag, true>(ix, a, max_grid, st);

@@ -43,7 +43,7 @@ enum : uint32_t {
   DEVERR_TIMEOUT = 8u,        // a bounded wait ran out
   DEVERR_OVERFLOW = 16u,      // a capacity check failed
   DEVERR_BAD_BUILD_KEY = 32u, // key >= n_keys in build input
-  DEVERR_RANGE = 64u,         // a weight beyond the fused scan's exact accumulator range
+  DEVERR_RANGE = 64u,         // a non-finite query weight
 };
 
 int check_device_flags(uint32_t flags, const char *where);
@@ -82,7 +82,7 @@ struct Ctrl {
   unsigned int flags;        // DEVERR_* bits
   unsigned long long total_units;  // Algorithm 2 work units
   unsigned int n_work;       // compacted work entries
-  unsigned int pad;
+  unsigned int pad;          // fused scan: max |w^| of the request (FP32 bits)
 };
 
 // Scratch of the batched (tensor-core) path.
