@@ -38,11 +38,12 @@ constexpr int kTeamThreads = kTeamWarps * 32;
 constexpr int kProducerWarp = kDotWarps + kTeams * kTeamWarps;
 constexpr int kFusedThreads = (kProducerWarp + 1) * 32;  // 608 (19 warps)
 constexpr int kAccBufs = 4;
-constexpr int kIdxSlots = 2;  // one per decoder team
+constexpr int kIdxSlots = kTeams;  // one per decoder team
 constexpr int kStageBytes = 16384;
 constexpr int kMaxStages = 12;
+constexpr int kMinStages = 4;
 constexpr int kChunksInFlight = 8;  // decoder chunks of 32 units per warp per round
-constexpr int kMaxChunkTab = 1024;  // chunk -> (group, chunk in group) table per team
+constexpr int kMaxChunkTab = 512;  // chunk -> (group, chunk in group) table per team
 static_assert(kWin % kDotThreads == 0, "scorer threads split the window evenly");
 static_assert(kIdxSlots == kTeams, "team t owns index slot t");
 
@@ -79,6 +80,7 @@ struct FusedShape {
   static constexpr int kRowsPer128 = kRowBytes >= 128 ? 1 : 128 / kRowBytes;
   static constexpr int kHPT = kCPT * EltTraits<Elt>::kVec;       // h_u entries per thread
   static_assert(kRowsPerStage <= kWin && kWin % kRowsPerStage == 0, "stage split");
+  static_assert(kRowsPerStage % (32 / kTPR) == 0, "a warp's rows lie in one stage");
   static_assert(kTPR >= 1 && kCPT >= 1 && kHPT <= 64, "row split");
 };
 
@@ -160,7 +162,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
     sm.thr = 0ull;
     for (uint32_t q = 0; q < S; q++) {
       mbar_init(&sm.full[q], 1);
-      mbar_init(&sm.empty[q], 1);
+      mbar_init(&sm.empty[q], Sh::kRowsPerStage * Sh::kTPR);  // every scorer visit of a row
     }
     for (int q = 0; q < kAccBufs; q++) {
       mbar_init(&sm.acc_full[q], kTeamThreads);
@@ -184,10 +186,16 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       for (uint32_t p = 0; p < (uint32_t)kPrefetch && p <= my_wins; p++)
         sm.wp[p][lane] = a.win_ptr[lane][w_begin + p];
     __syncwarp();
+    // win_ptr[lane][w_begin + j - 1 + kPrefetch], loaded one iteration ago: it
+    // is stored into the ring only now, so the load's latency is covered by a
+    // whole iteration instead of stalling the one that issued it
+    uint32_t pend_ptr = 0;
+    bool pend = false;
     for (uint32_t j = 0; j < my_wins && !stop; j++) {
-      uint32_t next_ptr = 0;  // win_ptr[lane][w_begin + j + kPrefetch], in flight
-      const bool pf = lane < kGroups && j + kPrefetch <= my_wins;
-      if (pf) next_ptr = a.win_ptr[lane][w_begin + j + kPrefetch];
+      if (pend) sm.wp[(j - 1) % kPrefetch][lane] = pend_ptr;  // the slot of window j - 1
+      __syncwarp();
+      pend = lane < kGroups && j + kPrefetch <= my_wins;
+      if (pend) pend_ptr = a.win_ptr[lane][w_begin + j + kPrefetch];
       const uint32_t w = w_begin + j;
       const uint32_t sl = j % kIdxSlots, use = j / kIdxSlots;
       // (a) index segments of window w into slot sl
@@ -275,7 +283,6 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       stop = __shfl_sync(0xffffffffu, stop, 0);
       seq = __shfl_sync(0xffffffffu, seq, 0);
       __syncwarp();
-      if (pf) sm.wp[(j + kPrefetch) % kPrefetch][lane] = next_ptr;  // slot of window j, now free
       __syncwarp();
     }
     if (stop && lane == 0) {
@@ -413,10 +420,6 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
     if (tid == 0) {
       uint32_t stop = *((volatile uint32_t *)&sm.abort);
       if (!stop && !mbar_wait_bounded(&sm.acc_full[b], apar, kWaitTimeoutNs)) stop = 1;
-      for (uint32_t q = 0; !stop && q < (uint32_t)Sh::kStagesPerWin; q++) {
-        const uint32_t seq = j * Sh::kStagesPerWin + q;
-        if (!mbar_wait_bounded(&sm.full[seq % S], (seq / S) & 1u, kWaitTimeoutNs)) stop = 1;
-      }
       if (stop && !*((volatile uint32_t *)&sm.abort)) {
         atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
         sm.abort = 1;
@@ -426,19 +429,25 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
     gsync();
     if (sm.stop_acc) break;
     mbar_try_wait(&sm.acc_full[b], apar);  // per-thread acquire
-#pragma unroll
-    for (uint32_t q = 0; q < (uint32_t)Sh::kStagesPerWin; q++) {
-      const uint32_t seq = j * Sh::kStagesPerWin + q;
-      mbar_try_wait(&sm.full[seq % S], (seq / S) & 1u);
-    }
     const uint32_t w = w_begin + j;
     const int *acc = sm.acc[b];
 #pragma unroll
     for (int ps = 0; ps < Sh::kPasses; ps++) {
       const uint32_t rw = ps * Sh::kRowsPerPass + prow;  // row within the window
       const uint32_t ad = w * kWin + rw;
-      const bool valid = ad < a.n_ads;
       const uint32_t seq = j * Sh::kStagesPerWin + rw / Sh::kRowsPerStage;
+      // Each warp's rows lie in one stage: wait for that stage only, and hand
+      // it back right after reading it, so the producer refills the ring while
+      // the rest of the window is still being scored.
+      bool staged = true;
+      if (lane == 0) staged = mbar_wait_bounded(&sm.full[seq % S], (seq / S) & 1u, kWaitTimeoutNs);
+      staged = __shfl_sync(0xffffffffu, staged, 0);
+      if (!staged && lane == 0) {
+        atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
+        sm.abort = 1;
+      }
+      if (staged) mbar_try_wait(&sm.full[seq % S], (seq / S) & 1u);  // per-thread acquire
+      const bool valid = staged && ad < a.n_ads;
       const uint8_t *row = stage0 + (size_t)(seq % S) * kStageBytes +
                            (size_t)(rw % Sh::kRowsPerStage) * Sh::kRowBytes;
       float2 dot2 = make_float2(0.f, 0.f);
@@ -455,6 +464,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
                               make_float2(f[e], f[e + 1]), dot2);
         }
       }
+      mbar_arrive(&sm.empty[seq % S]);  // this thread is done with the stage
       float dot = dot2.x + dot2.y;
 #pragma unroll
       for (int o = Sh::kTPR / 2; o >= 1; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
@@ -486,10 +496,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
         }
       }
     }
-    gsync();  // the window's stages and accumulator are fully read; appends visible
-    if (tid == 0)
-      for (uint32_t q = 0; q < (uint32_t)Sh::kStagesPerWin; q++)
-        mbar_arrive(&sm.empty[(j * Sh::kStagesPerWin + q) % S]);
+    gsync();  // the window's accumulator is fully read; appends visible
     for (int i = tid; i < kWin; i += kDotThreads) sm.acc[b][i] = 0;  // hand it back, zeroed
     mbar_arrive(&sm.acc_empty[b]);
     if (!ALL && sm.n + kWin > a.cap) {
@@ -576,12 +583,12 @@ static int launch_fused_t(const ebr_index *ix, FusedArgs a, int max_grid, cudaSt
   a.cap = ALL ? 0 : fused_cap(a.k);
   uint32_t slot_bytes = 0;
   const size_t fixed = fused_fixed_bytes(ix, D, a.cap, &slot_bytes);
-  if (fixed + 4 * (size_t)kStageBytes > kFusedSmemBudget) {
+  if (fixed + kMinStages * (size_t)kStageBytes > kFusedSmemBudget) {
     set_error("fused scan: k = %u with %u-byte window segments needs too much shared memory",
               a.k, ix->max_win_bytes);
     return EBR_EINVAL;
   }
-  uint32_t stages = 4;
+  uint32_t stages = kMinStages;
   while (stages < (uint32_t)kMaxStages &&
          fixed + (size_t)(stages + 1) * kStageBytes <= kFusedSmemBudget)
     stages++;
@@ -640,7 +647,7 @@ __global__ void k_absmax(const float *__restrict__ w, uint32_t n, uint32_t *__re
 bool fused_fits(const ebr_index *ix, uint32_t k) {
   uint32_t slot_bytes = 0;
   return ix->max_win_chunks <= (uint32_t)kMaxChunkTab && ix->max_keys_per_ad <= 65536u &&
-         fused_fixed_bytes(ix, ix->d, fused_cap(k), &slot_bytes) + 4 * (size_t)kStageBytes <=
+         fused_fixed_bytes(ix, ix->d, fused_cap(k), &slot_bytes) + kMinStages * (size_t)kStageBytes <=
              kFusedSmemBudget;
 }
 
