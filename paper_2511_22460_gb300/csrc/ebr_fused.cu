@@ -9,10 +9,12 @@
 // memory.
 //
 // One persistent CTA per SM, three warp roles:
-//   producer (1 warp): for every window, stages its compressed-list segments
-//       (keys and value bytes of all nine size groups) into one of two index
-//       slots, and its embedding rows into a ring of 16 KB stages, all by TMA
-//       bulk copies (cp.async.bulk + mbarrier, L2 evict-first);
+//   producers (2 warps, independent): one stages every window's
+//       compressed-list segments (keys and value bytes of all nine size
+//       groups) into a ring of index slots (two per decoder team when shared
+//       memory allows), the other streams its embedding rows into a ring of
+//       16 KB stages; all by TMA bulk copies (cp.async.bulk + mbarrier, L2
+//       evict-first);
 //   decoders (2 teams x 5 warps): each team takes every other window; warps
 //       walk the window's blocks in chunks of 32 work units of one size group,
 //       gather w^[key] and add it into one of four fixed-point accumulators
@@ -35,17 +37,18 @@ constexpr int kWin = 256;
 constexpr int kDotWarps = 8, kTeamWarps = 5, kTeams = 2;
 constexpr int kDotThreads = kDotWarps * 32;
 constexpr int kTeamThreads = kTeamWarps * 32;
-constexpr int kProducerWarp = kDotWarps + kTeams * kTeamWarps;
-constexpr int kFusedThreads = (kProducerWarp + 1) * 32;  // 608 (19 warps)
+constexpr int kIdxWarp = kDotWarps + kTeams * kTeamWarps;  // index producer
+constexpr int kEmbWarp = kIdxWarp + 1;                       // embedding producer
+constexpr int kFusedThreads = (kEmbWarp + 1) * 32;           // 640 (20 warps)
 constexpr int kAccBufs = 4;
-constexpr int kIdxSlots = kTeams;  // one per decoder team
+constexpr int kMaxIdxSlots = 2 * kTeams;  // two per decoder team when they fit
 constexpr int kStageBytes = 16384;
 constexpr int kMaxStages = 12;
 constexpr int kMinStages = 4;
 constexpr int kChunksInFlight = 8;  // decoder chunks of 32 units per warp per round
 constexpr int kMaxChunkTab = 512;  // chunk -> (group, chunk in group) table per team
 static_assert(kWin % kDotThreads == 0, "scorer threads split the window evenly");
-static_assert(kIdxSlots == kTeams, "team t owns index slot t");
+static_assert(kMaxIdxSlots % kTeams == 0, "window j uses slot j % slots, team j % kTeams");
 
 struct FusedArgs {
   const void *emb;
@@ -56,7 +59,7 @@ struct FusedArgs {
   const uint8_t *wvals[kGroups];
   const uint32_t *win_ptr[kGroups];
   const uint64_t *filter;
-  uint32_t n_ads, n_win, k, cap, stages, slot_bytes;
+  uint32_t n_ads, n_win, k, cap, stages, slot_bytes, idx_slots;
   uint64_t *cand_out;
   Ctrl *ctrl;
   float *all_out;   // score-all mode
@@ -119,12 +122,12 @@ struct FusedSmem {
   int acc[kAccBufs][kWin];
   uint32_t wp[kPrefetch][kGroups];  // producer's ring of window offsets
   uint32_t ctab[kTeams][kMaxChunkTab];  // per team: group << 16 | chunk within the group
-  SlotDesc desc[kIdxSlots];
+  SlotDesc desc[kMaxIdxSlots];
   uint32_t hist[256];
   uint32_t misc[8];
   uint32_t wtot[2][kDotWarps];
   uint64_t full[kMaxStages], empty[kMaxStages], acc_full[kAccBufs], acc_empty[kAccBufs];
-  uint64_t idx_full[kIdxSlots], idx_empty[kIdxSlots];
+  uint64_t idx_full[kMaxIdxSlots], idx_empty[kMaxIdxSlots];
   unsigned long long thr;
   uint32_t n, abort;
   // group-uniform stop decisions: written by one thread before a barrier of
@@ -144,7 +147,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
   const uint32_t S = a.stages;
   uint8_t *stage0 = smem;
   uint8_t *slot0 = smem + (size_t)S * kStageBytes;
-  float *s_h = reinterpret_cast<float *>(slot0 + (size_t)kIdxSlots * a.slot_bytes);
+  float *s_h = reinterpret_cast<float *>(slot0 + (size_t)a.idx_slots * a.slot_bytes);
   uint64_t *cand = reinterpret_cast<uint64_t *>(s_h + D);
 
   // a contiguous, balanced range of windows per CTA: one sequential stream per SM
@@ -168,7 +171,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       mbar_init(&sm.acc_full[q], kTeamThreads);
       mbar_init(&sm.acc_empty[q], kDotThreads);
     }
-    for (int q = 0; q < kIdxSlots; q++) {
+    for (int q = 0; q < kMaxIdxSlots; q++) {
       mbar_init(&sm.idx_full[q], 1);
       mbar_init(&sm.idx_empty[q], 1);
     }
@@ -176,12 +179,14 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
   }
   __syncthreads();
 
-  if (warp == kProducerWarp) {
-    // ---------------------------------------------------------- producer
+  if (warp == kIdxWarp) {
+    // ------------------------------------------------- index producer
+    // Lane g (< 9) stages window w's segment of size group g (its block keys
+    // and value bytes) into index slot j % idx_slots as soon as the decoder
+    // team that used the slot last has handed it back.
     const uint64_t pol = l2_evict_first_policy();
-    uint32_t seq = 0;  // embedding stages issued
+    const uint32_t NI = a.idx_slots;
     bool stop = false;
-    // window offsets win_ptr[g][w], w = w_begin .. w_end, read kPrefetch windows ahead
     if (lane < kGroups)
       for (uint32_t p = 0; p < (uint32_t)kPrefetch && p <= my_wins; p++)
         sm.wp[p][lane] = a.win_ptr[lane][w_begin + p];
@@ -191,14 +196,14 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
     // whole iteration instead of stalling the one that issued it
     uint32_t pend_ptr = 0;
     bool pend = false;
+    uint32_t issued = 0;
     for (uint32_t j = 0; j < my_wins && !stop; j++) {
       if (pend) sm.wp[(j - 1) % kPrefetch][lane] = pend_ptr;  // the slot of window j - 1
       __syncwarp();
       pend = lane < kGroups && j + kPrefetch <= my_wins;
       if (pend) pend_ptr = a.win_ptr[lane][w_begin + j + kPrefetch];
       const uint32_t w = w_begin + j;
-      const uint32_t sl = j % kIdxSlots, use = j / kIdxSlots;
-      // (a) index segments of window w into slot sl
+      const uint32_t sl = j % NI, use = j / NI;
       if (use > 0) {
         bool ok = true;
         if (lane == 0) ok = mbar_wait_bounded(&sm.idx_empty[sl], (use - 1) & 1u, kWaitTimeoutNs);
@@ -256,45 +261,55 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
         bulk_g2s_hint(slot + cursor + (uint32_t)(k1 - k0), a.wvals[g] + v0, (uint32_t)(v1 - v0),
                       &sm.idx_full[sl], pol);
       }
-      // (b) the window's embedding rows into the stage ring
-      if (lane == 0) {
-        for (uint32_t q = 0; q < (uint32_t)Sh::kStagesPerWin; q++, seq++) {
-          const uint32_t s = seq % S;
-          if (seq >= S && !mbar_wait_bounded(&sm.empty[s], ((seq / S) - 1) & 1u, kWaitTimeoutNs)) {
-            atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
-            sm.abort = 1;
-            stop = true;
-            break;
-          }
-          const uint32_t row0 = w * kWin + q * Sh::kRowsPerStage;
-          const uint32_t rows =
-              row0 < a.n_ads ? min((uint32_t)Sh::kRowsPerStage, a.n_ads - row0) : 0u;
-          if (rows) {
-            mbar_arrive_expect_tx(&sm.full[s], rows * Sh::kRowBytes);
-            bulk_g2s_hint(stage0 + (size_t)s * kStageBytes,
-                          reinterpret_cast<const uint8_t *>(a.emb) +
-                              (uint64_t)row0 * Sh::kRowBytes,
-                          rows * Sh::kRowBytes, &sm.full[s], pol);
-          } else {
-            mbar_arrive(&sm.full[s]);
-          }
-        }
-      }
-      stop = __shfl_sync(0xffffffffu, stop, 0);
-      seq = __shfl_sync(0xffffffffu, seq, 0);
-      __syncwarp();
+      issued = j + 1;
       __syncwarp();
     }
     if (stop && lane == 0) {
-      // stopped early: wait (bounded) for the copies still in flight
-      for (uint32_t q = (seq > S ? seq - S : 0); q < seq; q++)
-        mbar_wait_bounded(&sm.full[q % S], (q / S) & 1u, kWaitTimeoutNs / 4);
-      for (int q = 0; q < kIdxSlots; q++) {
-        // the latest phase of each slot: wait for it, whatever its parity
-        mbar_wait_bounded(&sm.idx_full[q], 0, kWaitTimeoutNs / 8);
-        mbar_wait_bounded(&sm.idx_full[q], 1, kWaitTimeoutNs / 8);
+      // stopped early: wait (bounded) for the index copies still in flight
+      for (uint32_t j = issued > NI ? issued - NI : 0; j < issued; j++)
+        mbar_wait_bounded(&sm.idx_full[j % NI], (j / NI) & 1u, kWaitTimeoutNs / 4);
+    }
+    return;
+  }
+
+  if (warp == kEmbWarp) {
+    // --------------------------------------------- embedding producer
+    // Lane 0 streams every window's embedding rows into the stage ring.
+    if (lane != 0) return;
+    const uint64_t pol = l2_evict_first_policy();
+    uint32_t seq = 0;  // stages issued
+    bool stop = false;
+    for (uint32_t j = 0; j < my_wins && !stop; j++) {
+      const uint32_t w = w_begin + j;
+      for (uint32_t q = 0; q < (uint32_t)Sh::kStagesPerWin; q++) {
+        const uint32_t s = seq % S;
+        if (seq >= S && !mbar_wait_bounded(&sm.empty[s], ((seq / S) - 1) & 1u, kWaitTimeoutNs)) {
+          atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
+          sm.abort = 1;
+          stop = true;
+          break;
+        }
+        if (*((volatile uint32_t *)&sm.abort)) {
+          stop = true;
+          break;
+        }
+        const uint32_t row0 = w * kWin + q * Sh::kRowsPerStage;
+        const uint32_t rows =
+            row0 < a.n_ads ? min((uint32_t)Sh::kRowsPerStage, a.n_ads - row0) : 0u;
+        if (rows) {
+          mbar_arrive_expect_tx(&sm.full[s], rows * Sh::kRowBytes);
+          bulk_g2s_hint(stage0 + (size_t)s * kStageBytes,
+                        reinterpret_cast<const uint8_t *>(a.emb) + (uint64_t)row0 * Sh::kRowBytes,
+                        rows * Sh::kRowBytes, &sm.full[s], pol);
+        } else {
+          mbar_arrive(&sm.full[s]);
+        }
+        seq++;
       }
     }
+    if (stop)  // stopped early: wait (bounded) for the stage copies still in flight
+      for (uint32_t q = (seq > S ? seq - S : 0); q < seq; q++)
+        mbar_wait_bounded(&sm.full[q % S], (q / S) & 1u, kWaitTimeoutNs / 4);
     return;
   }
 
@@ -303,15 +318,16 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
     const int team = (warp - kDotWarps) / kTeamWarps;
     const int tw = (warp - kDotWarps) % kTeamWarps;  // warp within the team
     const int tt = tid - kDotThreads - team * kTeamThreads;
-    const uint8_t *slot = slot0 + (size_t)team * a.slot_bytes;
     for (uint32_t j = team; j < my_wins; j += kTeams) {
-      const uint32_t b = j % kAccBufs, use = j / kAccBufs, iuse = j / kIdxSlots;
+      const uint32_t b = j % kAccBufs, use = j / kAccBufs;
+      const uint32_t sl = j % a.idx_slots, iuse = j / a.idx_slots;
+      const uint8_t *slot = slot0 + (size_t)sl * a.slot_bytes;
       if (tt == 0) {
         uint32_t stop = *((volatile uint32_t *)&sm.abort);
         if (!stop && use > 0 &&
             !mbar_wait_bounded(&sm.acc_empty[b], (use - 1) & 1u, kWaitTimeoutNs))
           stop = 1;
-        if (!stop && !mbar_wait_bounded(&sm.idx_full[team], iuse & 1u, kWaitTimeoutNs)) stop = 1;
+        if (!stop && !mbar_wait_bounded(&sm.idx_full[sl], iuse & 1u, kWaitTimeoutNs)) stop = 1;
         if (stop && !*((volatile uint32_t *)&sm.abort)) {
           atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
           sm.abort = 1;
@@ -321,8 +337,8 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       named_sync(2 + team, kTeamThreads);
       if (sm.team_stop[team]) break;
       if (use > 0) mbar_try_wait(&sm.acc_empty[b], (use - 1) & 1u);  // per-thread acquire
-      mbar_try_wait(&sm.idx_full[team], iuse & 1u);
-      const SlotDesc &dsc = sm.desc[team];
+      mbar_try_wait(&sm.idx_full[sl], iuse & 1u);
+      const SlotDesc &dsc = sm.desc[sl];
       // chunk prefix over the groups (chunks of 32 units never straddle groups)
       // and a chunk -> group table, one entry per thread, so the hot loop
       // below needs no search
@@ -396,7 +412,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
         }
       }
       named_sync(2 + team, kTeamThreads);  // every read of the slot is done
-      if (tt == 0) mbar_arrive(&sm.idx_empty[team]);
+      if (tt == 0) mbar_arrive(&sm.idx_empty[sl]);
       mbar_arrive(&sm.acc_full[b]);  // release: this thread's additions into acc[b]
     }
     return;
@@ -565,14 +581,14 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
 }
 
 // Shared memory the fused scan needs besides its stage ring.
-static size_t fused_fixed_bytes(const ebr_index *ix, uint32_t d, uint32_t cap,
+static size_t fused_fixed_bytes(const ebr_index *ix, uint32_t d, uint32_t cap, uint32_t slots,
                                 uint32_t *slot_bytes) {
   *slot_bytes = (ix->max_win_bytes + 127) / 128 * 128;
   if (*slot_bytes == 0) *slot_bytes = 128;
-  return (size_t)kIdxSlots * *slot_bytes + (size_t)d * 4 + (size_t)cap * 8;
+  return (size_t)slots * *slot_bytes + (size_t)d * 4 + (size_t)cap * 8;
 }
 
-constexpr size_t kFusedSmemBudget = 206 * 1024;  // dynamic part; the static part is ~18 KB
+constexpr size_t kFusedSmemBudget = 206 * 1024;  // dynamic part; the static part is ~15 KB
 
 static uint32_t fused_cap(uint32_t k) {
   return (std::max<uint32_t>(k, 1) + std::max<uint32_t>(k / 2, 1024) + 255) / 256 * 256;
@@ -582,7 +598,15 @@ template <typename Elt, int D, bool ALL>
 static int launch_fused_t(const ebr_index *ix, FusedArgs a, int max_grid, cudaStream_t st) {
   a.cap = ALL ? 0 : fused_cap(a.k);
   uint32_t slot_bytes = 0;
-  const size_t fixed = fused_fixed_bytes(ix, D, a.cap, &slot_bytes);
+  // two index slots per decoder team (the next window's segments arrive while
+  // the team decodes the current one) when that still leaves 8 stages
+  uint32_t slots = kMaxIdxSlots;
+  size_t fixed = fused_fixed_bytes(ix, D, a.cap, slots, &slot_bytes);
+  if (fixed + 8 * (size_t)kStageBytes > kFusedSmemBudget) {
+    slots = kTeams;
+    fixed = fused_fixed_bytes(ix, D, a.cap, slots, &slot_bytes);
+  }
+  a.idx_slots = slots;
   if (fixed + kMinStages * (size_t)kStageBytes > kFusedSmemBudget) {
     set_error("fused scan: k = %u with %u-byte window segments needs too much shared memory",
               a.k, ix->max_win_bytes);
@@ -647,7 +671,8 @@ __global__ void k_absmax(const float *__restrict__ w, uint32_t n, uint32_t *__re
 bool fused_fits(const ebr_index *ix, uint32_t k) {
   uint32_t slot_bytes = 0;
   return ix->max_win_chunks <= (uint32_t)kMaxChunkTab && ix->max_keys_per_ad <= 65536u &&
-         fused_fixed_bytes(ix, ix->d, fused_cap(k), &slot_bytes) + kMinStages * (size_t)kStageBytes <=
+         fused_fixed_bytes(ix, ix->d, fused_cap(k), kTeams, &slot_bytes) +
+                 kMinStages * (size_t)kStageBytes <=
              kFusedSmemBudget;
 }
 
