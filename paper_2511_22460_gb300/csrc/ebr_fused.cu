@@ -64,7 +64,7 @@ struct FusedArgs {
   Ctrl *ctrl;
   float *all_out;   // score-all mode
   float *wide_out;  // if set: the per-ad wide term is written here (FP32 rescoring needs it)
-  uint32_t *hist;   // [256 + 65536] candidate-score histogram (zeroed per request)
+  uint32_t *hist;   // [kCandBins + 1] candidate-score histogram + top bin (zeroed per request)
   const uint32_t *wmax_bits;  // max |w^| over the keys (FP32 bits), set by k_absmax
   uint32_t max_keys;          // most keys of one ad
 };
@@ -118,12 +118,50 @@ __device__ __forceinline__ int fix_exponent(uint32_t wmax_bits, uint32_t max_key
 }
 __device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(127 + e) << 23); }
 
+// Candidate-score histogram shared by all CTAs (for a global K-th bound):
+// bins are the top 11 bits of the order-preserving score key (sign, 8
+// exponent bits, 2 mantissa bits).  CTAs count in shared memory and add
+// their counts to the global histogram every kRefresh windows.
+constexpr int kCandBins = 2048;
+constexpr int kBinShift = 53;
+constexpr int kRefresh = 2;
+
+// Largest bin edge b << kBinShift with at least K candidates at or above it,
+// scanning the global histogram down from its highest bin to bin b_lo (a
+// bound already known); 0 if none.  Counts only grow, so racy snapshots give
+// a smaller, still valid, bound.  One full warp.
+__device__ __forceinline__ uint64_t hist_top_threshold(const uint32_t *gh, uint32_t b_lo,
+                                                       uint32_t K) {
+  const int lane = threadIdx.x & 31;
+  const int top = (int)min(__ldcg(gh + kCandBins), (uint32_t)kCandBins - 1u);
+  uint32_t run = 0;
+  for (int hi = top; hi >= (int)b_lo; hi -= 32) {
+    const int bin = hi - lane;
+    const uint32_t c = bin >= (int)b_lo ? __ldcg(gh + bin) : 0u;
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const uint32_t hit = __ballot_sync(0xffffffffu, run + incl >= K);
+    if (hit) {
+      const int src = __ffs(hit) - 1;
+      return (uint64_t)(hi - src) << kBinShift;
+    }
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  return 0ull;
+}
+
 struct FusedSmem {
   int acc[kAccBufs][kWin];
   uint32_t wp[kPrefetch][kGroups];  // producer's ring of window offsets
   uint32_t ctab[kTeams][kMaxChunkTab];  // per team: group << 16 | chunk within the group
   SlotDesc desc[kMaxIdxSlots];
   uint32_t hist[256];
+  uint32_t chist[kCandBins];  // this CTA's candidates per score bin since the last flush
+  uint32_t top_bin;           // highest bin this CTA has seen
   uint32_t misc[8];
   uint32_t wtot[2][kDotWarps];
   uint64_t full[kMaxStages], empty[kMaxStages], acc_full[kAccBufs], acc_empty[kAccBufs];
@@ -159,10 +197,12 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
   const int fx_e = fix_exponent(*a.wmax_bits, a.max_keys);
   const float fx_scale = pow2f(fx_e), fx_unit = pow2f(-fx_e);
   for (int i = tid; i < D; i += kFusedThreads) s_h[i] = a.h_u[i];
+  for (int i = tid; i < kCandBins; i += kFusedThreads) sm.chist[i] = 0;
   if (tid == 0) {
     sm.n = 0;
     sm.abort = 0;
     sm.thr = 0ull;
+    sm.top_bin = 0;
     for (uint32_t q = 0; q < S; q++) {
       mbar_init(&sm.full[q], 1);
       mbar_init(&sm.empty[q], Sh::kRowsPerStage * Sh::kTPR);  // every scorer visit of a row
@@ -506,9 +546,9 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
         const uint32_t pos = warp_append(keep, &sm.n);
         if (keep) {
           cand[pos] = kk;
-          const uint32_t o = (uint32_t)(kk >> 32);
-          atomicAdd(a.hist + 256 + (o >> 16), 1u);
-          atomicAdd(a.hist + (o >> 24), 1u);
+          const uint32_t bin = (uint32_t)(kk >> kBinShift);
+          atomicAdd(&sm.chist[bin], 1u);
+          if (bin > sm.top_bin) atomicMax(&sm.top_bin, bin);
         }
       }
     }
@@ -546,11 +586,24 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
         sm.thr = max((unsigned long long)T, max(g, (unsigned long long)sm.thr));
       }
       gsync();
-    } else if (!ALL && warp == 0 && (j & 7) == 7) {
-      const unsigned long long h = hist_threshold(a.hist, a.hist + 256, a.k);
-      if (lane == 0) {
-        const unsigned long long g = *((volatile unsigned long long *)&a.ctrl->thr);
-        sm.thr = max(sm.thr, max(g, h));
+    } else if (!ALL && (j % kRefresh) == kRefresh - 1) {
+      // add this CTA's counts to the global histogram (no appends run until
+      // the next window's barrier), then warp 0 raises the threshold
+      for (int i = tid; i < kCandBins; i += kDotThreads) {
+        const uint32_t c = sm.chist[i];
+        if (c) {
+          atomicAdd(a.hist + i, c);
+          sm.chist[i] = 0;
+        }
+      }
+      if (tid == 0) atomicMax(a.hist + kCandBins, sm.top_bin);
+      if (warp == 0) {
+        const unsigned long long h =
+            hist_top_threshold(a.hist, (uint32_t)(sm.thr >> kBinShift), a.k);
+        if (lane == 0) {
+          const unsigned long long g = *((volatile unsigned long long *)&a.ctrl->thr);
+          sm.thr = max(sm.thr, max(g, h));
+        }
       }
     }
   }
@@ -561,8 +614,14 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
   const uint32_t n = sm.n;
   uint64_t T = 0;
   if (n > a.k) T = group_radix_select<kDotThreads>(cand, n, a.k, sm.hist, sm.misc, tid, gsync);
+  for (int i = tid; i < kCandBins; i += kDotThreads) {  // last counts
+    const uint32_t c = sm.chist[i];
+    if (c) atomicAdd(a.hist + i, c);
+  }
+  if (tid == 0) atomicMax(a.hist + kCandBins, sm.top_bin);
   if (warp == 0) {
-    const unsigned long long h = hist_threshold(a.hist, a.hist + 256, a.k);
+    const unsigned long long h =
+        hist_top_threshold(a.hist, (uint32_t)(sm.thr >> kBinShift), a.k);
     if (lane == 0) {
       const unsigned long long g = *((volatile unsigned long long *)&a.ctrl->thr);
       sm.thr = max(max((unsigned long long)T, (unsigned long long)sm.thr), max(g, h));
@@ -588,7 +647,7 @@ static size_t fused_fixed_bytes(const ebr_index *ix, uint32_t d, uint32_t cap, u
   return (size_t)slots * *slot_bytes + (size_t)d * 4 + (size_t)cap * 8;
 }
 
-constexpr size_t kFusedSmemBudget = 206 * 1024;  // dynamic part; the static part is ~15 KB
+constexpr size_t kFusedSmemBudget = 204 * 1024;  // dynamic part; the static part is ~19 KB
 
 static uint32_t fused_cap(uint32_t k) {
   return (std::max<uint32_t>(k, 1) + std::max<uint32_t>(k / 2, 1024) + 255) / 256 * 256;

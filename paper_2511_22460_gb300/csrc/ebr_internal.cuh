@@ -167,7 +167,7 @@ int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
                  float *all_out, float *wide_out, uint32_t *hist, int max_grid,
                  cudaStream_t st);
 bool fused_fits(const ebr_index *ix, uint32_t k);
-constexpr size_t kHistWords = 256 + 65536;  // candidate-score histogram (coarse + fine)
+constexpr size_t kHistWords = 4096;  // candidate-score histogram of the fused scan (2048 bins + top bin)
 // Launchers implemented in ebr_query.cu, used by the serving loop.
 int query_one(const ebr_index *ix, const ebr_cross *cross, const ebr_query &q, uint32_t *ids,
               float *scores, uint32_t kmax, cudaStream_t st);
