@@ -302,6 +302,16 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
                       &sm.idx_full[sl], pol);
       }
       issued = j + 1;
+      if (!ALL && (j % kRefresh) == kRefresh - 1) {
+        // raise this CTA's running threshold from the global candidate
+        // histogram and the other CTAs' selections (off the scorers' path)
+        const unsigned long long h =
+            hist_top_threshold(a.hist, (uint32_t)(sm.thr >> kBinShift), a.k);
+        if (lane == 0) {
+          const unsigned long long g = *((volatile unsigned long long *)&a.ctrl->thr);
+          atomicMax(&sm.thr, max(g, h));
+        }
+      }
       __syncwarp();
     }
     if (stop && lane == 0) {
@@ -583,12 +593,12 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       if (tid == 0) {
         sm.n = kept;
         const unsigned long long g = atomicMax(&a.ctrl->thr, (unsigned long long)T);
-        sm.thr = max((unsigned long long)T, max(g, (unsigned long long)sm.thr));
+        atomicMax(&sm.thr, max((unsigned long long)T, g));
       }
       gsync();
     } else if (!ALL && (j % kRefresh) == kRefresh - 1) {
       // add this CTA's counts to the global histogram (no appends run until
-      // the next window's barrier), then warp 0 raises the threshold
+      // the next window's barrier); the index producer reads it back
       for (int i = tid; i < kCandBins; i += kDotThreads) {
         const uint32_t c = sm.chist[i];
         if (c) {
@@ -597,14 +607,6 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
         }
       }
       if (tid == 0) atomicMax(a.hist + kCandBins, sm.top_bin);
-      if (warp == 0) {
-        const unsigned long long h =
-            hist_top_threshold(a.hist, (uint32_t)(sm.thr >> kBinShift), a.k);
-        if (lane == 0) {
-          const unsigned long long g = *((volatile unsigned long long *)&a.ctrl->thr);
-          sm.thr = max(sm.thr, max(g, h));
-        }
-      }
     }
   }
   if (ALL) return;
