@@ -262,7 +262,7 @@ def run_gpu(args, rank, world, local_rank):
     return out
 
 
-KERNEL_REV = "fused-v1"
+KERNEL_REV = "fused-v2"
 
 # FP32 add throughput of the CUDA cores: 152 SMs x 128 FP32 lanes x 2.07 GHz
 ALU_ADD_PEAK_T = 152 * 128 * 2.07e9 / 1e12

@@ -252,6 +252,16 @@ int ebr_quantize(const float *x, uint64_t n, ebr_dtype dtype, void *out, void *s
 int ebr_debug_gemm_bf16(const uint16_t *A, uint32_t n, const uint16_t *U, uint32_t B, uint32_t d,
                         float *out, void *stream);
 
+/*
+ * Failure-detection check (no paper counterpart): launches one CTA whose
+ * thread waits, with the library's bounded-wait routine, on an mbarrier that
+ * nothing ever arrives on, giving up after timeout_us microseconds (1 .. 10^6).
+ * Returns EBR_ETIMEDOUT when the wait ran out and was reported through the
+ * device flag word, as every bounded wait in the library reports it; the CUDA
+ * context stays usable.  Synchronous.
+ */
+int ebr_debug_wait_timeout(uint32_t timeout_us, void *stream);
+
 /* ------------------------------------------------------- no-allocation form */
 /*
  * Allocation-free scan + top-K.  The paper has no counterpart: this entry

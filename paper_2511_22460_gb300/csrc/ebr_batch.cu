@@ -158,6 +158,43 @@ extern "C" int ebr_debug_gemm_bf16(const uint16_t *A, uint32_t n, const uint16_t
   return check_device_flags(hf, "ebr_debug_gemm_bf16");
 }
 
+namespace ebr {
+
+// A wait nobody ends: the bounded-wait path must give up and flag it.
+__global__ void k_wait_timeout(uint64_t timeout_ns, uint32_t *flags) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, timeout_ns))
+    atomicOr(flags, DEVERR_TIMEOUT);
+  __syncthreads();
+}
+
+}  // namespace ebr
+
+extern "C" int ebr_debug_wait_timeout(uint32_t timeout_us, void *stream) {
+  using namespace ebr;
+  clear_error();
+  if (timeout_us == 0 || timeout_us > 1000000u) {
+    set_error("ebr_debug_wait_timeout: timeout_us must be 1 .. 10^6");
+    return EBR_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t *flags = nullptr;
+  EBR_CUDA_TRY(cudaMallocAsync((void **)&flags, 4, st));
+  EBR_CUDA_TRY(cudaMemsetAsync(flags, 0, 4, st));
+  k_wait_timeout<<<1, 32, 0, st>>>((uint64_t)timeout_us * 1000ull, flags);
+  EBR_CUDA_TRY(cudaGetLastError());
+  uint32_t hf = 0;
+  EBR_CUDA_TRY(cudaMemcpyAsync(&hf, flags, 4, cudaMemcpyDeviceToHost, st));
+  EBR_CUDA_TRY(cudaStreamSynchronize(st));
+  cudaFreeAsync(flags, st);
+  return check_device_flags(hf, "ebr_debug_wait_timeout");
+}
+
 // =====================================================================
 // Batched scan: B users against every ad, one pass over the inventory
 // =====================================================================

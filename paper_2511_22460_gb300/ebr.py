@@ -107,6 +107,7 @@ ebr_quantize = _sig("ebr_quantize", i32, [vp, u64, i32, vp, vp])
 ebr_scan_topk_noalloc = _sig("ebr_scan_topk_noalloc", i32,
                              [vp, u32, u32, vp, vp, vp, u32, vp, vp, i32, vp])
 ebr_debug_gemm_bf16 = _sig("ebr_debug_gemm_bf16", i32, [vp, u32, vp, u32, u32, vp, vp])
+ebr_debug_wait_timeout = _sig("ebr_debug_wait_timeout", i32, [u32, vp])
 ebr_profile_enable = _sig("ebr_profile_enable", i32, [vp, i32])
 ebr_profile_read = _sig("ebr_profile_read", i32, [vp, C.POINTER(Profile)])
 ebr_server_create = _sig("ebr_server_create", i32, [vp, vp, vp, C.POINTER(vp)])
@@ -319,6 +320,11 @@ def scan_topk_noalloc(emb, h_u, wide, filt, k, out_ids, out_scores, device=0, st
     _check(ebr_scan_topk_noalloc(ptr(emb), int(emb.shape[0]), int(emb.shape[1]), ptr(h_u),
                                  ptr(wide), ptr(filt), int(k), ptr(out_ids), ptr(out_scores),
                                  device, stream_ptr(stream)), "ebr_scan_topk_noalloc")
+
+
+def debug_wait_timeout(timeout_us, stream=None):
+    """Status of a device wait that nothing ends (EBR_ETIMEDOUT expected)."""
+    return ebr_debug_wait_timeout(int(timeout_us), stream_ptr(stream))
 
 
 def debug_gemm_bf16(A, U, out, stream=None):

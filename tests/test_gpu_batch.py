@@ -24,3 +24,15 @@ def test_tcgen05_gemm_matches_fp64(n, B, d):
     mag = A.double().abs() @ U.double().abs().T
     err = (out.cpu().double() - ref).abs()
     assert torch.all(err <= 1e-6 * mag + 1e-30), float((err / (mag + 1e-30)).max())
+
+
+def test_bounded_wait_gives_up_and_reports_timeout():
+    """A device wait that nothing ends returns EBR_ETIMEDOUT after its limit;
+    the context stays usable (the tensor-core check runs right after)."""
+    import time
+    t0 = time.perf_counter()
+    rc = ebr.debug_wait_timeout(20_000)  # 20 ms
+    assert rc == ebr.EBR_ETIMEDOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert ebr.debug_wait_timeout(0) == ebr.EBR_EINVAL
+    test_tcgen05_gemm_matches_fp64(1000, 64, 64)
