@@ -862,7 +862,7 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
     EBR_TRY(launch_fused(ix, q.h_u, q_w, q.filter, kscan, (uint64_t *)w.cand.p, ctrl, nullptr,
                          quant ? (float *)w.wide.p : nullptr, (uint32_t *)w.hist.p,
                          ix->num_sms * kMaxCtasPerSm, st));
-    ix->launches += 1;
+    ix->launches += 2;  // k_absmax + k_fused_window
   } else {
     EBR_TRY(run_wide(ix, q_key, q_w, n_q, ctrl, st));
     if (n_q) {
