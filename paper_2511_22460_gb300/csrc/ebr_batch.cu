@@ -204,14 +204,14 @@ extern "C" int ebr_debug_wait_timeout(uint32_t timeout_us, void *stream) {
 //   MMA warp        -- tcgen05.mma with the users as the M side and the
 //                      window's ads as N = 256: deep[user][ad] (Eq. 1) lands
 //                      in TMEM with one user per TMEM lane;
-//   list warps (4)  -- walk the window's blocks in the window-major view of
+//   list warps (2)  -- walk the window's blocks in the window-major view of
 //                      the compressed list and lay out, per run of 32 ads, a
 //                      key table T[r][i] = r-th key of ad i (the window's
 //                      slice of L, transposed; short ads padded with a zero
 //                      row of w^T);
 //   epilogue (8)    -- thread = user (its TMEM lane), runs of 32 ads per
 //                      warp: wide[i] += w^T[T[r][i]][user] for every row r
-//                      (32 independent coalesced 128-byte loads per step,
+//                      (64 independent coalesced 128-byte loads per step,
 //                      accumulators in registers), added to the 32 deep
 //                      scores of one TMEM load, filtered, and each user's
 //                      candidates above its running threshold go to this
@@ -222,11 +222,12 @@ extern "C" int ebr_debug_wait_timeout(uint32_t timeout_us, void *stream) {
 namespace ebr {
 
 constexpr int kBWin = 256;
-constexpr int kEpiWarps = 8, kListWarps = 4;
+constexpr int kEpiWarps = 8, kListWarps = 2;
 constexpr int kEpiThreads = kEpiWarps * 32, kListThreads = kListWarps * 32;
 constexpr int kMmaWarp = kEpiWarps + kListWarps, kProdWarpB = kMmaWarp + 1;
-constexpr int kBatchThreads = (kProdWarpB + 1) * 32;  // 448
+constexpr int kBatchThreads = (kProdWarpB + 1) * 32;  // 384
 constexpr int kMaxUsers = 256;
+static_assert(kBWin % (kListWarps * 32) == 0, "list threads split the window's ads evenly");
 // List buffer: run_off[8], run_rows[8], fill[256], then the run tables.
 constexpr uint32_t kListHdr = 8 + 8 + kBWin;
 constexpr uint32_t kMaxBatchKeysPerAd = 64;  // longest key list the batched tables hold
@@ -516,34 +517,40 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
       uint32_t *fill = run_off + 16;
       uint32_t *tab = run_off + kListHdr;
       const uint32_t w = w_begin + j;
-      // rows of each run = most keys of its 32 ads; thread lt owns ads lt, lt + 128
-      uint32_t nk[2];
+      // rows of each run = most keys of its 32 ads; thread lt owns ads
+      // lt, lt + kListThreads, ... (whole warps per run of 32 ads)
+      constexpr int kPer = kBWin / kListThreads;
+      uint32_t nk[kPer];
 #pragma unroll
-      for (int h = 0; h < 2; h++) {
-        const uint32_t ad = w * kBWin + lt + 128 * h;
+      for (int h = 0; h < kPer; h++) {
+        const uint32_t al = lt + kListThreads * h;
+        const uint32_t ad = w * kBWin + al;
         nk[h] = ad < a.n_ads ? (uint32_t)__ldg(a.ad_nkeys + ad) : 0u;
-        fill[lt + 128 * h] = 0;
+        fill[al] = 0;
         uint32_t mx = nk[h];
 #pragma unroll
         for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) run_rows[warp - kEpiWarps + 4 * h] = mx;
+        if (lane == 0) run_rows[al >> 5] = mx;
       }
       named_sync(2, kListThreads);
-      uint32_t ro[2], rr[2];
+      uint32_t ro[kPer], rr[kPer];
       {
         uint32_t acc = 0;
-        const uint32_t r0 = (lt >> 5), r1 = r0 + 4;
         for (uint32_t r = 0; r < 8; r++) {
           const uint32_t rows = run_rows[r];
-          if (r == r0) { ro[0] = acc; rr[0] = rows; }
-          if (r == r1) { ro[1] = acc; rr[1] = rows; }
+#pragma unroll
+          for (int h = 0; h < kPer; h++)
+            if (r == ((lt + kListThreads * h) >> 5)) {
+              ro[h] = acc;
+              rr[h] = rows;
+            }
           if (lt == 0) run_off[r] = acc;
           acc += rows * 32u;
         }
       }
       // padding entries (rows nk .. rows-1) point at the zero row
 #pragma unroll
-      for (int h = 0; h < 2; h++)
+      for (int h = 0; h < kPer; h++)
         for (uint32_t r = nk[h]; r < rr[h]; r++) {
           const uint32_t pos = ro[h] + r * 32u + (uint32_t)lane;
           if (pos < a.list_cap) tab[pos] = a.zero_row;
@@ -609,7 +616,29 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
         float acc[32];
 #pragma unroll
         for (int i = 0; i < 32; i++) acc[i] = 0.f;
-        for (uint32_t r = 0; r < rows; r++) {
+        uint32_t r = 0;
+        for (; r + 2 <= rows; r += 2) {  // two rows: 64 independent loads in flight
+          float v0[32], v1[32];
+#pragma unroll
+          for (int i4 = 0; i4 < 8; i4++) {
+            const uint4 k = t4[r * 8 + i4];
+            v0[4 * i4 + 0] = __ldg(wcol + k.x);
+            v0[4 * i4 + 1] = __ldg(wcol + k.y);
+            v0[4 * i4 + 2] = __ldg(wcol + k.z);
+            v0[4 * i4 + 3] = __ldg(wcol + k.w);
+          }
+#pragma unroll
+          for (int i4 = 0; i4 < 8; i4++) {
+            const uint4 k = t4[(r + 1) * 8 + i4];
+            v1[4 * i4 + 0] = __ldg(wcol + k.x);
+            v1[4 * i4 + 1] = __ldg(wcol + k.y);
+            v1[4 * i4 + 2] = __ldg(wcol + k.z);
+            v1[4 * i4 + 3] = __ldg(wcol + k.w);
+          }
+#pragma unroll
+          for (int i = 0; i < 32; i++) acc[i] += v0[i] + v1[i];
+        }
+        if (r < rows) {
 #pragma unroll
           for (int i4 = 0; i4 < 8; i4++) {
             const uint4 k = t4[r * 8 + i4];
