@@ -743,7 +743,7 @@ bool fused_fits(const ebr_index *ix, uint32_t k) {
 int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
                  const uint64_t *filter, uint32_t k, uint64_t *cand_out, Ctrl *ctrl,
                  float *all_out, float *wide_out, uint32_t *hist, int max_grid,
-                 cudaStream_t st) {
+                 cudaStream_t st, bool wmax_ready) {
   FusedArgs a;
   memset(&a, 0, sizeof(a));
   a.emb = ix->dtype == EBR_F32 ? ix->emb_f32.p : ix->emb_q.p;
@@ -765,12 +765,15 @@ int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
   a.wide_out = wide_out;
   a.hist = hist;
   a.max_keys = std::max<uint32_t>(ix->max_keys_per_ad, 1);
-  // max |w^| for the accumulators' fixed-point scale (non-finite weights are flagged)
+  // max |w^| for the accumulators' fixed-point scale (non-finite weights are
+  // flagged); the query expansion computes it on the way when it made w^
   a.wmax_bits = &ctrl->pad;
-  EBR_CUDA_TRY(cudaMemsetAsync(&ctrl->pad, 0, sizeof(uint32_t), st));
-  k_absmax<<<std::max<uint32_t>(1, std::min<uint32_t>(64, (ix->n_keys + 1023) / 1024)), 256, 0,
-             st>>>(w_hat, ix->n_keys, &ctrl->pad, &ctrl->flags);
-  EBR_CUDA_TRY(cudaGetLastError());
+  if (!wmax_ready) {
+    EBR_CUDA_TRY(cudaMemsetAsync(&ctrl->pad, 0, sizeof(uint32_t), st));
+    k_absmax<<<std::max<uint32_t>(1, std::min<uint32_t>(64, (ix->n_keys + 1023) / 1024)), 256, 0,
+               st>>>(w_hat, ix->n_keys, &ctrl->pad, &ctrl->flags);
+    EBR_CUDA_TRY(cudaGetLastError());
+  }
   if (all_out) {
     if (ix->dtype == EBR_F32) return launch_fused_d<float, true>(ix, a, max_grid, st);
     if (ix->dtype == EBR_BF16) return launch_fused_d<Bf16Tag, true>(ix, a, max_grid, st);

@@ -68,13 +68,36 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 
 // w_hat[b][key_off[j] + v] = sum over pairs p = (i, j) of w_p(user[b][i], v).
 // One thread per (request, key); the pairs of field j are summed in pair order.
+// The pair lists of the ad fields (and, for one request, the request's user
+// value of every pair) are staged in shared memory, so a thread's loop over
+// the pairs of its key issues only the weight gathers, independently of
+// each other.  With wmax set, the largest |w^| (FP32 bits) is max-reduced
+// into it (non-finite sums are flagged).
 __global__ void k_expand(CrossView cv, const uint32_t *__restrict__ users, uint32_t batch,
-                         float *__restrict__ w_hat, uint32_t *__restrict__ flags) {
-  extern __shared__ uint32_t s_off[];  // key_off[f_a + 1]
-  for (uint32_t j = threadIdx.x; j <= cv.f_a; j += blockDim.x) s_off[j] = cv.key_off[j];
+                         float *__restrict__ w_hat, uint32_t *__restrict__ flags,
+                         uint32_t *__restrict__ wmax) {
+  extern __shared__ uint32_t s_mem[];
+  uint32_t *s_off = s_mem;                    // key_off[f_a + 1]
+  uint32_t *s_ptr = s_off + cv.f_a + 1;       // pair_ptr[f_a + 1]
+  uint32_t *s_of = s_ptr + cv.f_a + 1;        // pair_of[n_pairs]
+  uint32_t *s_usr = s_of + cv.n_pairs;        // pair_user[n_pairs]
+  uint32_t *s_u = s_usr + cv.n_pairs;         // batch 1: u of each pair, or ~0u if out of range
+  for (uint32_t j = threadIdx.x; j <= cv.f_a; j += blockDim.x) {
+    s_off[j] = cv.key_off[j];
+    s_ptr[j] = cv.pair_ptr[j];
+  }
+  for (uint32_t q = threadIdx.x; q < cv.n_pairs; q += blockDim.x) {
+    s_of[q] = cv.pair_of[q];
+    const uint32_t i = cv.pair_user[q];
+    s_usr[q] = i;
+    if (batch == 1) {
+      const uint32_t u = users[i];
+      s_u[q] = u < cv.vocab_u[i] ? u : ~0u;
+    }
+  }
   __syncthreads();
   const uint64_t total = (uint64_t)batch * cv.n_keys;
-  uint32_t bad = 0;
+  uint32_t bad = 0, mx = 0;
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
        t += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t b = (uint32_t)(t / cv.n_keys), key = (uint32_t)(t % cv.n_keys);
@@ -86,24 +109,40 @@ __global__ void k_expand(CrossView cv, const uint32_t *__restrict__ users, uint3
     }
     const uint32_t j = lo, v = key - s_off[j];
     float acc = 0.f;
-    for (uint32_t q = cv.pair_ptr[j]; q < cv.pair_ptr[j + 1]; q++) {
-      const uint32_t p = cv.pair_of[q];
-      const uint32_t i = cv.pair_user[p];
-      uint32_t u = users[(uint64_t)b * cv.f_u + i];
-      if (u >= cv.vocab_u[i]) { bad |= DEVERR_BAD_USER; continue; }
+    const uint32_t q0 = s_ptr[j], q1 = s_ptr[j + 1];
+#pragma unroll 4
+    for (uint32_t q = q0; q < q1; q++) {
+      const uint32_t p = s_of[q];
+      uint32_t u;
+      if (batch == 1) {
+        u = s_u[p];
+      } else {
+        const uint32_t i = s_usr[p];
+        u = users[(uint64_t)b * cv.f_u + i];
+        if (u >= cv.vocab_u[i]) u = ~0u;
+      }
+      if (u == ~0u) { bad |= DEVERR_BAD_USER; continue; }
       float w;
       if (cv.hashed) {
         uint64_t x = ((uint64_t)p << 40) | ((uint64_t)u << 20) | (uint64_t)v;
-        w = cv.table[splitmix64(x) & ((1ull << cv.hash_bits) - 1ull)];
+        w = __ldg(cv.table + (splitmix64(x) & ((1ull << cv.hash_bits) - 1ull)));
       } else {
         uint64_t off = ((uint64_t)cv.w_hi[p] << 32) | cv.w_lo[p];
-        w = cv.table[off + (uint64_t)u * cv.vocab_a[j] + v];
+        w = __ldg(cv.table + off + (uint64_t)u * cv.vocab_a[j] + v);
       }
       acc += w;
     }
     w_hat[t] = acc;
+    mx = max(mx, __float_as_uint(acc) & 0x7FFFFFFFu);
   }
   if (bad) atomicOr(flags, bad);
+  if (wmax) {
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) {
+      if (mx >= 0x7F800000u) atomicOr(flags, DEVERR_RANGE);
+      atomicMax(wmax, mx >= 0x7F800000u ? 0u : mx);
+    }
+  }
 }
 
 // =====================================================================
@@ -790,11 +829,19 @@ int expand_transposed(const ebr_cross *c, const uint32_t *users, uint32_t batch,
 }
 
 static int expand_into(const ebr_cross *c, const uint32_t *users, uint32_t batch, float *w_hat,
-                       uint32_t *flags, cudaStream_t st) {
+                       uint32_t *flags, cudaStream_t st, uint32_t *wmax = nullptr) {
   CrossView cv = cross_view(c);
   const uint64_t total = (uint64_t)batch * cv.n_keys;
-  k_expand<<<launch_grid(total, 256, 65535), 256, (c->f_a + 1) * 4, st>>>(cv, users, batch,
-                                                                          w_hat, flags);
+  const size_t smem = ((size_t)2 * (c->f_a + 1) + 3 * (size_t)c->n_pairs) * 4;
+  if (smem > 48 * 1024)
+    EBR_CUDA_TRY(cudaFuncSetAttribute(k_expand, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)std::min<size_t>(smem, 200 * 1024)));
+  if (smem > 200 * 1024) {
+    set_error("query expansion: %u cross pairs exceed the staging area", c->n_pairs);
+    return EBR_EINVAL;
+  }
+  k_expand<<<launch_grid(total, 256, 65535), 256, smem, st>>>(cv, users, batch, w_hat, flags,
+                                                              wmax);
   EBR_CUDA_TRY(cudaGetLastError());
   return EBR_OK;
 }
@@ -844,7 +891,8 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
   const float *q_w = q.q_w;
   uint32_t n_q = q.n_q;
   if (q.user_vals) {
-    EBR_TRY(expand_into(cross, q.user_vals, 1, (float *)w.w_dense.p, &ctrl->flags, st));
+    EBR_TRY(expand_into(cross, q.user_vals, 1, (float *)w.w_dense.p, &ctrl->flags, st,
+                        &ctrl->pad));  // + max |w^| for the fused scan
     ix->launches += 1;
     q_key = nullptr;
     q_w = (const float *)w.w_dense.p;
@@ -859,10 +907,11 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
     // dense query: wide term decoded window by window inside the scan
     pm.mark(2, st);
     EBR_CUDA_TRY(cudaMemsetAsync(w.hist.p, 0, kHistWords * 4, st));
+    const bool wmax_ready = q.user_vals != nullptr;  // the expansion reduced max |w^|
     EBR_TRY(launch_fused(ix, q.h_u, q_w, q.filter, kscan, (uint64_t *)w.cand.p, ctrl, nullptr,
                          quant ? (float *)w.wide.p : nullptr, (uint32_t *)w.hist.p,
-                         ix->num_sms * kMaxCtasPerSm, st));
-    ix->launches += 2;  // k_absmax + k_fused_window
+                         ix->num_sms * kMaxCtasPerSm, st, wmax_ready));
+    ix->launches += wmax_ready ? 1 : 2;  // (+ k_absmax) k_fused_window
   } else {
     EBR_TRY(run_wide(ix, q_key, q_w, n_q, ctrl, st));
     if (n_q) {
