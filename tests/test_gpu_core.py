@@ -366,3 +366,42 @@ def test_window_view_is_a_permutation_of_the_blocks():
     check_scores(out_k.cpu().numpy(), ref, tol, "key-major")
     info = ix.info()
     assert info.window_view_bytes > 0
+
+
+@pytest.mark.parametrize("n", [9_000, 3_000])
+@pytest.mark.parametrize("flags", [0, ebr.QF_KEY_MAJOR], ids=["window_major", "key_major"])
+def test_full_blocks_of_256_ads(n, flags):
+    """Keys held by every ad give blocks of 256 slots (group 8, the only blocks
+    that span two decode chunks) in every full window; a ragged tail window
+    holds a smaller one.  Dense w^ over all keys, FP64 postings oracle."""
+    rng = np.random.default_rng(n)
+    d = 32
+    emb = (rng.standard_normal((n, d)) / np.sqrt(d)).astype(np.float32)
+    h_u = (rng.standard_normal(d) / np.sqrt(d)).astype(np.float32)
+    n_keys = 40
+    keys, ads = [], []
+    for k in range(2):  # keys 0, 1: every ad
+        keys.append(np.full(n, k, np.uint32))
+        ads.append(np.arange(n, dtype=np.uint32))
+    for k in range(2, n_keys):  # the rest: random subsets of mixed density
+        m = rng.random(n) < rng.uniform(0.001, 0.9)
+        keys.append(np.full(int(m.sum()), k, np.uint32))
+        ads.append(np.nonzero(m)[0].astype(np.uint32))
+    pk, pa = np.concatenate(keys), np.concatenate(ads)
+    perm = rng.permutation(pk.size)
+    pk, pa = pk[perm], pa[perm]
+    ix = ebr.build_index(n, n_keys, pk, pa, emb)
+    assert ix.info().n_blocks[8] > 0
+    wh = rng.standard_normal(n_keys).astype(np.float32)
+    ref = oracle.scores_postings(h_u, emb, n_keys, pk, pa, np.arange(n_keys, dtype=np.uint32), wh)
+    out = torch.empty(n, dtype=torch.float32, device=DEV)
+    ebr.score_all(ix, None, ebr.Query(h_u=dev(h_u), k=1, q_w=dev(wh), flags=flags), out)
+    cond = np.abs(emb.astype(np.float64)) @ np.abs(h_u.astype(np.float64)) + np.bincount(
+        pa, weights=np.abs(wh[pk].astype(np.float64)), minlength=n)
+    check_scores(out.cpu().numpy(), ref, 1e-5 * np.maximum(np.abs(ref), cond))
+    k = 300
+    ids = torch.empty(k, dtype=torch.int32, device=DEV)
+    sc = torch.empty(k, dtype=torch.float32, device=DEV)
+    ebr.score_topk(ix, None, [ebr.Query(h_u=dev(h_u), k=k, q_w=dev(wh), flags=flags)], ids, sc)
+    check_topk(ids.cpu().numpy().view(np.uint32), sc.cpu().numpy(), ref,
+               1e-5 * np.maximum(np.abs(ref), cond), k)
