@@ -405,3 +405,30 @@ def test_full_blocks_of_256_ads(n, flags):
     ebr.score_topk(ix, None, [ebr.Query(h_u=dev(h_u), k=k, q_w=dev(wh), flags=flags)], ids, sc)
     check_topk(ids.cpu().numpy().view(np.uint32), sc.cpu().numpy(), ref,
                1e-5 * np.maximum(np.abs(ref), cond), k)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8e4m3"])
+def test_recall_before_and_after_rescoring(dtype, capsys):
+    """Recall@K of the quantised scan's own ranking (before the FP32 rescoring
+    of the top R*K) and of the returned top-K (after): the second must be 1.0;
+    the first is reported.  Precision-stress workload (32x32 fields, V=15)."""
+    n, k = 200_000, 500
+    w, post, ix, cross = _setup("fp8_10m", n, seed=6, dtype=dtype)
+    ref, tol = ref_scores(w, 0, post)
+    q = ebr.Query(h_u=dev(w.h_u[0]), k=k, user_vals=dev(w.users[0]))
+    allq = torch.empty(n, dtype=torch.float32, device=DEV)
+    ebr.score_all(ix, cross, q, allq)
+    s = allq.cpu().numpy().astype(np.float64)
+    pre_ids = np.lexsort((np.arange(n), -s))[:k]
+    pre = recall(pre_ids, ref, tol, k)
+    err = np.abs(s - ref) / np.maximum(np.abs(ref), 1e-30)
+    ids = torch.empty(k, dtype=torch.int32, device=DEV)
+    sc = torch.empty(k, dtype=torch.float32, device=DEV)
+    ebr.score_topk(ix, cross, [q], ids, sc)
+    got = ids.cpu().numpy().view(np.uint32)
+    post = recall(got, ref, tol, k)
+    with capsys.disabled():
+        print("\n[recall] %s %d ads K=%d: before rescoring %.4f (median rel. score error %.2e), "
+              "after %.4f" % (dtype, n, k, pre, float(np.median(err)), post))
+    assert post == 1.0
+    assert 0.0 < pre <= 1.0
