@@ -156,10 +156,25 @@ def run_gpu(args, rank, world, local_rank):
     sc = torch.empty(k, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    # a sparse query (--sparse-query N): N keys carry the weights, so the
+    # key-major traversal (Algorithm 2) serves it; else the user's fields
+    # expand to a dense w^ and the fused window-major scan serves it
+    sparse = args.sparse_query > 0
+    if sparse:
+        from paper_2511_22460_gb300.datagen import sparse_query
+        sq = [sparse_query(w, args.sparse_query, seed=b) for b in range(nreq)]
+        sq_d = [(torch.from_numpy(qk).to(dev), torch.from_numpy(qw).to(dev)) for qk, qw in sq]
+
+    def query(b, host=False):
+        if sparse:
+            qk, qw = sq[b] if host else sq_d[b]
+            return ebr.Query(h_u=(w.h_u[b].copy() if host else h_u[b]), k=k, q_key=qk, q_w=qw)
+        if host:
+            return ebr.Query(h_u=w.h_u[b].copy(), k=k, user_vals=w.users[b].copy())
+        return ebr.Query(h_u=h_u[b], k=k, user_vals=users[b])
+
     def step(i):
-        b = i % nreq
-        ebr.score_topk(ix, cross, [ebr.Query(h_u=h_u[b], k=k, user_vals=users[b])], ids, sc,
-                       stream=st)
+        ebr.score_topk(ix, cross, [query(i % nreq)], ids, sc, stream=st)
 
     for i in range(args.warmup):
         step(i)
@@ -192,16 +207,14 @@ def run_gpu(args, rank, world, local_rank):
     # End to end through the C ABI with host buffers (request in, K results out).
     hk_ids = np.empty(k, np.uint32)
     hk_sc = np.empty(k, np.float32)
-    h_hu = w.h_u.copy()
-    h_users = w.users.copy()
+    hqs = [query(b, host=True) for b in range(nreq)]
     e2e_t = []
     for i in range(args.warmup + args.steps):
         b = i % nreq
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ebr.score_topk(ix, cross, [ebr.Query(h_u=h_hu[b], k=k, user_vals=h_users[b])], hk_ids,
-                       hk_sc, io=ebr.IO_HOST, stream=st)
+        ebr.score_topk(ix, cross, [hqs[b]], hk_ids, hk_sc, io=ebr.IO_HOST, stream=st)
         t1 = time.perf_counter()
         if i >= args.warmup:
             e2e_t.append(t1 - t0)
@@ -215,6 +228,13 @@ def run_gpu(args, rank, world, local_rank):
     kern_bytes = emb_bytes + info.window_view_bytes
     if w.recipe.emb_dtype != "f32":
         kern_bytes += 4 * w.n_ads  # the FP32 wide term, written for the rescoring
+    kernel = "k_fused_window"
+    bytes_note = ("embedding table (+ FP8 row scales) + window-major view of the compressed "
+                  "lists (+ FP32 wide term out when the table is quantised), per launch")
+    if sparse:  # streaming scan over the table and the wide term Algorithm 2 scattered
+        kern_bytes = emb_bytes + 4 * w.n_ads
+        kernel = "k_scan_topk"
+        bytes_note = "embedding table (+ FP8 row scales) + the FP32 wide term, per launch"
     achieved = kern_bytes / (scan_ms / 1e3) / 1e9
     step_bytes = kern_bytes
     traffic = None
@@ -222,7 +242,8 @@ def run_gpu(args, rank, world, local_rank):
     if os.path.exists(tr_path):
         with open(tr_path) as f:
             tr = json.load(f)
-        if tr.get("workload") == args.workload and tr.get("kernel_rev") == KERNEL_REV:
+        if (tr.get("workload") == args.workload and tr.get("kernel_rev") == KERNEL_REV and
+                not sparse):
             traffic = tr.get("bytes_per_launch")
     launches_per_step = (prof.launches - launches0) / max(args.steps, 1)
     out = {
@@ -231,6 +252,8 @@ def run_gpu(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": w.recipe.emb_dtype,
         "data": "synthetic",
         "config": _config(w, {"replicas": world, "build_ms": round(info.build_ms, 3),
+                              "query": ("sparse: %d keys with weights" % args.sparse_query
+                                        if sparse else "user fields, dense w^"),
                               "window_view_ms": round(info.window_view_ms, 3),
                               "index_bytes": info.index_bytes,
                               "window_view_bytes": info.window_view_bytes}),
@@ -240,15 +263,14 @@ def run_gpu(args, rank, world, local_rank):
         "step_hbm_gbs": step_bytes / (ms_step / 1e3) / 1e9,
         "stage_ms": {"expand": prof.ms_expand / prof.calls, "wide": prof.ms_wide / prof.calls,
                      "scan_topk": scan_ms, "final": prof.ms_final / prof.calls},
-        "roofline": {"kernel": "k_fused_window", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": kernel, "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic,
                      "algorithmic_bytes": kern_bytes,
-                     "bytes_note": "embedding table (+ FP8 row scales) + window-major view of "
-                                   "the compressed lists (+ FP32 wide term out when the "
-                                   "table is quantised), per launch"},
+                     "bytes_note": bytes_note},
         "e2e": {"value": e2e_val, "unit": UNIT,
-                "h2d_bytes_per_step": int(w.recipe.d * 4 + w.recipe.f_u * 4),
+                "h2d_bytes_per_step": int(w.recipe.d * 4 + (8 * args.sparse_query if sparse
+                                                            else w.recipe.f_u * 4)),
                 "d2h_bytes_per_step": int(k * 8)},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "gpu_launches_per_step": launches_per_step,
@@ -257,7 +279,7 @@ def run_gpu(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
     del ix, h_u, users, flush
-    if world == 1 and not args.no_serve and args.workload == WORKLOAD:
+    if world == 1 and not args.no_serve and args.workload == WORKLOAD and not sparse:
         out["serving"] = run_serving(args, device=local_rank)
     return out
 
@@ -546,6 +568,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--n-ads", type=int, default=0, help="override the workload's inventory size")
     ap.add_argument("--batch", type=int, default=0, help="override the workload's users per step")
+    ap.add_argument("--sparse-query", type=int, default=0,
+                    help="requests carry this many (key, w) pairs instead of user fields")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[2000, 5000, 10000, 20000])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-batch", type=int, default=128)

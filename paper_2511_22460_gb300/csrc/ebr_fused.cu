@@ -66,6 +66,8 @@ struct FusedArgs {
   float *wide_out;  // if set: the per-ad wide term is written here (FP32 rescoring needs it)
   uint32_t *hist;   // [kCandBins + 1] candidate-score histogram + top bin (zeroed per request)
   const uint32_t *wmax_bits;  // max |w^| over the keys (FP32 bits), set by k_absmax
+  const float *wide_in;       // if set: the per-ad wide term, already summed (Algorithm 2
+                              // scattered it); no window is decoded
   uint32_t max_keys;          // most keys of one ad
 };
 
@@ -259,8 +261,9 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
         }
       }
       // lane g (< 9): the segments of group g; 16-byte aligned, in group order
+      // (all empty when the wide term comes precomputed)
       uint32_t lo = 0, hi = 0;
-      if (lane < kGroups) {
+      if (lane < kGroups && !a.wide_in) {
         lo = sm.wp[j % kPrefetch][lane];
         hi = sm.wp[(j + 1) % kPrefetch][lane];
       }
@@ -537,7 +540,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       const bool leader = valid && qd == 0;
       float score = 0.f;
       if (leader) {
-        const float wide = (float)acc[rw] * fx_unit;
+        const float wide = a.wide_in ? __ldg(a.wide_in + ad) : (float)acc[rw] * fx_unit;
         score = dot;
         if (a.scale) score *= a.scale[ad];
         score += wide;
@@ -743,7 +746,7 @@ bool fused_fits(const ebr_index *ix, uint32_t k) {
 int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
                  const uint64_t *filter, uint32_t k, uint64_t *cand_out, Ctrl *ctrl,
                  float *all_out, float *wide_out, uint32_t *hist, int max_grid,
-                 cudaStream_t st, bool wmax_ready) {
+                 cudaStream_t st, bool wmax_ready, const float *wide_in) {
   FusedArgs a;
   memset(&a, 0, sizeof(a));
   a.emb = ix->dtype == EBR_F32 ? ix->emb_f32.p : ix->emb_q.p;
@@ -768,7 +771,8 @@ int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
   // max |w^| for the accumulators' fixed-point scale (non-finite weights are
   // flagged); the query expansion computes it on the way when it made w^
   a.wmax_bits = &ctrl->pad;
-  if (!wmax_ready) {
+  a.wide_in = wide_in;
+  if (!wmax_ready && !wide_in) {
     EBR_CUDA_TRY(cudaMemsetAsync(&ctrl->pad, 0, sizeof(uint32_t), st));
     k_absmax<<<std::max<uint32_t>(1, std::min<uint32_t>(64, (ix->n_keys + 1023) / 1024)), 256, 0,
                st>>>(w_hat, ix->n_keys, &ctrl->pad, &ctrl->flags);

@@ -165,7 +165,8 @@ constexpr int kMaxCtasPerSm = 4;  // bound on scan CTAs per SM (candidate buffer
 int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
                  const uint64_t *filter, uint32_t k, uint64_t *cand_out, Ctrl *ctrl,
                  float *all_out, float *wide_out, uint32_t *hist, int max_grid,
-                 cudaStream_t st, bool wmax_ready = false);
+                 cudaStream_t st, bool wmax_ready = false,
+                 const float *wide_in = nullptr);
 bool fused_fits(const ebr_index *ix, uint32_t k);
 constexpr size_t kHistWords = 4096;  // candidate-score histogram of the fused scan (2048 bins + top bin)
 // Launchers implemented in ebr_query.cu, used by the serving loop.

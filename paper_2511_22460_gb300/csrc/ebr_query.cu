@@ -919,19 +919,29 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
       ix->lib_launches += 2;
     }
     pm.mark(2, st);
-    ScanArgs a;
-    memset(&a, 0, sizeof(a));
-    a.emb = quant ? ix->emb_q.p : ix->emb_f32.p;
-    a.scale = ix->dtype == EBR_FP8E4M3 ? (const float *)ix->emb_scale.p : nullptr;
-    a.h_u = q.h_u;
-    a.wide = (const float *)w.wide.p;
-    a.filter = q.filter;
-    a.n_ads = ix->n_ads;
-    a.k = kscan;
-    a.cand_out = (uint64_t *)w.cand.p;
-    a.ctrl = ctrl;
-    EBR_TRY(launch_scan<MODE_TOPK>(ix, a, st));
-    ix->launches += 1;
+    if (fused_fits(ix, kscan)) {
+      // the streaming scan of the fused kernel, adding the wide term that
+      // Algorithm 2 has just scattered (no window decoding)
+      EBR_CUDA_TRY(cudaMemsetAsync(w.hist.p, 0, kHistWords * 4, st));
+      EBR_TRY(launch_fused(ix, q.h_u, nullptr, q.filter, kscan, (uint64_t *)w.cand.p, ctrl,
+                           nullptr, nullptr, (uint32_t *)w.hist.p, ix->num_sms * kMaxCtasPerSm,
+                           st, true, (const float *)w.wide.p));
+      ix->launches += 1;
+    } else {
+      ScanArgs a;
+      memset(&a, 0, sizeof(a));
+      a.emb = quant ? ix->emb_q.p : ix->emb_f32.p;
+      a.scale = ix->dtype == EBR_FP8E4M3 ? (const float *)ix->emb_scale.p : nullptr;
+      a.h_u = q.h_u;
+      a.wide = (const float *)w.wide.p;
+      a.filter = q.filter;
+      a.n_ads = ix->n_ads;
+      a.k = kscan;
+      a.cand_out = (uint64_t *)w.cand.p;
+      a.ctrl = ctrl;
+      EBR_TRY(launch_scan<MODE_TOPK>(ix, a, st));
+      ix->launches += 1;
+    }
   }
   pm.mark(3, st);
   const uint32_t p2 = pow2_at_least(std::max<uint32_t>(kscan, 1));

@@ -231,6 +231,22 @@ def make_filters(rng, n: int, B: int, frac) -> np.ndarray:
     return out
 
 
+def sparse_query(w: "Workload", n_q: int, seed: int = 0, var: float = 0.05):
+    """A request whose cross term touches only a few hundred keys (the paper's
+    own regime: the user's history values carry the non-zero weights): n_q
+    distinct ad-field keys drawn with the frequency of their posting lists
+    (popular values are the likely history matches), weights iid N(0, var).
+    Returns (q_key uint32 [n], q_w float32 [n]), n <= n_q after de-duplication."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 11])))
+    n, f_a = w.ad_vals.shape
+    picks = rng.integers(0, n * f_a, size=4 * n_q)
+    keys = (w.ad_vals.reshape(-1)[picks] + w.key_off[picks % f_a]).astype(np.uint32)
+    _, first = np.unique(keys, return_index=True)
+    q_key = keys[np.sort(first)][:n_q]
+    q_w = (rng.standard_normal(q_key.size) * np.sqrt(var)).astype(np.float32)
+    return q_key, q_w
+
+
 def poisson_arrivals(rate_per_s: float, duration_s: float, seed: int = 0) -> np.ndarray:
     """Open-loop request arrival times (seconds), exponential inter-arrivals."""
     rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 7])))

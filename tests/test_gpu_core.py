@@ -432,3 +432,28 @@ def test_recall_before_and_after_rescoring(dtype, capsys):
               "after %.4f" % (dtype, n, k, pre, float(np.median(err)), post))
     assert post == 1.0
     assert 0.0 < pre <= 1.0
+
+
+@pytest.mark.parametrize("n_q", [1, 300, 3000])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_topk_sparse_query_matches_oracle(n_q, dtype):
+    """The paper's own regime: a few keys carry non-zero w^ (the user's history
+    matches), so the key-major traversal (Algorithm 2) serves the request."""
+    from paper_2511_22460_gb300.datagen import sparse_query
+    n, k = 150_000, 500
+    w, post, ix, cross = _setup("single_fp32_2m", n, seed=8, dtype=dtype)
+    pk, pa = post
+    qk, qw = sparse_query(w, n_q, seed=n_q)
+    ref = oracle.scores_postings(w.h_u[0], w.emb, w.n_keys, pk, pa, qk, qw)
+    wabs = np.zeros(w.n_keys)
+    np.add.at(wabs, qk, np.abs(qw.astype(np.float64)))
+    cond = np.abs(w.emb.astype(np.float64)) @ np.abs(w.h_u[0].astype(np.float64)) + np.bincount(
+        pa, weights=wabs[pk], minlength=n)
+    tol = 1e-5 * np.maximum(np.abs(ref), cond)
+    ids = torch.empty(k, dtype=torch.int32, device=DEV)
+    sc = torch.empty(k, dtype=torch.float32, device=DEV)
+    ebr.score_topk(ix, None, [ebr.Query(h_u=dev(w.h_u[0]), k=k, q_key=dev(qk), q_w=dev(qw))],
+                   ids, sc)
+    got = ids.cpu().numpy().view(np.uint32)
+    assert recall(got, ref, tol, k) == 1.0
+    check_topk(got, sc.cpu().numpy(), ref, tol, k)
