@@ -231,10 +231,10 @@ def run_gpu(args, rank, world, local_rank):
     kernel = "k_fused_window"
     bytes_note = ("embedding table (+ FP8 row scales) + window-major view of the compressed "
                   "lists (+ FP32 wide term out when the table is quantised), per launch")
-    if sparse:  # streaming scan over the table and the wide term Algorithm 2 scattered
+    if sparse:  # the fused scan reads the wide term Algorithm 2 scattered, decodes no window
         kern_bytes = emb_bytes + 4 * w.n_ads
-        kernel = "k_scan_topk"
-        bytes_note = "embedding table (+ FP8 row scales) + the FP32 wide term, per launch"
+        bytes_note = ("embedding table (+ FP8 row scales) + the FP32 wide term read, per "
+                      "launch")
     achieved = kern_bytes / (scan_ms / 1e3) / 1e9
     step_bytes = kern_bytes
     traffic = None
