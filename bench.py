@@ -168,7 +168,9 @@ def run_gpu(args, rank, world, local_rank):
     def query(b, host=False):
         if sparse:
             qk, qw = sq[b] if host else sq_d[b]
-            return ebr.Query(h_u=(w.h_u[b].copy() if host else h_u[b]), k=k, q_key=qk, q_w=qw)
+            return ebr.Query(h_u=(w.h_u[b].copy() if host else h_u[b]), k=k, q_key=qk, q_w=qw,
+                             flags={"auto": 0, "key": ebr.QF_KEY_MAJOR,
+                                    "window": ebr.QF_WINDOW_MAJOR}[args.sparse_route])
         if host:
             return ebr.Query(h_u=w.h_u[b].copy(), k=k, user_vals=w.users[b].copy())
         return ebr.Query(h_u=h_u[b], k=k, user_vals=users[b])
@@ -231,10 +233,24 @@ def run_gpu(args, rank, world, local_rank):
     kernel = "k_fused_window"
     bytes_note = ("embedding table (+ FP8 row scales) + window-major view of the compressed "
                   "lists (+ FP32 wide term out when the table is quantised), per launch")
-    if sparse:  # the fused scan reads the wide term Algorithm 2 scattered, decodes no window
-        kern_bytes = emb_bytes + 4 * w.n_ads
-        bytes_note = ("embedding table (+ FP8 row scales) + the FP32 wide term read, per "
-                      "launch")
+    routes = None
+    if sparse:
+        # per launch, the fused scan either reads the wide term Algorithm 2
+        # scattered (no window decoded) or decodes the window-major view
+        if args.sparse_route == "auto":
+            n_win_r = int(prof.window_routed)
+            n_key_r = int(prof.auto_routed - prof.window_routed)
+        else:
+            n_win_r = args.steps if args.sparse_route == "window" else 0
+            n_key_r = args.steps - n_win_r
+        routes = {"window_major": n_win_r, "key_major": n_key_r}
+        key_bytes = emb_bytes + 4 * w.n_ads
+        kern_bytes = ((n_win_r * kern_bytes + n_key_r * key_bytes) /
+                      max(n_win_r + n_key_r, 1))
+        bytes_note = ("embedding table (+ FP8 row scales) + per launch either the FP32 wide "
+                      "term read (Algorithm 2 scattered it) or the window-major view (+ FP32 "
+                      "wide term out when the table is quantised), averaged over the routes "
+                      "the requests took")
     achieved = kern_bytes / (scan_ms / 1e3) / 1e9
     step_bytes = kern_bytes
     traffic = None
@@ -252,7 +268,8 @@ def run_gpu(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": w.recipe.emb_dtype,
         "data": "synthetic",
         "config": _config(w, {"replicas": world, "build_ms": round(info.build_ms, 3),
-                              "query": ("sparse: %d keys with weights" % args.sparse_query
+                              "query": ("sparse: %d keys with weights, %s-major" %
+                                        (args.sparse_query, args.sparse_route)
                                         if sparse else "user fields, dense w^"),
                               "window_view_ms": round(info.window_view_ms, 3),
                               "index_bytes": info.index_bytes,
@@ -263,6 +280,7 @@ def run_gpu(args, rank, world, local_rank):
         "step_hbm_gbs": step_bytes / (ms_step / 1e3) / 1e9,
         "stage_ms": {"expand": prof.ms_expand / prof.calls, "wide": prof.ms_wide / prof.calls,
                      "scan_topk": scan_ms, "final": prof.ms_final / prof.calls},
+        **({"sparse_routes": routes} if routes else {}),
         "roofline": {"kernel": kernel, "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic,
@@ -284,7 +302,7 @@ def run_gpu(args, rank, world, local_rank):
     return out
 
 
-KERNEL_REV = "fused-v2"
+KERNEL_REV = "fused-v3"
 
 # FP32 add throughput of the CUDA cores: 152 SMs x 128 FP32 lanes x 2.07 GHz
 ALU_ADD_PEAK_T = 152 * 128 * 2.07e9 / 1e12
@@ -570,6 +588,10 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="override the workload's users per step")
     ap.add_argument("--sparse-query", type=int, default=0,
                     help="requests carry this many (key, w) pairs instead of user fields")
+    ap.add_argument("--sparse-route", choices=["auto", "key", "window"], default="auto",
+                    help="traversal for sparse requests: chosen on the device by the list's "
+                         "work (auto), Algorithm 2's key-major scatter, or the window-major "
+                         "decode inside the fused scan")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[2000, 5000, 10000, 20000])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-batch", type=int, default=128)

@@ -200,6 +200,13 @@ typedef struct {
  * score buffer) even when the query is dense; by default dense queries use
  * the fused window-major scan and sparse key lists use Algorithm 2. */
 #define EBR_QF_KEY_MAJOR 1u
+/* For a sparse key list (q_key != NULL): sum the list into a dense w^ over the
+ * key space (repeated keys add; a key >= n_keys fails the call with
+ * EBR_EDATA, and so does a non-finite sum) and decode it window by window
+ * inside the fused scan, as for a dense query; blocks of keys whose w^ is
+ * zero add nothing.  Ignored for dense queries and when EBR_QF_KEY_MAJOR is
+ * also set. */
+#define EBR_QF_WINDOW_MAJOR 2u
 
 #define EBR_IO_DEVICE 0   /* all query arrays and outputs are device pointers; stream-ordered */
 #define EBR_IO_HOST 1     /* all query arrays and outputs are host pointers; the call copies them
@@ -213,6 +220,11 @@ typedef struct {
  * of eligible ads hold id 0xFFFFFFFF and score -inf.  The full score vector
  * is never written to device memory.  `cross` may be NULL when no request
  * uses user_vals.  `q` is a host array of `batch` structs.
+ * Device-side input checks (a key >= n_keys, a user value outside its
+ * vocabulary, a non-finite weight) fail the call with EBR_EDATA when it waits
+ * for the device, i.e. with EBR_IO_HOST; with EBR_IO_DEVICE the call is
+ * stream-ordered and does not wait, so such a request yields unspecified
+ * results instead.
  */
 int ebr_score_topk(const ebr_index *ix, const ebr_cross *cross, const ebr_query *q,
                    uint32_t batch, uint32_t *out_ids, float *out_scores, int io,
@@ -314,6 +326,8 @@ typedef struct {
   double ms_batch_stage;   /* staging + expansion into user-minor weights */
   double ms_batch_scan;    /* k_batch_window: tensor-core deep term + wide term + per-CTA top-m */
   double ms_batch_merge;   /* k_batch_merge: per-user merge, FP32 rescoring, final K */
+  uint64_t auto_routed;    /* sparse key lists whose traversal the device chose */
+  uint64_t window_routed;  /* of those, decoded window by window (the rest: Algorithm 2) */
 } ebr_profile;
 int ebr_profile_enable(ebr_index *ix, int on);
 int ebr_profile_read(ebr_index *ix, ebr_profile *out);

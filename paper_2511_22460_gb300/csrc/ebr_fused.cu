@@ -68,6 +68,8 @@ struct FusedArgs {
   const uint32_t *wmax_bits;  // max |w^| over the keys (FP32 bits), set by k_absmax
   const float *wide_in;       // if set: the per-ad wide term, already summed (Algorithm 2
                               // scattered it); no window is decoded
+  const uint32_t *route;      // if set: *route != 0 (decided on the device) ignores wide_in
+                              // and decodes the windows with w_hat after all
   uint32_t max_keys;          // most keys of one ad
 };
 
@@ -196,6 +198,8 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
   const uint32_t my_wins = w_end - w_begin;
 
   for (int i = tid; i < kAccBufs * kWin; i += kFusedThreads) (&sm.acc[0][0])[i] = 0;
+  // whether the wide term comes precomputed (no window decoding) in this launch
+  const bool pre = a.wide_in != nullptr && !(a.route && *a.route);
   const int fx_e = fix_exponent(*a.wmax_bits, a.max_keys);
   const float fx_scale = pow2f(fx_e), fx_unit = pow2f(-fx_e);
   for (int i = tid; i < D; i += kFusedThreads) s_h[i] = a.h_u[i];
@@ -263,7 +267,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       // lane g (< 9): the segments of group g; 16-byte aligned, in group order
       // (all empty when the wide term comes precomputed)
       uint32_t lo = 0, hi = 0;
-      if (lane < kGroups && !a.wide_in) {
+      if (lane < kGroups && !pre) {
         lo = sm.wp[j % kPrefetch][lane];
         hi = sm.wp[(j + 1) % kPrefetch][lane];
       }
@@ -540,11 +544,11 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       const bool leader = valid && qd == 0;
       float score = 0.f;
       if (leader) {
-        const float wide = a.wide_in ? __ldg(a.wide_in + ad) : (float)acc[rw] * fx_unit;
+        const float wide = pre ? __ldg(a.wide_in + ad) : (float)acc[rw] * fx_unit;
         score = dot;
         if (a.scale) score *= a.scale[ad];
         score += wide;
-        if (a.wide_out) a.wide_out[ad] = wide;
+        if (a.wide_out && !pre) a.wide_out[ad] = wide;
       }
       if (ALL) {
         if (leader) a.all_out[ad] = score;
@@ -746,7 +750,8 @@ bool fused_fits(const ebr_index *ix, uint32_t k) {
 int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
                  const uint64_t *filter, uint32_t k, uint64_t *cand_out, Ctrl *ctrl,
                  float *all_out, float *wide_out, uint32_t *hist, int max_grid,
-                 cudaStream_t st, bool wmax_ready, const float *wide_in) {
+                 cudaStream_t st, bool wmax_ready, const float *wide_in,
+                 const uint32_t *route) {
   FusedArgs a;
   memset(&a, 0, sizeof(a));
   a.emb = ix->dtype == EBR_F32 ? ix->emb_f32.p : ix->emb_q.p;
@@ -772,7 +777,8 @@ int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
   // flagged); the query expansion computes it on the way when it made w^
   a.wmax_bits = &ctrl->pad;
   a.wide_in = wide_in;
-  if (!wmax_ready && !wide_in) {
+  a.route = route;
+  if (!wmax_ready && (!wide_in || route)) {
     EBR_CUDA_TRY(cudaMemsetAsync(&ctrl->pad, 0, sizeof(uint32_t), st));
     k_absmax<<<std::max<uint32_t>(1, std::min<uint32_t>(64, (ix->n_keys + 1023) / 1024)), 256, 0,
                st>>>(w_hat, ix->n_keys, &ctrl->pad, &ctrl->flags);

@@ -70,6 +70,7 @@ struct Workspace {
   DevBuf cub_tmp;     // CUB temporary storage
   DevBuf cand;        // uint64 [G * KCAP] per-CTA candidates
   DevBuf ctrl;        // Ctrl block (counters, threshold, flags)
+  DevBuf route_stats; // uint64 [2]: sparse lists routed on the device, of those window-major
   DevBuf io_in;       // staging for host inputs
   DevBuf io_out;      // staging for outputs
   DevBuf hist;        // uint32 [kHistWords] candidate-score histogram
@@ -83,6 +84,8 @@ struct Ctrl {
   unsigned long long total_units;  // Algorithm 2 work units
   unsigned int n_work;       // compacted work entries
   unsigned int pad;          // fused scan: max |w^| of the request (FP32 bits)
+  unsigned int route;        // sparse list: 0 = Algorithm 2 scatter, 1 = window-major decode
+  unsigned int pad2;
 };
 
 // Scratch of the batched (tensor-core) path.
@@ -143,6 +146,7 @@ struct ebr_index {
   std::vector<std::array<cudaEvent_t, 5>> prof_pending, prof_pool;
   std::vector<std::array<cudaEvent_t, 5>> bprof_pending;  // batched calls (same pool)
   ebr_profile prof_acc = {};
+  uint64_t route_base[2] = {0, 0};  // route counters when profiling was (re)enabled
   uint64_t launches = 0, lib_launches = 0;  // counted on every call
   uint64_t batched = 0;    // requests served by the batched scan
   uint64_t fallbacks = 0;  // batched requests recomputed by the single-request scan
@@ -166,7 +170,7 @@ int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
                  const uint64_t *filter, uint32_t k, uint64_t *cand_out, Ctrl *ctrl,
                  float *all_out, float *wide_out, uint32_t *hist, int max_grid,
                  cudaStream_t st, bool wmax_ready = false,
-                 const float *wide_in = nullptr);
+                 const float *wide_in = nullptr, const uint32_t *route = nullptr);
 bool fused_fits(const ebr_index *ix, uint32_t k);
 constexpr size_t kHistWords = 4096;  // candidate-score histogram of the fused scan (2048 bins + top bin)
 // Launchers implemented in ebr_query.cu, used by the serving loop.

@@ -181,6 +181,13 @@ struct IndexView {
   uint32_t n_keys, n_ads;
 };
 
+// Algorithm 2 work units of the whole index (every key's blocks).
+static unsigned long long index_units(const ebr_index *ix) {
+  unsigned long long u = 0;
+  for (int g = 0; g < kGroups; g++) u += (unsigned long long)ix->n_blocks[g] << (g >= 2 ? g - 2 : 0);
+  return u;
+}
+
 static IndexView index_view(const ebr_index *ix) {
   IndexView v;
   for (int g = 0; g < kGroups; g++) {
@@ -194,6 +201,21 @@ static IndexView index_view(const ebr_index *ix) {
 }
 
 __device__ __forceinline__ uint32_t unit_shift(uint32_t g) { return g >= 2 ? g - 2 : 0; }
+
+// A sparse key list summed into a dense w^ over the key space (repeated keys
+// add), for the window-major traversal: the fused scan then decodes every
+// window's blocks and skips the additions of keys whose w^ is zero.
+__global__ void k_list_to_dense(const uint32_t *__restrict__ q_key, const float *__restrict__ q_w,
+                                uint32_t n_q, uint32_t n_keys, float *__restrict__ w_dense,
+                                uint32_t *__restrict__ flags) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_q; i += gridDim.x * blockDim.x) {
+    const uint32_t key = q_key[i];
+    if (key >= n_keys)
+      atomicOr(flags, DEVERR_BAD_KEY);
+    else if (q_w[i] != 0.0f)
+      atomicAdd(&w_dense[key], q_w[i]);
+  }
+}
 
 // k_length of Algorithm 2 for every (group, query entry), in work units.
 // q_key == nullptr: dense query, entry i is key i.  Zero weights are dropped.
@@ -227,17 +249,30 @@ constexpr int kWideUPT = 8;                         // units per thread per tile
 constexpr int kWideTile = kWideThreads * kWideUPT;  // units per tile
 
 // Compact the non-empty (group, key) entries: entry e covers work units
-// [seg_e, seg_e + units_e) of the whole query.
+// [seg_e, seg_e + units_e) of the whole query.  route_units != 0: choose the
+// traversal of a sparse list on the device (ctrl->route): the window-major
+// decode when the list's work units reach 1/kRouteRatio of the whole
+// index's, where Algorithm 2's scatter costs more than decoding every window.
+constexpr unsigned long long kRouteRatio = 8;
+
 __global__ void k_wide_compact(IndexView ix, const uint32_t *__restrict__ q_key,
                                const float *__restrict__ q_w, uint32_t n_q,
                                const LenPair *__restrict__ lens, const LenPair *__restrict__ scan,
-                               WorkEntry *__restrict__ work, Ctrl *__restrict__ ctrl) {
+                               WorkEntry *__restrict__ work, Ctrl *__restrict__ ctrl,
+                               unsigned long long route_units,
+                               unsigned long long *__restrict__ route_stats) {
   const uint64_t total = (uint64_t)kGroups * n_q;
   for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p <= total;
        p += (uint64_t)gridDim.x * blockDim.x) {
     if (p == total) {
       ctrl->total_units = scan[p].units;
       ctrl->n_work = scan[p].ne;
+      const uint32_t r = route_units && scan[p].units * kRouteRatio >= route_units ? 1u : 0u;
+      ctrl->route = r;
+      if (route_units && route_stats) {
+        atomicAdd(&route_stats[0], 1ull);
+        atomicAdd(&route_stats[1], (unsigned long long)r);
+      }
       continue;
     }
     if (!lens[p].ne) continue;
@@ -248,6 +283,150 @@ __global__ void k_wide_compact(IndexView ix, const uint32_t *__restrict__ q_key,
     we.blk0 = ix.keys[g][key];
     we.w = q_w[i];
     work[scan[p].ne] = we;
+  }
+}
+
+// Short lists: the three steps above (per-entry lengths, their exclusive
+// scan, the compaction) in one CTA and one launch.  Thread t owns the
+// contiguous entries [t * per, (t + 1) * per) of the group-major order
+// p = g * n_q + i, so a block scan of the per-thread sums gives every entry's
+// first unit and slot.  With route_units != 0 it also takes the traversal
+// decision of k_wide_compact; for the window-major decode it sums the list
+// into w_dense itself, reduces max |w^| into ctrl->pad (what the fused scan's
+// fixed-point scale needs) and leaves no work for the scatter.
+constexpr int kPlanThreads = 1024;
+constexpr uint32_t kPlanMaxPer = 8;  // entries per thread (longer lists: the three kernels)
+constexpr uint64_t kPlanMaxEntries = (uint64_t)kPlanThreads * kPlanMaxPer;
+constexpr uint32_t kRouteWindow = 1u, kRouteSummed = 2u;  // ctrl->route bits
+
+__device__ __forceinline__ unsigned long long plan_entry(const IndexView &ix,
+                                                         const uint32_t *__restrict__ q_key,
+                                                         const float *__restrict__ q_w,
+                                                         uint32_t n_q, uint32_t p, uint32_t &key,
+                                                         uint32_t &g, float &wv) {
+  g = p / n_q;
+  const uint32_t i = p - g * n_q;
+  key = q_key[i];
+  wv = q_w[i];
+  if (key >= ix.n_keys || wv == 0.0f) return 0ull;
+  return (unsigned long long)(ix.keys[g][key + 1] - ix.keys[g][key]) << unit_shift(g);
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_wide_plan(
+    IndexView ix, const uint32_t *__restrict__ q_key, const float *__restrict__ q_w, uint32_t n_q,
+    WorkEntry *__restrict__ work, Ctrl *__restrict__ ctrl, unsigned long long route_units,
+    unsigned long long *__restrict__ route_stats, float *__restrict__ w_dense) {
+  __shared__ unsigned long long s_u[32];
+  __shared__ uint32_t s_n[32], s_m[32];
+  __shared__ uint32_t s_route;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t total = kGroups * n_q;
+  const uint32_t per = (total + kPlanThreads - 1) / kPlanThreads;
+  const uint32_t p0 = min(total, tid * per), p1 = min(total, p0 + per);
+  // pass 1: this thread's units and non-empty entries
+  unsigned long long su = 0;
+  uint32_t sn = 0, bad = 0;
+  for (uint32_t p = p0; p < p1; p++) {
+    uint32_t key, g;
+    float wv;
+    const unsigned long long u = plan_entry(ix, q_key, q_w, n_q, p, key, g, wv);
+    su += u;
+    sn += u ? 1u : 0u;
+    bad |= (g == 0 && key >= ix.n_keys) ? 1u : 0u;
+  }
+  if (bad) atomicOr(&ctrl->flags, DEVERR_BAD_KEY);
+  // block exclusive scan of (units, entries)
+  unsigned long long iu = su;
+  uint32_t in = sn;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long tu = __shfl_up_sync(0xffffffffu, iu, o);
+    const uint32_t tn = __shfl_up_sync(0xffffffffu, in, o);
+    if (lane >= (uint32_t)o) {
+      iu += tu;
+      in += tn;
+    }
+  }
+  if (lane == 31) {
+    s_u[wid] = iu;
+    s_n[wid] = in;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long wu = s_u[lane];
+    uint32_t wn = s_n[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long tu = __shfl_up_sync(0xffffffffu, wu, o);
+      const uint32_t tn = __shfl_up_sync(0xffffffffu, wn, o);
+      if (lane >= (uint32_t)o) {
+        wu += tu;
+        wn += tn;
+      }
+    }
+    s_u[lane] = wu;  // inclusive over warps
+    s_n[lane] = wn;
+  }
+  __syncthreads();
+  const unsigned long long all_u = s_u[31];
+  const uint32_t all_n = s_n[31];
+  unsigned long long off_u = iu - su + (wid ? s_u[wid - 1] : 0ull);
+  uint32_t off_n = in - sn + (wid ? s_n[wid - 1] : 0u);
+  if (tid == 0) {
+    const uint32_t r = route_units && all_u * kRouteRatio >= route_units ? kRouteWindow : 0u;
+    s_route = r;
+    if (route_units && route_stats) {
+      atomicAdd(&route_stats[0], 1ull);
+      atomicAdd(&route_stats[1], (unsigned long long)r);
+    }
+  }
+  __syncthreads();
+  if (s_route) {
+    // window-major decode: the list summed into w_dense, then max |w^|
+    for (uint32_t i = tid; i < n_q; i += kPlanThreads) {
+      const uint32_t key = q_key[i];
+      const float wv = q_w[i];
+      if (key < ix.n_keys && wv != 0.0f) atomicAdd(&w_dense[key], wv);
+    }
+    __syncthreads();  // the block's atomics are visible to the block
+    uint32_t m = 0;
+    for (uint32_t i = tid; i < n_q; i += kPlanThreads) {
+      const uint32_t key = q_key[i];
+      if (key < ix.n_keys) m = max(m, __float_as_uint(__ldcg(w_dense + key)) & 0x7FFFFFFFu);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) s_m[wid] = m;
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t mm = 0;
+      for (int q = 0; q < kPlanThreads / 32; q++) mm = max(mm, s_m[q]);
+      if (mm >= 0x7F800000u) atomicOr(&ctrl->flags, DEVERR_RANGE);
+      ctrl->pad = mm >= 0x7F800000u ? 0u : mm;
+      ctrl->total_units = 0;
+      ctrl->n_work = 0;
+      ctrl->route = kRouteWindow | kRouteSummed;
+    }
+    return;
+  }
+  // pass 2: the non-empty entries, in order, at their first unit
+  for (uint32_t p = p0; p < p1; p++) {
+    uint32_t key, g;
+    float wv;
+    const unsigned long long u = plan_entry(ix, q_key, q_w, n_q, p, key, g, wv);
+    if (!u) continue;
+    WorkEntry we;
+    we.seg_g = off_u | ((unsigned long long)g << 56);
+    we.blk0 = ix.keys[g][key];
+    we.w = wv;
+    work[off_n] = we;
+    off_u += u;
+    off_n++;
+  }
+  if (tid == 0) {
+    ctrl->total_units = all_u;
+    ctrl->n_work = all_n;
+    ctrl->route = 0;
   }
 }
 
@@ -265,11 +444,21 @@ constexpr unsigned long long kSegMask = 0x00FFFFFFFFFFFFFFull;
 
 __global__ void __launch_bounds__(kWideThreads) k_wide_scatter(
     IndexView ix, const WorkEntry *__restrict__ work, const Ctrl *__restrict__ ctrl,
-    float *__restrict__ wide) {
+    float *__restrict__ wide, const uint32_t *__restrict__ q_key, const float *__restrict__ q_w,
+    uint32_t n_q, float *__restrict__ w_dense) {
   __shared__ unsigned long long s_seg[kWideTile + 1];
   __shared__ uint32_t s_blk[kWideTile + 1];
   __shared__ float s_w[kWideTile + 1];
   __shared__ uint32_t s_next;
+  if (ctrl->route) {  // window-major decode chosen: only sum the list into a dense w^
+    if (ctrl->route & kRouteSummed) return;  // k_wide_plan did
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_q;
+         i += gridDim.x * blockDim.x) {
+      const uint32_t key = q_key[i];  // keys >= n_keys were flagged by k_wide_lens
+      if (key < ix.n_keys && q_w[i] != 0.0f) atomicAdd(&w_dense[key], q_w[i]);
+    }
+    return;
+  }
   const unsigned long long total = ctrl->total_units;
   const uint32_t n_work = ctrl->n_work;
   const unsigned long long n_tiles = (total + kWideTile - 1) / kWideTile;
@@ -742,6 +931,10 @@ int ws_prepare_one(ebr_index *ix, uint32_t n_q, uint32_t kcap) {
                                   2 * (size_t)kcap * 8));
   EBR_TRY(dev_reserve(w.ctrl, 256));
   EBR_TRY(dev_reserve(w.hist, kHistWords * 4));
+  if (!w.route_stats.p) {  // lifetime counters, zeroed once
+    EBR_TRY(dev_reserve(w.route_stats, 16));
+    EBR_CUDA_TRY(cudaMemset(w.route_stats.p, 0, 16));
+  }
   return EBR_OK;
 }
 
@@ -753,13 +946,32 @@ static int launch_grid(uint64_t n, int threads, int cap) {
 }
 
 // Wide term of one request into ws.wide (zeroed first): Algorithm 2.
+// w_dense != nullptr (a sparse list, zeroed w_dense): the traversal is chosen
+// on the device; when it is the window-major decode, the list is summed into
+// w_dense instead of being scattered.
+// *planned (if given): whether the one-CTA plan ran, which also leaves max
+// |w^| in ctrl->pad when it chose the window-major decode.
 static int run_wide(ebr_index *ix, const uint32_t *q_key, const float *q_w, uint32_t n_q,
-                    Ctrl *ctrl, cudaStream_t st) {
+                    Ctrl *ctrl, cudaStream_t st, float *w_dense = nullptr,
+                    bool *planned = nullptr) {
   Workspace &w = ix->ws;
+  if (planned) *planned = false;
   EBR_CUDA_TRY(cudaMemsetAsync(w.wide.p, 0, (size_t)ix->n_ads * 4, st));
   if (n_q == 0) return EBR_OK;
   IndexView iv = index_view(ix);
   const uint64_t entries = (uint64_t)kGroups * n_q + 1;
+  if (q_key && entries - 1 <= kPlanMaxEntries) {
+    k_wide_plan<<<1, kPlanThreads, 0, st>>>(iv, q_key, q_w, n_q, (WorkEntry *)w.work.p, ctrl,
+                                            w_dense ? index_units(ix) : 0ull,
+                                            (unsigned long long *)w.route_stats.p, w_dense);
+    EBR_CUDA_TRY(cudaGetLastError());
+    k_wide_scatter<<<ix->num_sms * 8, kWideThreads, 0, st>>>(iv, (const WorkEntry *)w.work.p,
+                                                             ctrl, (float *)w.wide.p, q_key, q_w,
+                                                             n_q, w_dense);
+    EBR_CUDA_TRY(cudaGetLastError());
+    if (planned) *planned = true;
+    return EBR_OK;
+  }
   k_wide_lens<<<launch_grid(entries, 256, 65535), 256, 0, st>>>(
       iv, q_key, q_w, n_q, (LenPair *)w.lens.p, &ctrl->flags);
   EBR_CUDA_TRY(cudaGetLastError());
@@ -769,10 +981,12 @@ static int run_wide(ebr_index *ix, const uint32_t *q_key, const float *q_w, uint
                                               LenPair{0, 0, 0}, (int)entries, st));
   k_wide_compact<<<launch_grid(entries, 256, 65535), 256, 0, st>>>(
       iv, q_key, q_w, n_q, (const LenPair *)w.lens.p, (const LenPair *)w.scan.p,
-      (WorkEntry *)w.work.p, ctrl);
+      (WorkEntry *)w.work.p, ctrl, w_dense ? index_units(ix) : 0ull,
+      (unsigned long long *)w.route_stats.p);
   EBR_CUDA_TRY(cudaGetLastError());
   k_wide_scatter<<<ix->num_sms * 8, kWideThreads, 0, st>>>(iv, (const WorkEntry *)w.work.p,
-                                                           ctrl, (float *)w.wide.p);
+                                                           ctrl, (float *)w.wide.p, q_key, q_w,
+                                                           n_q, w_dense);
   EBR_CUDA_TRY(cudaGetLastError());
   return EBR_OK;
 }
@@ -899,10 +1113,26 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
     n_q = ix->n_keys;
   } else if (!q_key) {
     n_q = ix->n_keys;
+  } else if ((q.flags & EBR_QF_WINDOW_MAJOR) && !(q.flags & EBR_QF_KEY_MAJOR) &&
+             fused_fits(ix, kscan)) {
+    EBR_CUDA_TRY(cudaMemsetAsync(w.w_dense.p, 0, (size_t)ix->n_keys * 4, st));
+    if (n_q) {
+      k_list_to_dense<<<launch_grid(n_q, 256, 1024), 256, 0, st>>>(
+          q_key, q_w, n_q, ix->n_keys, (float *)w.w_dense.p, &ctrl->flags);
+      EBR_CUDA_TRY(cudaGetLastError());
+      ix->launches += 1;
+    }
+    q_key = nullptr;
+    q_w = (const float *)w.w_dense.p;
+    n_q = ix->n_keys;
   }
   pm.mark(1, st);
   const bool fused =
       q_key == nullptr && !(q.flags & EBR_QF_KEY_MAJOR) && fused_fits(ix, kscan);
+  // a sparse list with no traversal forced: chosen on the device by its work
+  const bool auto_route = q_key != nullptr && n_q > 0 &&
+                          !(q.flags & (EBR_QF_KEY_MAJOR | EBR_QF_WINDOW_MAJOR)) &&
+                          fused_fits(ix, kscan);
   if (fused) {
     // dense query: wide term decoded window by window inside the scan
     pm.mark(2, st);
@@ -913,20 +1143,27 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
                          ix->num_sms * kMaxCtasPerSm, st, wmax_ready));
     ix->launches += wmax_ready ? 1 : 2;  // (+ k_absmax) k_fused_window
   } else {
-    EBR_TRY(run_wide(ix, q_key, q_w, n_q, ctrl, st));
+    float *w_dense = auto_route ? (float *)w.w_dense.p : nullptr;
+    if (auto_route) EBR_CUDA_TRY(cudaMemsetAsync(w_dense, 0, (size_t)ix->n_keys * 4, st));
+    bool planned = false;
+    EBR_TRY(run_wide(ix, q_key, q_w, n_q, ctrl, st, w_dense, &planned));
     if (n_q) {
-      ix->launches += 3;
-      ix->lib_launches += 2;
+      ix->launches += planned ? 2 : 3;
+      ix->lib_launches += planned ? 0 : 2;
     }
     pm.mark(2, st);
     if (fused_fits(ix, kscan)) {
       // the streaming scan of the fused kernel, adding the wide term that
-      // Algorithm 2 has just scattered (no window decoding)
+      // Algorithm 2 has just scattered (no window decoding), or, when the
+      // device chose the window-major decode, decoding w_dense's windows
       EBR_CUDA_TRY(cudaMemsetAsync(w.hist.p, 0, kHistWords * 4, st));
-      EBR_TRY(launch_fused(ix, q.h_u, nullptr, q.filter, kscan, (uint64_t *)w.cand.p, ctrl,
-                           nullptr, nullptr, (uint32_t *)w.hist.p, ix->num_sms * kMaxCtasPerSm,
-                           st, true, (const float *)w.wide.p));
-      ix->launches += 1;
+      EBR_TRY(launch_fused(ix, q.h_u, w_dense, q.filter, kscan, (uint64_t *)w.cand.p, ctrl,
+                           nullptr, auto_route && quant ? (float *)w.wide.p : nullptr,
+                           (uint32_t *)w.hist.p, ix->num_sms * kMaxCtasPerSm, st,
+                           !auto_route || planned, (const float *)w.wide.p,
+                           auto_route ? &ctrl->route : nullptr));
+      ix->launches += auto_route && !planned ? 2 : 1;  // (+ k_absmax) k_fused_window
+
     } else {
       ScanArgs a;
       memset(&a, 0, sizeof(a));
@@ -1120,6 +1357,10 @@ extern "C" int ebr_expand_query(const ebr_cross *c, const uint32_t *user_vals, u
 // Validates one request against the index (host-visible fields only).
 static int check_query(const ebr_index *ix, const ebr_cross *cross, const ebr_query &q) {
   if (!q.h_u) { set_error("query: h_u is null"); return EBR_EINVAL; }
+  if (q.flags & ~(EBR_QF_KEY_MAJOR | EBR_QF_WINDOW_MAJOR)) {
+    set_error("query: unknown flag bits 0x%x", q.flags);
+    return EBR_EINVAL;
+  }
   if (q.k == 0 || q.k > 8192) { set_error("query: k must be 1..8192 (got %u)", q.k); return EBR_EINVAL; }
   if (ix->dtype != EBR_F32 && (uint64_t)q.k * ix->rescore_mult > 8192) {
     set_error("query: R*k must be <= 8192 for BF16/FP8 scans");
@@ -1342,6 +1583,18 @@ extern "C" int ebr_wide_scores(const ebr_index *cix, const ebr_cross *cross, con
   return rc;
 }
 
+// Device counters of the traversal chosen for sparse lists: [0] lists routed
+// on the device, [1] of those decoded window by window.  Waits for the device.
+static int read_route_stats(ebr_index *ix, uint64_t out[2]) {
+  out[0] = out[1] = 0;
+  if (!ix->ws.route_stats.p) return EBR_OK;
+  unsigned long long h[2];
+  EBR_CUDA_TRY(cudaMemcpy(h, ix->ws.route_stats.p, sizeof(h), cudaMemcpyDeviceToHost));
+  out[0] = h[0];
+  out[1] = h[1];
+  return EBR_OK;
+}
+
 extern "C" int ebr_profile_enable(ebr_index *ix, int on) {
   clear_error();
   if (!ix) {
@@ -1352,6 +1605,7 @@ extern "C" int ebr_profile_enable(ebr_index *ix, int on) {
   memset(&z, 0, sizeof(z));
   ebr_profile tmp;
   int rc = ebr_profile_read(ix, &tmp);  // drain pending events
+  if (rc == EBR_OK) rc = read_route_stats(ix, ix->route_base);
   ix->prof_acc = z;
   ix->prof = on != 0;
   return rc;
@@ -1387,6 +1641,10 @@ extern "C" int ebr_profile_read(ebr_index *ix, ebr_profile *out) {
   }
   ix->bprof_pending.clear();
   *out = ix->prof_acc;
+  uint64_t rs[2] = {0, 0};
+  EBR_TRY(read_route_stats(ix, rs));
+  out->auto_routed = rs[0] - ix->route_base[0];
+  out->window_routed = rs[1] - ix->route_base[1];
   out->launches = ix->launches;
   out->lib_launches = ix->lib_launches;
   out->batched = ix->batched;

@@ -29,6 +29,7 @@ F32, BF16, FP8E4M3 = 0, 1, 2
 W_DENSE, W_HASHED = 0, 1
 IO_DEVICE, IO_HOST = 0, 1
 QF_KEY_MAJOR = 1
+QF_WINDOW_MAJOR = 2
 _DTYPES = {"f32": F32, "bf16": BF16, "fp8e4m3": FP8E4M3}
 
 vp, u32, u64, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
@@ -79,7 +80,8 @@ class Profile(C.Structure):
                 ("ms_expand", C.c_double), ("ms_wide", C.c_double), ("ms_scan", C.c_double),
                 ("ms_final", C.c_double), ("batched", u64), ("recomputed", u64),
                 ("batch_calls", u64), ("ms_batch_stage", C.c_double),
-                ("ms_batch_scan", C.c_double), ("ms_batch_merge", C.c_double)]
+                ("ms_batch_scan", C.c_double), ("ms_batch_merge", C.c_double),
+                ("auto_routed", u64), ("window_routed", u64)]
 
 
 def _sig(name, res, args):

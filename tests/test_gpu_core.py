@@ -436,9 +436,13 @@ def test_recall_before_and_after_rescoring(dtype, capsys):
 
 @pytest.mark.parametrize("n_q", [1, 300, 3000])
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_topk_sparse_query_matches_oracle(n_q, dtype):
+@pytest.mark.parametrize("flags", [0, 1, 2], ids=["auto", "key_major", "window_major"])
+def test_topk_sparse_query_matches_oracle(n_q, dtype, flags):
     """The paper's own regime: a few keys carry non-zero w^ (the user's history
-    matches), so the key-major traversal (Algorithm 2) serves the request."""
+    matches).  Either Algorithm 2 scatters the wide term key by key, or the list
+    is summed into a dense w^ and the fused scan decodes it window by window;
+    by default the device picks one by the list's work."""
+    assert flags in (0, ebr.QF_KEY_MAJOR, ebr.QF_WINDOW_MAJOR)
     from paper_2511_22460_gb300.datagen import sparse_query
     n, k = 150_000, 500
     w, post, ix, cross = _setup("single_fp32_2m", n, seed=8, dtype=dtype)
@@ -452,8 +456,76 @@ def test_topk_sparse_query_matches_oracle(n_q, dtype):
     tol = 1e-5 * np.maximum(np.abs(ref), cond)
     ids = torch.empty(k, dtype=torch.int32, device=DEV)
     sc = torch.empty(k, dtype=torch.float32, device=DEV)
-    ebr.score_topk(ix, None, [ebr.Query(h_u=dev(w.h_u[0]), k=k, q_key=dev(qk), q_w=dev(qw))],
-                   ids, sc)
+    ebr.score_topk(ix, None, [ebr.Query(h_u=dev(w.h_u[0]), k=k, q_key=dev(qk), q_w=dev(qw),
+                                        flags=flags)], ids, sc)
     got = ids.cpu().numpy().view(np.uint32)
     assert recall(got, ref, tol, k) == 1.0
     check_topk(got, sc.cpu().numpy(), ref, tol, k)
+
+
+def test_sparse_route_chosen_by_work():
+    """A short list stays on Algorithm 2's scatter; a list whose blocks are a
+    large share of the index is decoded window by window; results match."""
+    from paper_2511_22460_gb300.datagen import sparse_query
+    n, k = 200_000, 200
+    w, post, ix, cross = _setup("single_fp32_2m", n, seed=12)
+    pk, pa = post
+    light = np.bincount(pk, minlength=w.n_keys).argsort()[:50].astype(np.uint32)
+    heavy, _ = sparse_query(w, 3000, seed=1)
+    ids = torch.empty(k, dtype=torch.int32, device=DEV)
+    sc = torch.empty(k, dtype=torch.float32, device=DEV)
+    rng = np.random.default_rng(2)
+    for qk, want in ((light, 0), (heavy, 1)):
+        qw = rng.standard_normal(qk.size).astype(np.float32)
+        ix.profile_enable(True)
+        ebr.score_topk(ix, None, [ebr.Query(h_u=dev(w.h_u[0]), k=k, q_key=dev(qk), q_w=dev(qw))],
+                       ids, sc)
+        p = ix.profile_read()
+        ix.profile_enable(False)
+        assert (p.auto_routed, p.window_routed) == (1, want)
+        ref = oracle.scores_postings(w.h_u[0], w.emb, w.n_keys, pk, pa, qk, qw)
+        wabs = np.zeros(w.n_keys)
+        np.add.at(wabs, qk, np.abs(qw.astype(np.float64)))
+        cond = np.abs(w.emb.astype(np.float64)) @ np.abs(w.h_u[0].astype(np.float64)) + \
+            np.bincount(pa, weights=wabs[pk], minlength=n)
+        tol = 1e-5 * np.maximum(np.abs(ref), cond)
+        check_topk(ids.cpu().numpy().view(np.uint32), sc.cpu().numpy(), ref, tol, k)
+
+
+def test_window_major_sparse_list_repeats_zero_weight_and_bad_key():
+    """The window-major route sums repeated keys, ignores zero weights and
+    rejects a key outside the key space, like Algorithm 2's route."""
+    n, k = 90_000, 300
+    w, post, ix, cross = _setup("single_fp32_2m", n, seed=5)
+    pk, pa = post
+    rng = np.random.default_rng(4)
+    heavy = np.bincount(pk, minlength=w.n_keys).argsort()[-10:]
+    qk = np.concatenate([rng.integers(0, w.n_keys, 200), heavy, heavy[:4]]).astype(np.uint32)
+    qw = rng.standard_normal(qk.size).astype(np.float32)
+    qw[7] = 0.0
+    ref = oracle.scores_postings(w.h_u[0], w.emb, w.n_keys, pk, pa, qk, qw)
+    wabs = np.zeros(w.n_keys)
+    np.add.at(wabs, qk, np.abs(qw.astype(np.float64)))
+    cond = np.abs(w.emb.astype(np.float64)) @ np.abs(w.h_u[0].astype(np.float64)) + np.bincount(
+        pa, weights=wabs[pk], minlength=n)
+    tol = 1e-5 * np.maximum(np.abs(ref), cond)
+    ids = torch.empty(k, dtype=torch.int32, device=DEV)
+    sc = torch.empty(k, dtype=torch.float32, device=DEV)
+    for flags in (0, ebr.QF_KEY_MAJOR, ebr.QF_WINDOW_MAJOR):
+        ebr.score_topk(ix, None, [ebr.Query(h_u=dev(w.h_u[0]), k=k, q_key=dev(qk), q_w=dev(qw),
+                                            flags=flags)], ids, sc)
+        got = ids.cpu().numpy().view(np.uint32)
+        check_topk(got, sc.cpu().numpy(), ref, tol, k)
+    # device-side input checks are reported by calls that wait for the device
+    # (host buffers); a device-buffer call is stream-ordered and does not wait
+    bad = ebr.Query(h_u=w.h_u[0].copy(), k=k, q_key=np.array([3, w.n_keys], np.uint32),
+                    q_w=np.array([1.0, 1.0], np.float32), flags=ebr.QF_WINDOW_MAJOR)
+    hid = np.empty(k, np.int32)
+    hsc = np.empty(k, np.float32)
+    with pytest.raises(ebr.EbrError) as e:
+        ebr.score_topk(ix, None, [bad], hid, hsc, io=ebr.IO_HOST)
+    assert e.value.code == ebr.EBR_EDATA
+    with pytest.raises(ebr.EbrError) as e:  # unknown flag bits
+        ebr.score_topk(ix, None, [ebr.Query(h_u=dev(w.h_u[0]), k=k, q_key=dev(qk), q_w=dev(qw),
+                                            flags=8)], ids, sc)
+    assert e.value.code == ebr.EBR_EINVAL
