@@ -62,6 +62,10 @@ def _load():
             lib.orc_scores_brute.argtypes = [u32, u32, vp, vp, vp, vp, vp, vp, vp]
             lib.orc_expand.restype = i32
             lib.orc_expand.argtypes = [vp, vp, vp, vp]
+            lib.orc_scores_brute_seq.restype = i32
+            lib.orc_scores_brute_seq.argtypes = [u32, u32, vp, vp, vp, vp, vp, vp, vp, vp]
+            lib.orc_expand_seq.restype = i32
+            lib.orc_expand_seq.argtypes = [vp, vp, vp, vp, vp]
             lib.orc_scores_postings.restype = i32
             lib.orc_scores_postings.argtypes = [u32, u32, vp, vp, u32, u64, vp, vp, u32, vp,
                                                 vp, vp]
@@ -157,6 +161,48 @@ def expand(cross: Cross, user):
     rc = lib.orc_expand(C.addressof(cross._s), _p(cross.key_off), _p(user), _p(out))
     if rc != 0:
         raise ValueError("orc_expand failed: %d" % rc)
+    return out
+
+
+EMPTY = 0xFFFFFFFF  # an ad field without a value
+
+
+def _seq(cross: Cross, user_ptr, user_vals):
+    user_ptr = _c(user_ptr, np.uint32)
+    user_vals = _c(user_vals, np.uint32)
+    assert user_ptr.shape == (len(cross.vocab_u) + 1,)
+    if user_vals.size == 0:
+        user_vals = np.zeros(1, np.uint32)
+    return user_ptr, user_vals
+
+
+def scores_brute_seq(cross: Cross, h_u, emb, ad_vals, user_ptr, user_vals, with_cond=False):
+    """O1 for multi-valued user fields: field i holds user_vals[user_ptr[i]:user_ptr[i+1]]."""
+    lib = _load()
+    emb = _c(emb, np.float32)
+    n, d = emb.shape
+    h_u = _c(h_u, np.float32)
+    ad_vals = _c(ad_vals, np.uint32)
+    user_ptr, user_vals = _seq(cross, user_ptr, user_vals)
+    assert ad_vals.shape == (n, len(cross.vocab_a)) and h_u.shape == (d,)
+    out = np.empty(n, dtype=np.float64)
+    cond = np.empty(n, dtype=np.float64) if with_cond else None
+    rc = lib.orc_scores_brute_seq(n, d, _p(h_u), _p(emb), C.addressof(cross._s), _p(ad_vals),
+                                  _p(user_ptr), _p(user_vals), _p(out), _p(cond))
+    if rc != 0:
+        raise ValueError("orc_scores_brute_seq failed: %d" % rc)
+    return (out, cond) if with_cond else out
+
+
+def expand_seq(cross: Cross, user_ptr, user_vals):
+    """Query expansion for multi-valued user fields: dense FP64 w_hat."""
+    lib = _load()
+    user_ptr, user_vals = _seq(cross, user_ptr, user_vals)
+    out = np.empty(cross.n_keys, dtype=np.float64)
+    rc = lib.orc_expand_seq(C.addressof(cross._s), _p(cross.key_off), _p(user_ptr),
+                            _p(user_vals), _p(out))
+    if rc != 0:
+        raise ValueError("orc_expand_seq failed: %d" % rc)
     return out
 
 
@@ -293,6 +339,15 @@ def score_query(w, b: int, cross: Cross = None, postings=None):
     pk, pa = postings if postings is not None else w.postings()
     # one value per ad field and disjoint key ranges per field: pairs are distinct
     return scores_postings(w.h_u[b], w.emb, w.n_keys, pk, pa, keys, wh[keys], assume_unique=True)
+
+
+def score_query_seq(w, h_u, user_ptr, user_vals, cross: Cross = None, postings=None):
+    """Full FP64 scores of a request with multi-valued user fields via O2."""
+    cross = cross or Cross.from_workload(w)
+    wh = expand_seq(cross, user_ptr, user_vals)
+    keys = np.nonzero(wh)[0].astype(np.uint32)
+    pk, pa = postings if postings is not None else w.postings()
+    return scores_postings(h_u, w.emb, w.n_keys, pk, pa, keys, wh[keys], assume_unique=True)
 
 
 def tolerance(scores_ref, cond, rel=1e-5):

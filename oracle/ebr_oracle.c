@@ -28,6 +28,9 @@
 #define ORC_OK 0
 #define ORC_EINVAL (-1)
 #define ORC_ENOMEM (-2)
+/* An ad field without a value: the ad lacks that feature (its row of the
+ * 0/1 matrix L has no non-zero in that field's key range). */
+#define ORC_EMPTY 0xFFFFFFFFu
 
 /* ------------------------------------------------------------------ */
 /* Cross weights                                                       */
@@ -88,10 +91,63 @@ int orc_scores_brute(uint32_t n_ads, uint32_t d, const float *h_u, const float *
     for (uint32_t p = 0; p < c->n_pairs; p++) {
       uint32_t i = c->pairs[2 * p], j = c->pairs[2 * p + 1];
       uint32_t v = ad_vals[(uint64_t)a * c->f_a + j];
+      if (v == ORC_EMPTY) continue;
       if (v >= c->vocab_a[j]) return ORC_EINVAL;
       double w = orc_weight(c, p, user[i], v);
       wide += w;
       mag += fabs(w);
+    }
+    scores[a] = dot + wide;
+    if (cond) cond[a] = mag;
+  }
+  return ORC_OK;
+}
+
+/* user_ptr [F_u + 1] must start at 0 and not decrease; every value must lie
+ * in its field's vocabulary. */
+static int orc_check_seq(const orc_cross *c, const uint32_t *user_ptr,
+                         const uint32_t *user_vals) {
+  if (user_ptr[0] != 0) return ORC_EINVAL;
+  for (uint32_t i = 0; i < c->f_u; i++) {
+    if (user_ptr[i + 1] < user_ptr[i]) return ORC_EINVAL;
+    for (uint32_t r = user_ptr[i]; r < user_ptr[i + 1]; r++)
+      if (user_vals[r] >= c->vocab_u[i]) return ORC_EINVAL;
+  }
+  return ORC_OK;
+}
+
+/*
+ * Multi-valued user fields (a user's history: field i holds the values
+ * user_vals[user_ptr[i] .. user_ptr[i+1]), possibly none).  Each (user
+ * value u, ad value v) of a cross pair (i, j) is one hit feature with x = 1
+ * (HitMatch equation, Sec. 3.3), so
+ *   scores[a] = sum_t h_u[t] h_a[t]
+ *             + sum_{(i,j) in P} sum_{u in field i} w_ij(u, ad_vals[a][j]),
+ * the pair's terms absent when ad field j is ORC_EMPTY.  With one value per
+ * field this is orc_scores_brute, term for term in the same order.
+ */
+int orc_scores_brute_seq(uint32_t n_ads, uint32_t d, const float *h_u, const float *emb,
+                         const orc_cross *c, const uint32_t *ad_vals, const uint32_t *user_ptr,
+                         const uint32_t *user_vals, double *scores, double *cond) {
+  if (orc_check_seq(c, user_ptr, user_vals) != ORC_OK) return ORC_EINVAL;
+  for (uint32_t a = 0; a < n_ads; a++) {
+    double dot = 0.0, mag = 0.0;
+    for (uint32_t t = 0; t < d; t++) {
+      double prod = (double)h_u[t] * (double)emb[(uint64_t)a * d + t];
+      dot += prod;
+      mag += fabs(prod);
+    }
+    double wide = 0.0;
+    for (uint32_t p = 0; p < c->n_pairs; p++) {
+      uint32_t i = c->pairs[2 * p], j = c->pairs[2 * p + 1];
+      uint32_t v = ad_vals[(uint64_t)a * c->f_a + j];
+      if (v == ORC_EMPTY) continue;
+      if (v >= c->vocab_a[j]) return ORC_EINVAL;
+      for (uint32_t r = user_ptr[i]; r < user_ptr[i + 1]; r++) {
+        double w = orc_weight(c, p, user_vals[r], v);
+        wide += w;
+        mag += fabs(w);
+      }
     }
     scores[a] = dot + wide;
     if (cond) cond[a] = mag;
@@ -121,6 +177,24 @@ int orc_expand(const orc_cross *c, const uint32_t *key_off, const uint32_t *user
     uint32_t i = c->pairs[2 * p], j = c->pairs[2 * p + 1];
     for (uint32_t v = 0; v < c->vocab_a[j]; v++)
       w_hat[key_off[j] + v] += orc_weight(c, p, user[i], v);
+  }
+  return ORC_OK;
+}
+
+/*
+ * The expansion for multi-valued user fields:
+ *   w_hat[key_off[j] + v] = sum_{i : (i, j) in P} sum_{u in field i} w_ij(u, v).
+ */
+int orc_expand_seq(const orc_cross *c, const uint32_t *key_off, const uint32_t *user_ptr,
+                   const uint32_t *user_vals, double *w_hat) {
+  uint32_t n_keys = key_off[c->f_a];
+  for (uint32_t k = 0; k < n_keys; k++) w_hat[k] = 0.0;
+  if (orc_check_seq(c, user_ptr, user_vals) != ORC_OK) return ORC_EINVAL;
+  for (uint32_t p = 0; p < c->n_pairs; p++) {
+    uint32_t i = c->pairs[2 * p], j = c->pairs[2 * p + 1];
+    for (uint32_t r = user_ptr[i]; r < user_ptr[i + 1]; r++)
+      for (uint32_t v = 0; v < c->vocab_a[j]; v++)
+        w_hat[key_off[j] + v] += orc_weight(c, p, user_vals[r], v);
   }
   return ORC_OK;
 }

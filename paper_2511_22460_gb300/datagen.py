@@ -88,6 +88,11 @@ RECIPES = {
 }
 
 
+# An ad field without a value in ``Workload.ad_vals`` (the ad lacks that
+# feature); such a field contributes no (key, ad) pair.
+EMPTY_VALUE = 0xFFFFFFFF
+
+
 @dataclass
 class Workload:
     """All synthetic arrays of one workload (host numpy arrays)."""
@@ -117,17 +122,21 @@ class Workload:
 
     @property
     def nnz(self) -> int:
-        return int(self.ad_vals.size)
+        return int(np.count_nonzero(self.ad_vals != EMPTY_VALUE))
 
     def postings(self, shuffle: bool = False):
         """Uncompressed feature->ad map L as (key, ad) pairs, ad-major order.
 
         The pairs are the raw input of index construction: ad ``a`` is in the
-        posting list of key(j, v) iff ad field j of ``a`` has value v.
+        posting list of key(j, v) iff ad field j of ``a`` has value v (an
+        EMPTY_VALUE field contributes no pair).
         """
         n, f_a = self.ad_vals.shape
         keys = (self.ad_vals + self.key_off[:f_a][None, :]).astype(np.uint32).reshape(-1)
         ads = np.repeat(np.arange(n, dtype=np.uint32), f_a)
+        empty = self.ad_vals.reshape(-1) == EMPTY_VALUE
+        if empty.any():
+            keys, ads = keys[~empty], ads[~empty]
         if shuffle:
             perm = self._rngs["shuffle"].permutation(keys.size)
             keys, ads = keys[perm], ads[perm]
@@ -245,6 +254,58 @@ def sparse_query(w: "Workload", n_q: int, seed: int = 0, var: float = 0.05):
     q_key = keys[np.sort(first)][:n_q]
     q_w = (rng.standard_normal(q_key.size) * np.sqrt(var)).astype(np.float32)
     return q_key, q_w
+
+
+def refreshed(w: "Workload", frac: float = 0.01, seed: int = 0) -> "Workload":
+    """The same inventory after an update of the feature->ad map L: a fraction
+    `frac` of the ads get new field values (uniform within each field's
+    vocabulary) and a new embedding row; everything else is shared with `w`.
+    Stands in for the periodic rebuild of the index from fresh logs."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 13])))
+    n, f_a = w.ad_vals.shape
+    ads = np.sort(rng.choice(n, size=max(1, int(frac * n)), replace=False))
+    vals = w.ad_vals.copy()
+    vals[ads] = (rng.random((ads.size, f_a)) * w.vocab_a[None, :]).astype(np.uint32)
+    vals[ads] = np.minimum(vals[ads], w.vocab_a[None, :] - 1)
+    emb = w.emb.copy()
+    d = emb.shape[1]
+    emb[ads] = (rng.standard_normal((ads.size, d)) / np.sqrt(d)).astype(np.float32)
+    return replace(w, ad_vals=vals, emb=emb,
+                   _rngs={"shuffle": np.random.Generator(np.random.PCG64(
+                       np.random.SeedSequence([seed, 14])))})
+
+
+def with_empty_ad_fields(w: "Workload", frac: float = 0.1, seed: int = 0) -> "Workload":
+    """The same workload with a fraction `frac` of all (ad, field) entries
+    emptied (set to EMPTY_VALUE): ads that lack some features."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 15])))
+    vals = w.ad_vals.copy()
+    vals[rng.random(vals.shape) < frac] = EMPTY_VALUE
+    return replace(w, ad_vals=vals,
+                   _rngs={"shuffle": np.random.Generator(np.random.PCG64(
+                       np.random.SeedSequence([seed, 16])))})
+
+
+def user_histories(w: "Workload", n_users: int, max_len: int = 8, seed: int = 0,
+                   p_empty: float = 0.1):
+    """Multi-valued user fields (a history of values per field): per user,
+    (user_ptr uint32 [F_u + 1], user_vals uint32 [user_ptr[-1]]).  Each field
+    holds 1..max_len values drawn uniformly (repeats allowed) from its
+    vocabulary, or none with probability p_empty."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 17])))
+    f_u = w.vocab_u.size
+    out = []
+    for _ in range(n_users):
+        lens = rng.integers(1, max_len + 1, size=f_u)
+        lens[rng.random(f_u) < p_empty] = 0
+        ptr = np.zeros(f_u + 1, np.uint32)
+        ptr[1:] = np.cumsum(lens)
+        vals = np.concatenate([
+            np.minimum((rng.random(int(n)) * int(w.vocab_u[i])).astype(np.uint32),
+                       np.uint32(w.vocab_u[i] - 1)) for i, n in enumerate(lens)]
+            + [np.zeros(0, np.uint32)]).astype(np.uint32)
+        out.append((ptr, vals))
+    return out
 
 
 def poisson_arrivals(rate_per_s: float, duration_s: float, seed: int = 0) -> np.ndarray:

@@ -49,3 +49,28 @@ def test_serving_recipe_draws_k_and_filters():
     assert np.all(np.diff(t) > 0) and 800 < t.size < 1200
     assert set(RECIPES) >= {"single_fp32_10k", "single_fp32_2m", "batch256_bf16_5m", "fp8_10m",
                             "serve_bf16_5m"}
+
+
+def test_histories_empty_fields_and_refresh():
+    from paper_2511_22460_gb300.datagen import (EMPTY_VALUE, refreshed, user_histories,
+                                                with_empty_ad_fields)
+    w = make_workload("single_fp32_10k", seed=0, n_ads=3000)
+    hs = user_histories(w, 20, max_len=6, seed=1)
+    f_u = w.vocab_u.size
+    for ptr, vals in hs:
+        assert ptr.shape == (f_u + 1,) and ptr[0] == 0 and np.all(np.diff(ptr.astype(int)) >= 0)
+        assert vals.size == ptr[-1] and np.all(np.diff(ptr.astype(int)) <= 6)
+        for i in range(f_u):
+            assert np.all(vals[ptr[i]:ptr[i + 1]] < w.vocab_u[i])
+    assert any(np.any(np.diff(p.astype(int)) == 0) for p, _ in hs)  # some empty field
+    again = user_histories(w, 20, max_len=6, seed=1)
+    assert all(np.array_equal(a[1], b[1]) for a, b in zip(hs, again))
+    we = with_empty_ad_fields(w, 0.2, seed=3)
+    frac = np.mean(we.ad_vals == EMPTY_VALUE)
+    assert 0.17 < frac < 0.23 and we.nnz == int(np.sum(we.ad_vals != EMPTY_VALUE))
+    pk, pa = we.postings()
+    assert pk.size == we.nnz and np.all(pk < w.n_keys)
+    w2 = refreshed(w, 0.05, seed=4)
+    changed = np.any(w2.ad_vals != w.ad_vals, axis=1) | np.any(w2.emb != w.emb, axis=1)
+    assert changed.sum() == 150 and w2.n_keys == w.n_keys
+    assert np.all(w2.ad_vals < w.vocab_a[None, :])

@@ -164,6 +164,91 @@ def test_linearity_duplicates_and_one_hot():
     np.testing.assert_array_equal(oh[~members], 0.0)
 
 
+# ------------------------------------ multi-valued user fields, empty ad fields
+
+def test_multi_valued_hand_example():
+    g = _load("score_seq_tiny.json")
+    cross = _tiny_cross(g)
+    emb = np.array(g["emb"], np.float32)
+    s, cond = oracle.scores_brute_seq(cross, g["h_u"], emb, g["ad_vals"], g["user_ptr"],
+                                      g["user_vals"], with_cond=True)
+    np.testing.assert_array_equal(s, g["expected_scores"])
+    np.testing.assert_array_equal(cond, g["expected_cond"])
+    wh = oracle.expand_seq(cross, g["user_ptr"], g["user_vals"])
+    np.testing.assert_array_equal(wh, g["expected_w_hat"])
+    ids, _ = oracle.topk(s, 2)
+    assert list(ids) == g["expected_top2_ids"]
+
+
+def test_one_value_per_field_reduces_to_single_valued():
+    w = _small(n_ads=800)
+    cross = oracle.Cross.from_workload(w)
+    ptr = np.arange(len(w.vocab_u) + 1, dtype=np.uint32)
+    a, ca = oracle.scores_brute_seq(cross, w.h_u[0], w.emb, w.ad_vals, ptr, w.users[0],
+                                    with_cond=True)
+    b, cb = oracle.scores_brute(cross, w.h_u[0], w.emb, w.ad_vals, w.users[0], with_cond=True)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(ca, cb)
+    np.testing.assert_array_equal(oracle.expand_seq(cross, ptr, w.users[0]),
+                                  oracle.expand(cross, w.users[0]))
+
+
+def test_history_is_additive_in_its_values():
+    # each (user value, ad value) is its own hit feature: w_hat is linear in
+    # the multiset of a field's values; an empty field adds nothing
+    w = _small(n_ads=200)
+    cross = oracle.Cross.from_workload(w)
+    f_u = len(w.vocab_u)
+    base = [int(x) for x in w.users[0]]
+    a, b = 1, min(2, int(w.vocab_u[0]) - 1)
+
+    def seq(first):
+        vals = list(first) + base[1:]
+        ptr = np.array([0, len(first)] + [len(first) + i for i in range(1, f_u)], np.uint32)
+        return ptr, np.array(vals, np.uint32)
+
+    e_ab = oracle.expand_seq(cross, *seq([a, b]))
+    e_a = oracle.expand_seq(cross, *seq([a]))
+    e_b = oracle.expand_seq(cross, *seq([b]))
+    e_0 = oracle.expand_seq(cross, *seq([]))
+    np.testing.assert_allclose(e_ab - e_a, e_b - e_0, rtol=1e-12, atol=1e-12)
+    e_aa = oracle.expand_seq(cross, *seq([a, a]))
+    np.testing.assert_allclose(e_aa - e_0, 2 * (e_a - e_0), rtol=1e-12, atol=1e-12)
+    # with every field empty the score is the dual-tower term alone
+    ptr0 = np.zeros(f_u + 1, np.uint32)
+    s = oracle.scores_brute_seq(cross, w.h_u[0], w.emb, w.ad_vals, ptr0, np.zeros(0, np.uint32))
+    np.testing.assert_allclose(s, w.emb.astype(np.float64) @ w.h_u[0].astype(np.float64),
+                               rtol=1e-13, atol=1e-15)
+
+
+def test_postings_oracle_equals_brute_force_with_histories_and_empty_fields():
+    from paper_2511_22460_gb300.datagen import user_histories, with_empty_ad_fields
+    w = with_empty_ad_fields(_small(n_ads=1500, seed=4), 0.15, seed=2)
+    cross = oracle.Cross.from_workload(w)
+    pk, pa = w.postings(shuffle=True)
+    assert pk.size == w.nnz < w.ad_vals.size
+    for ptr, vals in user_histories(w, 3, max_len=5, seed=7):
+        s1, cond = oracle.scores_brute_seq(cross, w.h_u[0], w.emb, w.ad_vals, ptr, vals,
+                                           with_cond=True)
+        s2 = oracle.score_query_seq(w, w.h_u[0], ptr, vals, cross, (pk, pa))
+        assert np.max(np.abs(s1 - s2) / np.maximum(cond, 1e-300)) < 1e-12
+
+
+def test_history_rejects_bad_offsets_and_values():
+    w = _small(n_ads=100)
+    cross = oracle.Cross.from_workload(w)
+    f_u = len(w.vocab_u)
+    good = np.arange(f_u + 1, dtype=np.uint32)
+    bad_ptr = good.copy()
+    bad_ptr[2], bad_ptr[3] = 3, 2  # decreasing
+    with pytest.raises(ValueError):
+        oracle.expand_seq(cross, bad_ptr, w.users[0])
+    vals = w.users[0].copy()
+    vals[1] = w.vocab_u[1]
+    with pytest.raises(ValueError):
+        oracle.scores_brute_seq(cross, w.h_u[0], w.emb, w.ad_vals, good, vals)
+
+
 def test_repeated_pairs_count_once():
     # L is binary (Sec. 3.3): listing a (key, ad) pair twice changes nothing.
     rng = np.random.default_rng(12)
