@@ -175,11 +175,31 @@ uint32_t ebr_cross_n_keys(const ebr_cross *c);
  */
 int ebr_expand_query(const ebr_cross *c, const uint32_t *user_vals, uint32_t batch,
                      float *w_hat, void *stream);
+/*
+ * The expansion of one user with multi-valued fields (history): field i
+ * holds user_vals[user_ptr[i] .. user_ptr[i+1]), and every value is one hit
+ * feature, so w_hat[key_off[j] + v] = sum over pairs (i, j) and values u of
+ * field i of w_ij(u, v) (HitMatch equation, Sec. 3.3).  user_ptr: device
+ * [f_u + 1], starting at 0, not decreasing, ending at n_user_vals;
+ * user_vals: device [n_user_vals]; w_hat: device [n_keys].  Bad offsets or a
+ * value outside its vocabulary give EBR_EDATA after the stream drains.
+ */
+int ebr_expand_query_seq(const ebr_cross *c, const uint32_t *user_ptr, const uint32_t *user_vals,
+                         uint32_t n_user_vals, float *w_hat, void *stream);
 
 /* ------------------------------------------------------------- queries */
 /*
  * One request.  The wide term's query is either
  *   - raw user features: user_vals[f_u], expanded with the call's cross model;
+ *   - multi-valued user features (a history per field): user_ptr[f_u + 1]
+ *     and user_vals[n_user_vals], field i holding user_vals[user_ptr[i] ..
+ *     user_ptr[i+1]) (none when equal); each (user value, ad value) of a
+ *     cross pair is one hit feature with x = 1 (HitMatch equation, Sec. 3.3),
+ *     so w^[key_off[j] + v] = sum over pairs (i, j) and values u of field i
+ *     of w_ij(u, v).  user_ptr must start at 0, not decrease and end at
+ *     n_user_vals; a violation or a value outside its vocabulary is a
+ *     device-side input error (EBR_EDATA).  Such requests take the
+ *     single-request scan, also inside a batch;
  *   - a dense weight vector: q_key == NULL, q_w[n_keys] indexed by key;
  *   - a sparse list: q_key[n_q], q_w[n_q] (duplicates add, keys must be < n_keys).
  * filter: targeting bitmap, bit a of word a >> 6 keeps ad a (NULL keeps all).
@@ -194,11 +214,15 @@ typedef struct {
   const uint64_t *filter;      /* [ceil(N / 64)] or NULL */
   uint32_t k;
   uint32_t flags;              /* EBR_QF_* bits */
+  const uint32_t *user_ptr;    /* [f_u + 1] or NULL (one value per field) */
+  uint32_t n_user_vals;        /* values in user_vals when user_ptr is set */
 } ebr_query;
 
 /* Walk the key-major arrays with Algorithm 2 (global scatter into a per-ad
- * score buffer) even when the query is dense; by default dense queries use
- * the fused window-major scan and sparse key lists use Algorithm 2. */
+ * score buffer) even when the query is dense.  By default dense queries use
+ * the fused window-major scan, and a sparse key list takes Algorithm 2 or
+ * the window-major decode, chosen on the device by its share of the index's
+ * work (the window-major decode from 1/8 of the index's work units on). */
 #define EBR_QF_KEY_MAJOR 1u
 /* For a sparse key list (q_key != NULL): sum the list into a dense w^ over the
  * key space (repeated keys add; a key >= n_keys fails the call with
@@ -367,6 +391,7 @@ typedef struct {
   uint64_t device_bytes;            /* device memory held by slots and workspaces */
   uint64_t slot_bytes;              /* device bytes of one request slot */
   double launch_ms, finish_ms;      /* worker host time staging+launching / waiting+publishing */
+  uint64_t index_swaps;             /* indexes swapped in by ebr_server_swap_index */
 } ebr_server_stats;
 
 /*
@@ -398,6 +423,21 @@ int ebr_server_reset_stats(ebr_server *s);
  */
 int ebr_server_completed(ebr_server *s, uint64_t *tickets, uint32_t cap, uint32_t *n);
 /* Stops the worker (requests still pending are dropped) and frees everything. */
+/*
+ * Serve every request not yet launched from `next` instead (the production
+ * mode of Sec. 3.4 and Sec. 4.3: the index is rebuilt from an updated
+ * feature->ad map L with ebr_build_index, off the serving loop, then swapped
+ * in without stopping it).  `next` must have the served index's n_ads,
+ * n_keys, d, embedding dtype and device, and fit the server's cross model.
+ * Batches already launched finish on the old index; no new batch starts
+ * until they have, so the call blocks for at most about one batch.  When it
+ * returns, the server no longer uses the old index and the caller may free
+ * it; the server never owns an index.  Requests keep their tickets across a
+ * swap.  It must not run concurrently with ebr_server_destroy.  Errors:
+ * EBR_EINVAL (null, shape mismatch, a swap already in progress),
+ * EBR_ENOMEM (workspace of `next`).
+ */
+int ebr_server_swap_index(ebr_server *s, ebr_index *next);
 int ebr_server_destroy(ebr_server *s);
 
 #ifdef __cplusplus

@@ -932,7 +932,7 @@ bool batch_qualifies(const ebr_index *ix, const ebr_cross *cross, const ebr_quer
       (uint64_t)(ix->n_keys + 1) * users_pow2(batch) >= (1ull << 32))
     return false;
   for (uint32_t b = 0; b < batch; b++) {
-    if (!q[b].user_vals || (q[b].flags & EBR_QF_KEY_MAJOR)) return false;
+    if (!q[b].user_vals || q[b].user_ptr || (q[b].flags & EBR_QF_KEY_MAJOR)) return false;
     if ((uint64_t)q[b].k * ix->rescore_mult > 8192) return false;
   }
   BatchPlan p;

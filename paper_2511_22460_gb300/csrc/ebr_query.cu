@@ -73,29 +73,51 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 // the pairs of its key issues only the weight gathers, independently of
 // each other.  With wmax set, the largest |w^| (FP32 bits) is max-reduced
 // into it (non-finite sums are flagged).
+// user_ptr != nullptr (batch 1 only): multi-valued user fields, field i
+// holding users[user_ptr[i] .. user_ptr[i+1]); every value is one hit
+// feature, so a pair (i, j) adds w_ij(u, v) for each u of field i.
 __global__ void k_expand(CrossView cv, const uint32_t *__restrict__ users, uint32_t batch,
                          float *__restrict__ w_hat, uint32_t *__restrict__ flags,
-                         uint32_t *__restrict__ wmax) {
+                         uint32_t *__restrict__ wmax, const uint32_t *__restrict__ user_ptr,
+                         uint32_t n_uv) {
   extern __shared__ uint32_t s_mem[];
+  __shared__ uint32_t s_seq_ok;
   uint32_t *s_off = s_mem;                    // key_off[f_a + 1]
   uint32_t *s_ptr = s_off + cv.f_a + 1;       // pair_ptr[f_a + 1]
   uint32_t *s_of = s_ptr + cv.f_a + 1;        // pair_of[n_pairs]
   uint32_t *s_usr = s_of + cv.n_pairs;        // pair_user[n_pairs]
   uint32_t *s_u = s_usr + cv.n_pairs;         // batch 1: u of each pair, or ~0u if out of range
+  uint32_t *s_up = s_u + cv.n_pairs;          // multi-valued: user_ptr[f_u + 1]
+  const bool multi = user_ptr != nullptr && batch == 1;
+  if (threadIdx.x == 0) s_seq_ok = 1;
   for (uint32_t j = threadIdx.x; j <= cv.f_a; j += blockDim.x) {
     s_off[j] = cv.key_off[j];
     s_ptr[j] = cv.pair_ptr[j];
+  }
+  if (multi) {
+    __syncthreads();  // s_seq_ok initialised
+    for (uint32_t i = threadIdx.x; i <= cv.f_u; i += blockDim.x) {
+      const uint32_t x = user_ptr[i];
+      s_up[i] = x;
+      const bool ok = i == 0 ? x == 0 : (user_ptr[i - 1] <= x && (i < cv.f_u || x == n_uv));
+      if (!ok) s_seq_ok = 0;
+    }
   }
   for (uint32_t q = threadIdx.x; q < cv.n_pairs; q += blockDim.x) {
     s_of[q] = cv.pair_of[q];
     const uint32_t i = cv.pair_user[q];
     s_usr[q] = i;
-    if (batch == 1) {
+    if (batch == 1 && !multi) {
       const uint32_t u = users[i];
       s_u[q] = u < cv.vocab_u[i] ? u : ~0u;
     }
   }
   __syncthreads();
+  if (multi && !s_seq_ok) {  // malformed offsets: flag, every field treated as empty
+    if (threadIdx.x == 0) atomicOr(flags, DEVERR_BAD_USER);
+    for (uint32_t i = threadIdx.x; i <= cv.f_u; i += blockDim.x) s_up[i] = 0;
+    __syncthreads();
+  }
   const uint64_t total = (uint64_t)batch * cv.n_keys;
   uint32_t bad = 0, mx = 0;
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
@@ -110,6 +132,28 @@ __global__ void k_expand(CrossView cv, const uint32_t *__restrict__ users, uint3
     const uint32_t j = lo, v = key - s_off[j];
     float acc = 0.f;
     const uint32_t q0 = s_ptr[j], q1 = s_ptr[j + 1];
+    if (multi) {
+      for (uint32_t q = q0; q < q1; q++) {
+        const uint32_t p = s_of[q];
+        const uint32_t i = s_usr[p];
+        for (uint32_t r = s_up[i]; r < s_up[i + 1]; r++) {
+          const uint32_t u = __ldg(users + r);
+          if (u >= cv.vocab_u[i]) { bad |= DEVERR_BAD_USER; continue; }
+          float w;
+          if (cv.hashed) {
+            uint64_t x = ((uint64_t)p << 40) | ((uint64_t)u << 20) | (uint64_t)v;
+            w = __ldg(cv.table + (splitmix64(x) & ((1ull << cv.hash_bits) - 1ull)));
+          } else {
+            uint64_t off = ((uint64_t)cv.w_hi[p] << 32) | cv.w_lo[p];
+            w = __ldg(cv.table + off + (uint64_t)u * cv.vocab_a[j] + v);
+          }
+          acc += w;
+        }
+      }
+      w_hat[t] = acc;
+      mx = max(mx, __float_as_uint(acc) & 0x7FFFFFFFu);
+      continue;
+    }
 #pragma unroll 4
     for (uint32_t q = q0; q < q1; q++) {
       const uint32_t p = s_of[q];
@@ -1043,10 +1087,16 @@ int expand_transposed(const ebr_cross *c, const uint32_t *users, uint32_t batch,
 }
 
 static int expand_into(const ebr_cross *c, const uint32_t *users, uint32_t batch, float *w_hat,
-                       uint32_t *flags, cudaStream_t st, uint32_t *wmax = nullptr) {
+                       uint32_t *flags, cudaStream_t st, uint32_t *wmax = nullptr,
+                       const uint32_t *user_ptr = nullptr, uint32_t n_uv = 0) {
   CrossView cv = cross_view(c);
   const uint64_t total = (uint64_t)batch * cv.n_keys;
-  const size_t smem = ((size_t)2 * (c->f_a + 1) + 3 * (size_t)c->n_pairs) * 4;
+  const size_t smem =
+      ((size_t)2 * (c->f_a + 1) + 3 * (size_t)c->n_pairs + (size_t)c->f_u + 1) * 4;
+  if (user_ptr && batch != 1) {
+    set_error("query expansion: multi-valued user fields are expanded one user at a time");
+    return EBR_EINVAL;
+  }
   if (smem > 48 * 1024)
     EBR_CUDA_TRY(cudaFuncSetAttribute(k_expand, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)std::min<size_t>(smem, 200 * 1024)));
@@ -1055,7 +1105,7 @@ static int expand_into(const ebr_cross *c, const uint32_t *users, uint32_t batch
     return EBR_EINVAL;
   }
   k_expand<<<launch_grid(total, 256, 65535), 256, smem, st>>>(cv, users, batch, w_hat, flags,
-                                                              wmax);
+                                                              wmax, user_ptr, n_uv);
   EBR_CUDA_TRY(cudaGetLastError());
   return EBR_OK;
 }
@@ -1106,7 +1156,7 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
   uint32_t n_q = q.n_q;
   if (q.user_vals) {
     EBR_TRY(expand_into(cross, q.user_vals, 1, (float *)w.w_dense.p, &ctrl->flags, st,
-                        &ctrl->pad));  // + max |w^| for the fused scan
+                        &ctrl->pad, q.user_ptr, q.n_user_vals));  // + max |w^| for the fused scan
     ix->launches += 1;
     q_key = nullptr;
     q_w = (const float *)w.w_dense.p;
@@ -1323,6 +1373,22 @@ extern "C" void ebr_cross_free(ebr_cross *c) {
 
 extern "C" uint32_t ebr_cross_n_keys(const ebr_cross *c) { return c ? c->n_keys : 0; }
 
+static int expand_checked(const ebr_cross *c, const uint32_t *user_vals, uint32_t batch,
+                          float *w_hat, void *stream, const uint32_t *user_ptr, uint32_t n_uv,
+                          const char *where);
+
+extern "C" int ebr_expand_query_seq(const ebr_cross *c, const uint32_t *user_ptr,
+                                    const uint32_t *user_vals, uint32_t n_user_vals,
+                                    float *w_hat, void *stream) {
+  clear_error();
+  if (!c || !user_ptr || !user_vals || !w_hat) {
+    set_error("ebr_expand_query_seq: null argument");
+    return EBR_EINVAL;
+  }
+  return expand_checked(c, user_vals, 1, w_hat, stream, user_ptr, n_user_vals,
+                        "ebr_expand_query_seq");
+}
+
 extern "C" int ebr_expand_query(const ebr_cross *c, const uint32_t *user_vals, uint32_t batch,
                                 float *w_hat, void *stream) {
   clear_error();
@@ -1331,6 +1397,14 @@ extern "C" int ebr_expand_query(const ebr_cross *c, const uint32_t *user_vals, u
     return EBR_EINVAL;
   }
   if (!batch) return EBR_OK;
+  return expand_checked(c, user_vals, batch, w_hat, stream, nullptr, 0, "ebr_expand_query");
+}
+
+// Expansion on the call's stream, then a wait for it and a check of the
+// device-side input flags.
+static int expand_checked(const ebr_cross *c, const uint32_t *user_vals, uint32_t batch,
+                          float *w_hat, void *stream, const uint32_t *user_ptr, uint32_t n_uv,
+                          const char *where) {
   int prev = 0;
   cudaGetDevice(&prev);
   EBR_CUDA_TRY(cudaSetDevice(c->device));
@@ -1338,19 +1412,19 @@ extern "C" int ebr_expand_query(const ebr_cross *c, const uint32_t *user_vals, u
   uint32_t *flags = nullptr;
   EBR_CUDA_TRY(cudaMallocAsync((void **)&flags, 4, st));
   EBR_CUDA_TRY(cudaMemsetAsync(flags, 0, 4, st));
-  int rc = expand_into(c, user_vals, batch, w_hat, flags, st);
+  int rc = expand_into(c, user_vals, batch, w_hat, flags, st, nullptr, user_ptr, n_uv);
   uint32_t hf = 0;
   if (rc == EBR_OK) {
     cudaError_t e = cudaMemcpyAsync(&hf, flags, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
-      set_error("ebr_expand_query: %s", cudaGetErrorString(e));
+      set_error("%s: %s", where, cudaGetErrorString(e));
       rc = EBR_ECUDA;
     }
   }
   cudaFreeAsync(flags, st);
   cudaSetDevice(prev);
-  if (rc == EBR_OK && hf) rc = check_device_flags(hf, "ebr_expand_query");
+  if (rc == EBR_OK && hf) rc = check_device_flags(hf, where);
   return rc;
 }
 
@@ -1364,6 +1438,10 @@ static int check_query(const ebr_index *ix, const ebr_cross *cross, const ebr_qu
   if (q.k == 0 || q.k > 8192) { set_error("query: k must be 1..8192 (got %u)", q.k); return EBR_EINVAL; }
   if (ix->dtype != EBR_F32 && (uint64_t)q.k * ix->rescore_mult > 8192) {
     set_error("query: R*k must be <= 8192 for BF16/FP8 scans");
+    return EBR_EINVAL;
+  }
+  if (q.user_ptr && !q.user_vals) {
+    set_error("query: user_ptr needs user_vals");
     return EBR_EINVAL;
   }
   if (q.user_vals) {
@@ -1385,8 +1463,9 @@ static int stage_in(ebr_index *ix, const ebr_cross *cross, const ebr_query &hq, 
   Workspace &w = ix->ws;
   const size_t words = ((size_t)ix->n_ads + 63) / 64;
   const size_t nq = hq.user_vals ? 0 : (hq.q_key ? hq.n_q : ix->n_keys);
-  size_t need = 256 + ix->d * 4 + 256 + (cross ? cross->f_u * 4 : 0) + 256 + nq * 8 + 256 +
-                (hq.filter ? words * 8 : 0) + 256;
+  const size_t n_uv = hq.user_ptr ? hq.n_user_vals : (cross ? cross->f_u : 0);
+  size_t need = 256 + ix->d * 4 + 256 + n_uv * 4 + 256 + nq * 8 + 256 +
+                (hq.filter ? words * 8 : 0) + 256 + (cross ? (cross->f_u + 1) * 4 : 0) + 256;
   EBR_TRY(dev_reserve(w.io_in, need));
   char *base = (char *)w.io_in.p;
   size_t off = 0;
@@ -1398,7 +1477,8 @@ static int stage_in(ebr_index *ix, const ebr_cross *cross, const ebr_query &hq, 
   };
   dq = hq;
   dq.h_u = (const float *)put(hq.h_u, ix->d * 4);
-  if (hq.user_vals) dq.user_vals = (const uint32_t *)put(hq.user_vals, cross->f_u * 4);
+  if (hq.user_vals) dq.user_vals = (const uint32_t *)put(hq.user_vals, n_uv * 4);
+  if (hq.user_ptr) dq.user_ptr = (const uint32_t *)put(hq.user_ptr, (cross->f_u + 1) * 4);
   if (!hq.user_vals) {
     if (hq.q_key) dq.q_key = (const uint32_t *)put(hq.q_key, (size_t)hq.n_q * 4);
     dq.q_w = (const float *)put(hq.q_w, (hq.q_key ? (size_t)hq.n_q : ix->n_keys) * 4);
@@ -1494,7 +1574,8 @@ static int single_query_prep(ebr_index *ix, const ebr_cross *cross, const ebr_qu
   *q_w = q->q_w;
   *n_q = q->n_q;
   if (q->user_vals) {
-    EBR_TRY(expand_into(cross, q->user_vals, 1, (float *)ix->ws.w_dense.p, &(*ctrl)->flags, st));
+    EBR_TRY(expand_into(cross, q->user_vals, 1, (float *)ix->ws.w_dense.p, &(*ctrl)->flags, st,
+                        nullptr, q->user_ptr, q->n_user_vals));
     *q_key = nullptr;
     *q_w = (const float *)ix->ws.w_dense.p;
     *n_q = ix->n_keys;

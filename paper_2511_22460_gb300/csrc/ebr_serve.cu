@@ -94,9 +94,13 @@ static size_t batch_ws_bytes(const ebr_index *ix, const ebr_cross *cross, uint32
 using namespace ebr;
 
 struct ebr_server {
-  ebr_index *ix = nullptr;
+  ebr_index *ix = nullptr;       // read and replaced by the worker thread only
+  ebr_index *next_ix = nullptr;  // an index waiting to replace ix (under mu)
+  bool swap_req = false;         // next_ix is set; no batch is launched until it is in
+  std::condition_variable swap_cv;
   const ebr_cross *cross = nullptr;
   int device = 0;
+  uint32_t d = 0;                // embedding dimension (the same for every index served)
   uint32_t max_batch = 64, max_slots = 256, k_max = 1000, timeout_ms = 0;
   uint32_t words = 0;
   bool batched_ok = false;
@@ -233,7 +237,15 @@ void worker_main(ebr_server *s) {
         }
         s->queue.swap(keep);
       }
-      for (int p = 0; p < 2 && lp < 0; p++)
+      if (s->swap_req && inflight.empty()) {  // no batch uses the old index any more
+        s->ix = s->next_ix;
+        s->next_ix = nullptr;
+        s->swap_req = false;
+        s->st.index_swaps += 1;
+        s->swap_cv.notify_all();
+      }
+      // while a swap waits, launched batches drain and nothing new starts
+      for (int p = 0; p < 2 && lp < 0 && !s->swap_req; p++)
         if (!s->pipes[p].busy) lp = p;
       if (lp >= 0 && !s->queue.empty()) {
         while (!s->queue.empty() && take.size() < s->max_batch) {
@@ -360,6 +372,7 @@ extern "C" int ebr_server_create(ebr_index *ix, const ebr_cross *cross, const eb
   EBR_CUDA_TRY(cudaSetDevice(ix->device));
   ebr_server *s = new ebr_server();
   s->ix = ix;
+  s->d = ix->d;
   s->cross = cross;
   s->device = ix->device;
   s->k_max = c.k_max;
@@ -454,8 +467,9 @@ extern "C" int ebr_submit(ebr_server *s, const ebr_query *q, uint64_t *ticket) {
     set_error("ebr_submit: needs a server, h_u and user_vals (host pointers) and a ticket");
     return EBR_EINVAL;
   }
-  if (q->k == 0 || q->k > s->k_max || q->q_key || q->q_w) {
-    set_error("ebr_submit: k must be 1..%u; q_key/q_w are not accepted", s->k_max);
+  if (q->k == 0 || q->k > s->k_max || q->q_key || q->q_w || q->user_ptr) {
+    set_error("ebr_submit: k must be 1..%u; q_key/q_w and multi-valued user fields "
+              "(user_ptr) are not accepted", s->k_max);
     return EBR_EINVAL;
   }
   for (uint32_t f = 0; f < s->cross->f_u; f++)
@@ -485,14 +499,13 @@ extern "C" int ebr_submit(ebr_server *s, const ebr_query *q, uint64_t *ticket) {
   sl.rc = EBR_OK;
   sl.err.clear();
   sl.t_submit = now_s();
-  const ebr_index *ix = s->ix;
-  memcpy(sl.h_hu, q->h_u, (size_t)ix->d * 4);
+  memcpy(sl.h_hu, q->h_u, (size_t)s->d * 4);
   memcpy(sl.h_uv, q->user_vals, (size_t)s->cross->f_u * 4);
   if (sl.has_filter) memcpy(sl.h_filter, q->filter, (size_t)s->words * 8);
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(s->device);
-  cudaError_t e = cudaMemcpyAsync(sl.d_hu, sl.h_hu, (size_t)ix->d * 4, cudaMemcpyHostToDevice,
+  cudaError_t e = cudaMemcpyAsync(sl.d_hu, sl.h_hu, (size_t)s->d * 4, cudaMemcpyHostToDevice,
                                   s->copy_st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(sl.d_uv, sl.h_uv, (size_t)s->cross->f_u * 4, cudaMemcpyHostToDevice,
@@ -607,6 +620,52 @@ extern "C" int ebr_server_completed(ebr_server *s, uint64_t *tickets, uint32_t c
   return EBR_OK;
 }
 
+extern "C" int ebr_server_swap_index(ebr_server *s, ebr_index *next) {
+  clear_error();
+  if (!s || !next) {
+    set_error("ebr_server_swap_index: null argument");
+    return EBR_EINVAL;
+  }
+  ebr_index *cur = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    cur = s->ix;
+    if (s->swap_req) {
+      set_error("ebr_server_swap_index: another swap is in progress");
+      return EBR_EINVAL;
+    }
+  }
+  if (next == cur) return EBR_OK;
+  if (next->n_ads != cur->n_ads || next->n_keys != cur->n_keys || next->d != cur->d ||
+      next->dtype != cur->dtype || next->device != cur->device) {
+    set_error("ebr_server_swap_index: the new index must have the served index's n_ads, "
+              "n_keys, d, dtype and device (%u/%u/%u/%d vs %u/%u/%u/%d)",
+              next->n_ads, next->n_keys, next->d, (int)next->dtype, cur->n_ads, cur->n_keys,
+              cur->d, (int)cur->dtype);
+    return EBR_EINVAL;
+  }
+  // the single-request workspace of the new index, reserved here so that the
+  // serving loop still allocates nothing
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  int rc = ws_prepare_one(next, next->n_keys, 8192);
+  cudaSetDevice(prev);
+  if (rc != EBR_OK) return rc;
+  std::unique_lock<std::mutex> lk(s->mu);
+  s->next_ix = next;
+  s->swap_req = true;
+  s->cv.notify_all();
+  s->swap_cv.wait(lk, [s] { return !s->swap_req || s->stop; });
+  if (s->swap_req) {  // the server stopped first
+    s->swap_req = false;
+    s->next_ix = nullptr;
+    set_error("ebr_server_swap_index: the server was destroyed");
+    return EBR_EINVAL;
+  }
+  return EBR_OK;
+}
+
 extern "C" int ebr_server_destroy(ebr_server *s) {
   clear_error();
   if (!s) return EBR_OK;
@@ -615,6 +674,7 @@ extern "C" int ebr_server_destroy(ebr_server *s) {
     s->stop = true;
   }
   s->cv.notify_all();
+  s->swap_cv.notify_all();
   if (s->worker.joinable()) s->worker.join();
   int prev = 0;
   cudaGetDevice(&prev);

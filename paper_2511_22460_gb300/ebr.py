@@ -59,7 +59,8 @@ class CrossDesc(C.Structure):
 
 class QueryC(C.Structure):
     _fields_ = [("h_u", vp), ("user_vals", vp), ("n_q", u32), ("q_key", vp), ("q_w", vp),
-                ("filter", vp), ("k", u32), ("flags", u32)]
+                ("filter", vp), ("k", u32), ("flags", u32), ("user_ptr", vp),
+                ("n_user_vals", u32)]
 
 
 class ServerCfg(C.Structure):
@@ -72,7 +73,8 @@ class ServerStats(C.Structure):
                 ("failed", u64), ("batches", u64), ("batched_requests", u64),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
                 ("max_batch", u32), ("max_slots", u32), ("device_bytes", u64),
-                ("slot_bytes", u64), ("launch_ms", C.c_double), ("finish_ms", C.c_double)]
+                ("slot_bytes", u64), ("launch_ms", C.c_double), ("finish_ms", C.c_double),
+                ("index_swaps", u64)]
 
 
 class Profile(C.Structure):
@@ -102,6 +104,7 @@ ebr_cross_create = _sig("ebr_cross_create", i32, [C.POINTER(CrossDesc), C.POINTE
 ebr_cross_free = _sig("ebr_cross_free", None, [vp])
 ebr_cross_n_keys = _sig("ebr_cross_n_keys", u32, [vp])
 ebr_expand_query = _sig("ebr_expand_query", i32, [vp, vp, u32, vp, vp])
+ebr_expand_query_seq = _sig("ebr_expand_query_seq", i32, [vp, vp, vp, u32, vp, vp])
 ebr_score_topk = _sig("ebr_score_topk", i32, [vp, vp, C.POINTER(QueryC), u32, vp, vp, i32, vp])
 ebr_score_all = _sig("ebr_score_all", i32, [vp, vp, C.POINTER(QueryC), vp, vp])
 ebr_wide_scores = _sig("ebr_wide_scores", i32, [vp, vp, C.POINTER(QueryC), vp, vp])
@@ -117,6 +120,7 @@ ebr_submit = _sig("ebr_submit", i32, [vp, C.POINTER(QueryC), C.POINTER(u64)])
 ebr_poll = _sig("ebr_poll", i32, [vp, u64, vp, vp])
 ebr_server_get_stats = _sig("ebr_server_get_stats", i32, [vp, vp])
 ebr_server_destroy = _sig("ebr_server_destroy", i32, [vp])
+ebr_server_swap_index = _sig("ebr_server_swap_index", i32, [vp, vp])
 ebr_server_reset_stats = _sig("ebr_server_reset_stats", i32, [vp])
 ebr_server_completed = _sig("ebr_server_completed", i32, [vp, vp, u32, C.POINTER(u32)])
 
@@ -267,6 +271,17 @@ def expand_query(cross: Cross, user_vals, w_hat, stream=None):
            "ebr_expand_query")
 
 
+def expand_query_seq(cross: Cross, user_ptr, user_vals, w_hat, stream=None):
+    """One user's expansion with multi-valued fields (device arrays)."""
+    n = int(user_vals.numel())
+    _check(ebr_expand_query_seq(cross.h, ptr(user_ptr), ptr(user_vals), n, ptr(w_hat),
+                                stream_ptr(stream)), "ebr_expand_query_seq")
+
+
+def _numel(x) -> int:
+    return int(x.numel() if hasattr(x, "numel") else x.size)
+
+
 @dataclass
 class Query:
     h_u: object
@@ -277,13 +292,15 @@ class Query:
     n_q: int = 0
     filter: object = None
     flags: int = 0
+    user_ptr: object = None  # multi-valued user fields: offsets [f_u + 1] into user_vals
 
     def c(self) -> QueryC:
         n_q = self.n_q
         if self.q_key is not None and not n_q:
-            n_q = int(self.q_key.numel() if hasattr(self.q_key, "numel") else self.q_key.size)
+            n_q = _numel(self.q_key)
+        n_uv = _numel(self.user_vals) if self.user_ptr is not None else 0
         return QueryC(ptr(self.h_u), ptr(self.user_vals), n_q, ptr(self.q_key), ptr(self.q_w),
-                      ptr(self.filter), int(self.k), int(self.flags))
+                      ptr(self.filter), int(self.k), int(self.flags), ptr(self.user_ptr), n_uv)
 
 
 def _queries(qs: Sequence[Query]):
@@ -387,6 +404,14 @@ class Server:
 
     def reset_stats(self):
         _check(ebr_server_reset_stats(self.h), "ebr_server_reset_stats")
+
+    def swap_index(self, index: Index) -> Index:
+        """Serve requests not yet launched from `index`; returns the index it
+        replaced, which the server no longer uses (ebr_server_swap_index)."""
+        _check(ebr_server_swap_index(self.h, index.h), "ebr_server_swap_index")
+        old = self._keep[0]
+        self._keep = (index, self._keep[1])
+        return old
 
     def completed(self, cap=4096):
         """Tickets finished since the previous call (done or failed)."""

@@ -529,3 +529,61 @@ def test_window_major_sparse_list_repeats_zero_weight_and_bad_key():
         ebr.score_topk(ix, None, [ebr.Query(h_u=dev(w.h_u[0]), k=k, q_key=dev(qk), q_w=dev(qw),
                                             flags=8)], ids, sc)
     assert e.value.code == ebr.EBR_EINVAL
+
+
+# ------------------------------ multi-valued user fields, empty ad fields
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_multi_valued_user_fields_and_empty_ad_fields(dtype):
+    """User fields holding histories (several values, some none) against ads
+    that lack some features: the expansion, and top-K alone, with host
+    buffers and inside a batch, against the FP64 oracle."""
+    from paper_2511_22460_gb300.datagen import user_histories, with_empty_ad_fields
+    n, k = 120_000, 300
+    w = with_empty_ad_fields(make_workload("single_fp32_2m", n_ads=n, seed=9, batch=3), 0.1,
+                             seed=2)
+    pk, pa = w.postings(shuffle=True)
+    ix = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype=dtype)
+    cross = ebr.cross_from_workload(w)
+    cr = oracle.Cross.from_workload(w)
+    cr_abs = oracle.Cross(w.vocab_u, w.vocab_a, w.pairs, np.abs(w.w_table), w.w_off,
+                          hashed=cr.hashed, hash_bits=cr.hash_bits)
+    hs = user_histories(w, 3, max_len=6, seed=4)
+    ptr, vals = hs[0]
+    wh = torch.empty(w.n_keys, dtype=torch.float32, device=DEV)
+    ebr.expand_query_seq(cross, dev(ptr), dev(vals), wh)
+    ref_wh = oracle.expand_seq(cr, ptr, vals)
+    mag = oracle.expand_seq(cr_abs, ptr, vals)
+    check_scores(wh.cpu().numpy(), ref_wh, 1e-6 * np.maximum(mag, 1e-30), "w_hat (history)")
+    refs = []
+    for b, (p_b, v_b) in enumerate(hs):
+        ref = oracle.score_query_seq(w, w.h_u[b], p_b, v_b, cr, (pk, pa))
+        _, cond = oracle.scores_brute_seq(cr, w.h_u[b], w.emb, w.ad_vals, p_b, v_b,
+                                          with_cond=True)
+        refs.append((ref, oracle.tolerance(ref, cond)))
+    ids = torch.empty((3, k), dtype=torch.int32, device=DEV)
+    sc = torch.empty((3, k), dtype=torch.float32, device=DEV)
+    qs = [ebr.Query(h_u=dev(w.h_u[b]), k=k, user_vals=dev(v_b), user_ptr=dev(p_b))
+          for b, (p_b, v_b) in enumerate(hs)]
+    ebr.score_topk(ix, cross, qs[:1], ids[0], sc[0])
+    got = ids[0].cpu().numpy().view(np.uint32)
+    assert recall(got, *refs[0], k) == 1.0
+    check_topk(got, sc[0].cpu().numpy(), *refs[0], k)
+    ebr.score_topk(ix, cross, qs, ids, sc)  # a batch: each request on the single-request scan
+    for b in range(3):
+        check_topk(ids[b].cpu().numpy().view(np.uint32), sc[b].cpu().numpy(), *refs[b], k)
+    hid = np.empty(k, np.int32)
+    hsc = np.empty(k, np.float32)
+    p1, v1 = hs[1]
+    ebr.score_topk(ix, cross, [ebr.Query(h_u=w.h_u[1].copy(), k=k, user_vals=v1, user_ptr=p1)],
+                   hid, hsc, io=ebr.IO_HOST)
+    check_topk(hid.view(np.uint32), hsc, *refs[1], k)
+    bad_end = p1.copy()
+    bad_end[-1] += 1  # offsets that do not end at the number of values
+    bad_order = p1.copy()
+    bad_order[1] = p1[-1] + 5  # decreasing offsets
+    for bad in (bad_end, bad_order):
+        with pytest.raises(ebr.EbrError) as e:
+            ebr.score_topk(ix, cross, [ebr.Query(h_u=w.h_u[1].copy(), k=k, user_vals=v1,
+                                                 user_ptr=bad)], hid, hsc, io=ebr.IO_HOST)
+        assert e.value.code == ebr.EBR_EDATA

@@ -10,7 +10,7 @@ if not torch.cuda.is_available():
 
 from gpu_util import bitmap_to_mask, check_topk, recall, ref_scores  # noqa: E402
 from paper_2511_22460_gb300 import ebr  # noqa: E402
-from paper_2511_22460_gb300.datagen import make_filters, make_workload  # noqa: E402
+from paper_2511_22460_gb300.datagen import make_filters, make_workload, refreshed  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -146,5 +146,64 @@ def test_fp32_index_server_matches_oracle():
             check_topk(res[b][0], res[b][1], ref, tol, 200)
         st = srv.stats()
         assert st.completed == B and st.p99_ms >= st.p50_ms > 0
+    finally:
+        srv.close()
+
+
+def _check_either(res, refs, k):
+    """The result matches the oracle of one of the indexes it may come from."""
+    errs = []
+    for ref, tol in refs:
+        try:
+            check_topk(res[0], res[1], ref, tol, k)
+            return
+        except AssertionError as e:
+            errs.append(str(e))
+    raise AssertionError("matches no index: %s" % errs)
+
+
+def test_index_swap_under_serving():
+    """The index is rebuilt from an updated feature->ad map and swapped in
+    while requests flow: later requests are answered from the new index,
+    requests in flight from one of the two, none fails, tickets survive;
+    an index of another shape is refused; swapping back works."""
+    n, k = 40_000, 200
+    w, post, ix, cross = _setup(n, 24)
+    w2 = refreshed(w, 0.05, seed=3)
+    post2 = w2.postings(shuffle=True)
+    srv = ebr.Server(ix, cross, max_batch=16, k_max=k)
+    try:
+        before = [srv.wait(srv.submit(w.h_u[b], w.users[b], k), k) for b in range(4)]
+        mid = [srv.submit(w.h_u[b], w.users[b], k) for b in range(4, 16)]
+        ix2 = ebr.build_index(w2.n_ads, w2.n_keys, post2[0], post2[1], w2.emb, dtype="bf16")
+        assert srv.swap_index(ix2) is ix
+        mid_res = [srv.wait(t, k) for t in mid]
+        after = [srv.wait(srv.submit(w.h_u[b], w.users[b], k), k) for b in range(16, 24)]
+        st = srv.stats()
+        assert st.index_swaps == 1 and st.failed == 0 and st.completed == 24
+        old = {b: ref_scores(w, b, post) for b in range(24)}
+        new = {b: ref_scores(w2, b, post2) for b in range(24)}
+        for b in (0, 3):
+            check_topk(before[b][0], before[b][1], *old[b], k)
+        for i, b in enumerate(range(4, 16)):
+            if i % 3 == 0:
+                _check_either(mid_res[i], (old[b], new[b]), k)
+        for i, b in enumerate(range(16, 24)):
+            check_topk(after[i][0], after[i][1], *new[b], k)
+        # the update is visible: some request's top-K changed with the index
+        assert any(set(after[i][0].tolist()) != set(
+            np.argsort(-old[b][0], kind="stable")[:k].tolist()) for i, b in enumerate(range(16, 24)))
+        wo = make_workload("serve_bf16_5m", n_ads=n // 2, seed=5, batch=1)
+        pko, pao = wo.postings()
+        ixo = ebr.build_index(wo.n_ads, wo.n_keys, pko, pao, wo.emb, dtype="bf16")
+        with pytest.raises(ebr.EbrError) as e:
+            srv.swap_index(ixo)
+        assert e.value.code == ebr.EBR_EINVAL
+        assert srv.swap_index(ix) is ix2  # and back
+        res = srv.wait(srv.submit(w.h_u[5], w.users[5], k), k)
+        check_topk(res[0], res[1], *old[5], k)
+        assert srv.stats().index_swaps == 2
+        print("\n[swap] rebuild of %d ads (%d postings) on the GPU: %.2f ms"
+              % (n, post2[0].size, ix2.info().build_ms))
     finally:
         srv.close()
