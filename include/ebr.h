@@ -433,8 +433,8 @@ int ebr_server_completed(ebr_server *s, uint64_t *tickets, uint32_t cap, uint32_
  * until they have, so the call blocks for at most about one batch.  When it
  * returns, the server no longer uses the old index and the caller may free
  * it; the server never owns an index.  Requests keep their tickets across a
- * swap.  It must not run concurrently with ebr_server_destroy.  Errors:
- * EBR_EINVAL (null, shape mismatch, a swap already in progress),
+ * swap.  Concurrent calls run one after another; none may run concurrently
+ * with ebr_server_destroy.  Errors: EBR_EINVAL (null, shape mismatch),
  * EBR_ENOMEM (workspace of `next`).
  */
 int ebr_server_swap_index(ebr_server *s, ebr_index *next);

@@ -98,6 +98,7 @@ struct ebr_server {
   ebr_index *next_ix = nullptr;  // an index waiting to replace ix (under mu)
   bool swap_req = false;         // next_ix is set; no batch is launched until it is in
   std::condition_variable swap_cv;
+  std::mutex swap_mu;            // one ebr_server_swap_index at a time
   const ebr_cross *cross = nullptr;
   int device = 0;
   uint32_t d = 0;                // embedding dimension (the same for every index served)
@@ -626,14 +627,11 @@ extern "C" int ebr_server_swap_index(ebr_server *s, ebr_index *next) {
     set_error("ebr_server_swap_index: null argument");
     return EBR_EINVAL;
   }
+  std::lock_guard<std::mutex> one_swap(s->swap_mu);  // concurrent swaps run one after another
   ebr_index *cur = nullptr;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    cur = s->ix;
-    if (s->swap_req) {
-      set_error("ebr_server_swap_index: another swap is in progress");
-      return EBR_EINVAL;
-    }
+    cur = s->ix;  // only a swap replaces it, and no other swap runs now
   }
   if (next == cur) return EBR_OK;
   if (next->n_ads != cur->n_ads || next->n_keys != cur->n_keys || next->d != cur->d ||
