@@ -204,6 +204,8 @@ def test_score_all_matches_oracle(name, n, flags):
 
 
 @pytest.mark.parametrize("name,n,k,flags", [("single_fp32_10k", 10_000, 100, 0),
+                                            # the benchmark's own size and launch (2M ads, K=500)
+                                            ("single_fp32_2m", 2_000_000, 500, 0),
                                             ("single_fp32_2m", 300_007, 500, 0),
                                             ("single_fp32_2m", 300_007, 500, ebr.QF_KEY_MAJOR),
                                             ("single_fp32_2m", 100_000, 2000, 0),
