@@ -312,18 +312,23 @@ int ebr_debug_wait_timeout(uint32_t timeout_us, void *stream);
  * number of eligible ads.  All pointers are device pointers on `device`:
  * emb [n_ads][d] FP32 row-major, h_u [d], wide [n_ads] or NULL, filter
  * (bit a of word a >> 6 keeps ad a) or NULL.  d is 4, 8, 16, 32, 64 or 128;
- * 1 <= k <= 1024, larger k returns EBR_EINVAL.
+ * 1 <= k <= 1024, larger k returns EBR_EINVAL.  emb must start on a 16-byte
+ * boundary (its rows are staged by bulk copies); a misaligned emb returns
+ * EBR_EINVAL before anything is launched.
  *
  * It allocates nothing: its scratch is a static device array of 1.25 MiB
  * (candidates of up to 160 CTAs x 1024, plus a 64-byte control block), held by
  * every GPU that loads this library until the process exits.  The first call
  * on a device looks up that array's device address (cudaGetSymbolAddress),
- * so make the first call on each device before any stream capture.  Every
+ * so make the first call on each device before any stream capture; the
+ * lookup is repeated when the device's context has been replaced (after
+ * cudaDeviceReset).  Every
  * call clears the control block and reuses the array, so calls whose work
  * overlaps on the GPU (different streams, or different host threads without
  * ordering) race and corrupt each other's results; order them on one stream.
  * Stream-ordered: returns before the GPU is done; device-side status is not
- * reported.
+ * reported, so a scan whose bounded device waits ran out (2 s) can leave an
+ * incomplete top-K in the outputs with no error returned.
  */
 int ebr_scan_topk_noalloc(const float *emb, uint32_t n_ads, uint32_t d, const float *h_u,
                           const float *wide, const uint64_t *filter, uint32_t k,
@@ -422,7 +427,6 @@ int ebr_server_reset_stats(ebr_server *s);
  * client poll only what is ready.
  */
 int ebr_server_completed(ebr_server *s, uint64_t *tickets, uint32_t cap, uint32_t *n);
-/* Stops the worker (requests still pending are dropped) and frees everything. */
 /*
  * Serve every request not yet launched from `next` instead (the production
  * mode of Sec. 3.4 and Sec. 4.3: the index is rebuilt from an updated
@@ -433,11 +437,17 @@ int ebr_server_completed(ebr_server *s, uint64_t *tickets, uint32_t cap, uint32_
  * until they have, so the call blocks for at most about one batch.  When it
  * returns, the server no longer uses the old index and the caller may free
  * it; the server never owns an index.  Requests keep their tickets across a
- * swap.  Concurrent calls run one after another; none may run concurrently
- * with ebr_server_destroy.  Errors: EBR_EINVAL (null, shape mismatch),
- * EBR_ENOMEM (workspace of `next`).
+ * swap.  Concurrent calls run one after another.  A call still waiting when
+ * ebr_server_destroy runs returns EBR_EINVAL ("the server was destroyed"),
+ * and destroy waits for it to return before freeing the server; a call made
+ * after destroy has begun is a use after free.  Errors: EBR_EINVAL (null,
+ * shape mismatch, server destroyed), EBR_ENOMEM (workspace of `next`).
  */
 int ebr_server_swap_index(ebr_server *s, ebr_index *next);
+/*
+ * Stops the worker (requests still pending are dropped), waits for swap
+ * calls in progress to return, and frees everything.
+ */
 int ebr_server_destroy(ebr_server *s);
 
 #ifdef __cplusplus

@@ -102,13 +102,21 @@ struct SlotDesc {                // one window's staged segments
 
 constexpr int kPrefetch = 4;  // producer reads window offsets this many windows ahead
 
-// The window accumulators hold each ad's wide term in 32-bit fixed point
-// (shared-memory integer atomics are fast where FP32 ones are not, and an
-// integer sum does not depend on the order of the additions): every slot adds
-// round(w^ * 2^F), and the term is the sum times 2^-F.  F is chosen per request
-// as the largest power of two with max|w^| * 2^F * (most keys of one ad) below
-// 2^31, so no sum can overflow; each term is then off by at most 2^-(F+1),
-// about 2^-31 of max|w^| times the key count, far inside the FP32 path's error.
+// The window accumulators hold each ad's wide term in two parts.  The main
+// part is 32-bit fixed point (shared-memory integer atomics are fast where
+// FP32 ones are not, and an integer sum does not depend on the order of the
+// additions): a slot adds f = round(w^ * 2^F) and the part is the sum times
+// 2^-F.  F is chosen per request as the largest power of two with
+// max|w^| * 2^F * (most keys of one ad) below 2^31, so no sum can overflow.
+// Rounding a term to the quantum 2^-F costs at most half a quantum, which is
+// small next to the term itself only when |f| is large: a term is kept in
+// fixed point only when |f| >= 2^kFixMinBits, so its relative error is below
+// 2^-(kFixMinBits+1).  Every other non-zero term (a weight far below the
+// request's largest) is added in FP32 to a second accumulator of the window.
+// So each ad's wide term is off by at most about 2^-19 of the sum of its
+// terms' magnitudes plus the FP32 error of its small terms: the bound follows
+// each ad's own weights, whatever the range of w^ over the request.
+constexpr int kFixMinBits = 18;
 __device__ __forceinline__ int fix_exponent(uint32_t wmax_bits, uint32_t max_keys) {
   const float wmax = __uint_as_float(wmax_bits);
   if (!(wmax > 0.f)) return 0;
@@ -160,6 +168,7 @@ __device__ __forceinline__ uint64_t hist_top_threshold(const uint32_t *gh, uint3
 
 struct FusedSmem {
   int acc[kAccBufs][kWin];
+  float accf[kAccBufs][kWin];  // FP32 part: terms too small for the fixed-point quantum
   uint32_t wp[kPrefetch][kGroups];  // producer's ring of window offsets
   uint32_t ctab[kTeams][kMaxChunkTab];  // per team: group << 16 | chunk within the group
   SlotDesc desc[kMaxIdxSlots];
@@ -197,7 +206,10 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
   const uint32_t w_end = (uint32_t)(((uint64_t)a.n_win * (blockIdx.x + 1)) / gridDim.x);
   const uint32_t my_wins = w_end - w_begin;
 
-  for (int i = tid; i < kAccBufs * kWin; i += kFusedThreads) (&sm.acc[0][0])[i] = 0;
+  for (int i = tid; i < kAccBufs * kWin; i += kFusedThreads) {
+    (&sm.acc[0][0])[i] = 0;
+    (&sm.accf[0][0])[i] = 0.f;
+  }
   // whether the wide term comes precomputed (no window decoding) in this launch
   const bool pre = a.wide_in != nullptr && !(a.route && *a.route);
   const int fx_e = fix_exponent(*a.wmax_bits, a.max_keys);
@@ -445,14 +457,22 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
           first[q] = wi == 0;
           valid[q] = v;
         }
+        // fx[q]: the fixed-point term, or (bit q of `small` set) the FP32
+        // bits of a non-zero weight too small for the quantum
         int fx[kChunksInFlight];
+        uint32_t small = 0;
 #pragma unroll
-        for (int q = 0; q < kChunksInFlight; q++)
-          fx[q] = valid[q] ? __float2int_rn(__ldg(a.w_hat + key[q]) * fx_scale) : 0;
+        for (int q = 0; q < kChunksInFlight; q++) {
+          const float wv = valid[q] ? __ldg(a.w_hat + key[q]) : 0.f;
+          const int f = __float2int_rn(wv * fx_scale);
+          const bool tiny = wv != 0.f && (f < (1 << kFixMinBits) && f > -(1 << kFixMinBits));
+          small |= (tiny ? 1u : 0u) << q;
+          fx[q] = tiny ? __float_as_int(wv) : f;
+        }
 #pragma unroll
         for (int q = 0; q < kChunksInFlight; q++) {
           const uint32_t g = gq[q];
-          const bool add = fx[q] != 0;
+          const bool add = fx[q] != 0 && !((small >> q) & 1u);
           if (g >= 2 && g < (uint32_t)kGroups) {
 #pragma unroll
             for (int s2 = 0; s2 < 4; s2++) {
@@ -465,6 +485,21 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
             if (add && l != 0) atomicAdd(&acc[l], fx[q]);
           } else if (g == 0) {
             if (add) atomicAdd(&acc[word[q] & 255u], fx[q]);
+          }
+        }
+        if (__any_sync(0xffffffffu, small != 0)) {
+          // rare: the same slots, FP32 additions of the small terms
+          float *accf = sm.accf[b];
+#pragma unroll
+          for (int q = 0; q < kChunksInFlight; q++) {
+            if (!((small >> q) & 1u)) continue;
+            const uint32_t g = gq[q];
+            const float wv = __int_as_float(fx[q]);
+            const uint32_t ns = g >= 2 ? 4u : (g == 1 ? 2u : 1u);
+            for (uint32_t s2 = 0; s2 < ns; s2++) {
+              const uint32_t l = (word[q] >> (8 * s2)) & 255u;
+              if ((s2 == 0 && (first[q] || g < 2)) || l != 0) atomicAdd(&accf[l], wv);
+            }
           }
         }
       }
@@ -544,7 +579,8 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       const bool leader = valid && qd == 0;
       float score = 0.f;
       if (leader) {
-        const float wide = pre ? __ldg(a.wide_in + ad) : (float)acc[rw] * fx_unit;
+        const float wide =
+            pre ? __ldg(a.wide_in + ad) : (float)acc[rw] * fx_unit + sm.accf[b][rw];
         score = dot;
         if (a.scale) score *= a.scale[ad];
         score += wide;
@@ -570,7 +606,10 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       }
     }
     gsync();  // the window's accumulator is fully read; appends visible
-    for (int i = tid; i < kWin; i += kDotThreads) sm.acc[b][i] = 0;  // hand it back, zeroed
+    for (int i = tid; i < kWin; i += kDotThreads) {  // hand it back, zeroed
+      sm.acc[b][i] = 0;
+      sm.accf[b][i] = 0.f;
+    }
     mbar_arrive(&sm.acc_empty[b]);
     if (!ALL && sm.n + kWin > a.cap) {
       // trim the candidates to the K best: radix select, then a stable

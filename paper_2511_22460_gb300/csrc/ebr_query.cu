@@ -1755,7 +1755,27 @@ static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocWo
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+void *g_noalloc_ctx[kNoAllocMaxDevices] = {nullptr};  // context the address belongs to
 int g_noalloc_sms[kNoAllocMaxDevices] = {0};
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+
+// The current driver context (nullptr if it cannot be read): a device reset
+// replaces the primary context, and with it the array's device address.
+void *current_context() {
+  if (!g_ctx_get_current) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return nullptr;
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+  }
+  CUcontext c = nullptr;
+  if (g_ctx_get_current(&c) != CUDA_SUCCESS) return nullptr;
+  return reinterpret_cast<void *>(c);
+}
 
 template <int D>
 int noalloc_launch(const ScanArgs &a0, int sms, cudaStream_t st) {
@@ -1791,6 +1811,11 @@ extern "C" int ebr_scan_topk_noalloc(const float *emb, uint32_t n_ads, uint32_t 
     set_error("ebr_scan_topk_noalloc: null pointer or n_ads == 0");
     return EBR_EINVAL;
   }
+  if ((reinterpret_cast<uintptr_t>(emb) & 15u) != 0) {
+    // the scan stages rows with bulk copies, which start on 16-byte boundaries
+    set_error("ebr_scan_topk_noalloc: emb must be 16-byte aligned");
+    return EBR_EINVAL;
+  }
   if (k == 0 || k > kNoAllocMaxK) {
     set_error("ebr_scan_topk_noalloc: k = %u is outside 1..%u (the static scratch holds %u "
               "candidates per CTA)", k, kNoAllocMaxK, kNoAllocMaxK);
@@ -1810,13 +1835,16 @@ extern "C" int ebr_scan_topk_noalloc(const float *emb, uint32_t n_ads, uint32_t 
   void *base = nullptr;
   int sms = 0;
   {
-    // One-time set-up per device, with that device current: resolve the
+    // Set-up once per device, with that device current (and again if the
+    // device's context was replaced, as cudaDeviceReset does): resolve the
     // device address of the static scratch array (the host-side symbol is
     // only a stand-in and must never reach a kernel).
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[device]) {
+    void *ctx = current_context();
+    if (!g_noalloc_addr[device] || ctx != g_noalloc_ctx[device]) {
       void *p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // creates the context if needed
+      ctx = current_context();
       if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&g_noalloc_sms[device], cudaDevAttrMultiProcessorCount,
                                    device);
@@ -1826,6 +1854,7 @@ extern "C" int ebr_scan_topk_noalloc(const float *emb, uint32_t n_ads, uint32_t 
         return EBR_ECUDA;
       }
       g_noalloc_addr[device] = p;
+      g_noalloc_ctx[device] = ctx;
     }
     base = g_noalloc_addr[device];
     sms = g_noalloc_sms[device];

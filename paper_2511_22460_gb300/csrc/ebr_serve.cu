@@ -99,6 +99,7 @@ struct ebr_server {
   bool swap_req = false;         // next_ix is set; no batch is launched until it is in
   std::condition_variable swap_cv;
   std::mutex swap_mu;            // one ebr_server_swap_index at a time
+  uint32_t swappers = 0;         // swap calls inside the server (under mu); destroy waits for 0
   const ebr_cross *cross = nullptr;
   int device = 0;
   uint32_t d = 0;                // embedding dimension (the same for every index served)
@@ -627,10 +628,32 @@ extern "C" int ebr_server_swap_index(ebr_server *s, ebr_index *next) {
     set_error("ebr_server_swap_index: null argument");
     return EBR_EINVAL;
   }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {
+      set_error("ebr_server_swap_index: the server was destroyed");
+      return EBR_EINVAL;
+    }
+    s->swappers++;
+  }
+  // leaves the count (after swap_mu is released: declared before it) and
+  // wakes a destroy that waits for the swap calls to return
+  struct Leave {
+    ebr_server *s;
+    ~Leave() {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->swappers--;
+      s->swap_cv.notify_all();
+    }
+  } leave{s};
   std::lock_guard<std::mutex> one_swap(s->swap_mu);  // concurrent swaps run one after another
   ebr_index *cur = nullptr;
   {
     std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {  // destroyed while this call waited for the previous swap
+      set_error("ebr_server_swap_index: the server was destroyed");
+      return EBR_EINVAL;
+    }
     cur = s->ix;  // only a swap replaces it, and no other swap runs now
   }
   if (next == cur) return EBR_OK;
@@ -674,6 +697,11 @@ extern "C" int ebr_server_destroy(ebr_server *s) {
   s->cv.notify_all();
   s->swap_cv.notify_all();
   if (s->worker.joinable()) s->worker.join();
+  {
+    // swap calls still inside the server see `stop` and return; wait for them
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->swap_cv.wait(lk, [s] { return s->swappers == 0; });
+  }
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(s->device);

@@ -334,11 +334,56 @@ def quantize(x, dtype, out, stream=None):
     _check(ebr_quantize(ptr(x), int(x.numel()), dt, ptr(out), stream_ptr(stream)), "ebr_quantize")
 
 
-def scan_topk_noalloc(emb, h_u, wide, filt, k, out_ids, out_scores, device=0, stream=None):
-    """Allocation-free scan + top-K over caller-owned device buffers."""
-    _check(ebr_scan_topk_noalloc(ptr(emb), int(emb.shape[0]), int(emb.shape[1]), ptr(h_u),
-                                 ptr(wide), ptr(filt), int(k), ptr(out_ids), ptr(out_scores),
-                                 device, stream_ptr(stream)), "ebr_scan_topk_noalloc")
+NOALLOC_DIMS = (4, 8, 16, 32, 64, 128)
+NOALLOC_MAX_K = 1024
+
+
+def scan_topk_noalloc(emb, h_u, wide, filt, k, out_ids, out_scores, stream=None):
+    """Allocation-free scan + top-K over caller-owned device buffers.
+
+    Every tensor must be a contiguous CUDA tensor on emb's device: emb
+    float32 [n_ads][d] with d in NOALLOC_DIMS, h_u float32 [d], wide float32
+    [n_ads] or None, filt int64/uint64 words [>= ceil(n_ads / 64)] or None,
+    out_ids int32/uint32 [>= k], out_scores float32 [>= k]; 1 <= k <= 1024.
+    The shapes are checked here, before anything reaches the device, because
+    the kernel trusts them (a short buffer would be read or written out of
+    bounds rather than rejected)."""
+    import torch
+
+    def need(cond, msg):
+        if not cond:
+            raise ValueError("scan_topk_noalloc: " + msg)
+
+    k = int(k)
+    need(isinstance(emb, torch.Tensor) and emb.dim() == 2, "emb must be a 2-D tensor")
+    need(emb.dtype == torch.float32, "emb must be float32")
+    need(emb.is_contiguous(), "emb must be contiguous")
+    n_ads, d = int(emb.shape[0]), int(emb.shape[1])
+    need(n_ads > 0 and d in NOALLOC_DIMS, "need n_ads > 0 and d in %s" % (NOALLOC_DIMS,))
+    need(1 <= k <= NOALLOC_MAX_K, "k must be in 1..%d" % NOALLOC_MAX_K)
+
+    def vec(t, name, dtypes, min_len):
+        need(isinstance(t, torch.Tensor), "%s must be a tensor" % name)
+        need(t.dtype in dtypes, "%s must have dtype in %s" % (name, dtypes))
+        need(t.is_contiguous(), "%s must be contiguous" % name)
+        need(t.numel() >= min_len, "%s needs at least %d elements" % (name, min_len))
+
+    vec(h_u, "h_u", (torch.float32,), d)
+    if wide is not None:
+        vec(wide, "wide", (torch.float32,), n_ads)
+    if filt is not None:
+        vec(filt, "filter", (torch.int64, torch.uint64), (n_ads + 63) // 64)
+    vec(out_ids, "out_ids", (torch.int32, torch.uint32), k)
+    vec(out_scores, "out_scores", (torch.float32,), k)
+    need(emb.is_cuda, "emb must be a CUDA tensor")
+    device = emb.device.index if emb.device.index is not None else torch.cuda.current_device()
+    for name, t in (("h_u", h_u), ("wide", wide), ("filter", filt), ("out_ids", out_ids),
+                    ("out_scores", out_scores)):
+        need(t is None or (t.is_cuda and t.device.index == device),
+             "%s must be on emb's device (cuda:%d)" % (name, device))
+    _check(ebr_scan_topk_noalloc(ptr(emb), n_ads, d, ptr(h_u), ptr(wide), ptr(filt), k,
+                                 ptr(out_ids), ptr(out_scores), device, stream_ptr(stream)),
+           "ebr_scan_topk_noalloc")
 
 
 def debug_wait_timeout(timeout_us, stream=None):

@@ -110,13 +110,16 @@ def test_expand_query_matches_oracle(name):
     w = make_workload(name, n_ads=1000, batch=5, seed=4)
     cross = ebr.cross_from_workload(w)
     oc = oracle.Cross.from_workload(w)
+    oc_abs = oracle.Cross(w.vocab_u, w.vocab_a, w.pairs, np.abs(w.w_table), w.w_off,
+                          hashed=oc.hashed, hash_bits=oc.hash_bits)
     out = torch.empty((5, w.n_keys), dtype=torch.float32, device=DEV)
     ebr.expand_query(cross, dev(w.users), out)
     got = out.cpu().numpy()
     for b in range(5):
         ref = oracle.expand(oc, w.users[b])
-        tol = 1e-6 * np.maximum(np.abs(ref), 1e-30) + 4e-7 * 8
-        np.testing.assert_allclose(got[b], ref, rtol=2e-6, atol=1e-6)
+        # the Z8 form: relative to the sum of the magnitudes of the summed weights
+        mag = oracle.expand(oc_abs, w.users[b])
+        check_scores(got[b], ref, 1e-5 * np.maximum(np.abs(ref), mag) + 1e-30, "w_hat")
     bad = w.users.copy()
     bad[2, 1] = w.vocab_u[1]
     with pytest.raises(ebr.EbrError) as e:

@@ -63,6 +63,8 @@ def test_alone_and_in_a_mix_give_the_same_result():
         st = srv.stats()
         assert st.completed == B + len(probe) and st.failed == 0
         assert st.batches < B + len(probe), "requests were never batched"
+        prof = ix.profile_read()
+        assert prof.batched > 0 and prof.recomputed == 0, "batched users were recomputed"
         for b in probe + [1, 2, 5, 39]:
             ref, tol = ref_scores(w, b, post)
             mask = None if filt[b] is None else bitmap_to_mask(filt[b], n)
@@ -207,3 +209,40 @@ def test_index_swap_under_serving():
               % (n, post2[0].size, ix2.info().build_ms))
     finally:
         srv.close()
+
+
+def test_destroy_while_swap_calls_wait():
+    """ebr_server_destroy runs while one swap call is waiting for the worker to
+    take the new index and a second waits for the first: destroy waits for
+    both to return (each either swapped or reports that the server was
+    destroyed) before it frees the server."""
+    import threading
+    import time
+    n, k = 40_000, 100
+    w, post, ix, cross = _setup(n, 48)
+    w2 = refreshed(w, 0.05, seed=4)
+    p2 = w2.postings()
+    ix2 = ebr.build_index(w2.n_ads, w2.n_keys, p2[0], p2[1], w2.emb, dtype="bf16")
+    for trial in range(3):
+        srv = ebr.Server(ix, cross, max_batch=16, k_max=k)
+        for b in range(48):  # keep the worker busy so that the swaps have to wait
+            srv.submit(w.h_u[b], w.users[b], k)
+        h = srv.h
+        out, entered = [], threading.Semaphore(0)
+
+        def swap(target):
+            entered.release()
+            out.append(ebr.ebr_server_swap_index(h, target.h))
+
+        ts = [threading.Thread(target=swap, args=(x,)) for x in (ix2, ix)]
+        for t in ts:
+            t.start()
+        for _ in ts:
+            entered.acquire()
+        time.sleep(0.05 + 0.02 * trial)  # both calls are inside the server by now
+        assert ebr.ebr_server_destroy(h) == ebr.EBR_OK
+        srv.h = None
+        for t in ts:
+            t.join(timeout=30)
+        assert not any(t.is_alive() for t in ts)
+        assert sorted(out) and all(rc in (ebr.EBR_OK, ebr.EBR_EINVAL) for rc in out), out

@@ -76,6 +76,27 @@ def test_noalloc_rejects_k_beyond_its_scratch():
     h = torch.zeros(16, dtype=torch.float32, device=DEV)
     ids = torch.empty(2000, dtype=torch.int32, device=DEV)
     sc = torch.empty(2000, dtype=torch.float32, device=DEV)
-    with pytest.raises(ebr.EbrError) as e:
+    with pytest.raises(ValueError):  # the binding refuses it first
         ebr.scan_topk_noalloc(emb, h, None, None, 1025, ids, sc)
+    # and so does the C ABI itself
+    rc = ebr.ebr_scan_topk_noalloc(emb.data_ptr(), 1000, 16, h.data_ptr(), None, None, 1025,
+                                   ids.data_ptr(), sc.data_ptr(), 0, None)
+    assert rc == ebr.EBR_EINVAL
+
+
+def test_noalloc_rejects_a_misaligned_table_on_the_host():
+    """A view whose first row is not 16-byte aligned is refused before any
+    launch (its rows are staged by bulk copies, which need that alignment)."""
+    base = torch.zeros(1000 * 16 + 1, dtype=torch.float32, device=DEV)
+    emb = base[1:].view(1000, 16)
+    assert emb.data_ptr() % 16 != 0
+    h = torch.zeros(16, dtype=torch.float32, device=DEV)
+    ids = torch.empty(10, dtype=torch.int32, device=DEV)
+    sc = torch.empty(10, dtype=torch.float32, device=DEV)
+    with pytest.raises(ebr.EbrError) as e:
+        ebr.scan_topk_noalloc(emb, h, None, None, 10, ids, sc)
     assert e.value.code == ebr.EBR_EINVAL
+    # the context is untouched: an aligned call right after works
+    ebr.scan_topk_noalloc(base[4:4 + 999 * 16].view(999, 16), h, None, None, 10, ids, sc)
+    torch.cuda.synchronize()
+    assert torch.all(ids >= 0)
