@@ -4,6 +4,9 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
 
 namespace ebr {
 
@@ -78,12 +81,25 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+// The same test, letting the hardware suspend the thread for up to
+// suspend_ns (or until the phase completes, whichever comes first) instead
+// of returning at once: a waiting warp then issues almost nothing.
+__device__ __forceinline__ uint32_t mbar_try_wait_suspend(uint64_t *b, uint32_t parity,
+                                                          uint32_t suspend_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity), "r"(suspend_ns)
+      : "memory");
+  return ok;
+}
 // Wait for phase `parity` of barrier b, giving up after timeout_ns.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity,
                                                   uint64_t timeout_ns) {
   if (mbar_try_wait(b, parity)) return true;
   uint64_t t0 = global_timer_ns();
-  while (!mbar_try_wait(b, parity)) {
+  while (!mbar_try_wait_suspend(b, parity, 1000000u)) {
     if (global_timer_ns() - t0 > timeout_ns) return false;
   }
   return true;
@@ -263,6 +279,72 @@ __device__ __forceinline__ uint64_t hist_threshold(const uint32_t *hist_c, const
   if (!bal) return ((uint64_t)((uint32_t)cb << 24)) << 32;  // coarse bound only
   const int fb = __shfl_sync(0xffffffffu, found, __ffs(bal) - 1);
   return ((uint64_t)(((uint32_t)cb << 24) | ((uint32_t)fb << 16))) << 32;
+}
+
+// ------------------------------------------------- fixed-point wide terms
+// The window accumulators hold each ad's wide term in 32-bit fixed point
+// (shared-memory integer atomics run several times faster than FP32 or 64-bit
+// ones on this part, and an integer sum does not depend on the order of the
+// additions), in three exponent classes plus an FP32 remainder:
+//   a weight w is turned into a term of class c in {0, 1, 2}, the first one
+//   with |w| * 2^(F + c S) >= 2^kFixMinBits, and adds f = round(w * 2^(F + c S))
+//   to accumulator c; a weight below all three classes is added in FP32.
+// The ad's wide term is sum_c acc_c * 2^-(F + c S) + acc_fp32.  Every integer
+// term has at least kFixMinBits significant bits, so its rounding error is
+// below 2^-(kFixMinBits + 1) of the term: each ad's error is bounded by about
+// 2^-19 of the sum of its own terms' magnitudes (plus the FP32 error of its
+// smallest terms), whatever the range of w^ over the request.
+// F is the largest power of two with max|w^| * 2^F <= min(2^28, 2^31 / (most
+// keys of one ad)), and S <= 12 - ceil(log2(most keys of one ad)), so no
+// class sum can overflow and a term packs into 30 bits:
+//   packed = f << 2 | c, or the FP32 bits of w with the low two bits set to 3
+//   (class 3, FP32), or 0 for a zero weight.
+constexpr int kFixMinBits = 18;
+__host__ __device__ __forceinline__ int fix_exponent(float wmax, uint32_t max_keys) {
+  if (!(wmax > 0.f) || !(wmax < 3.0e38f)) return 0;
+  const float mk = (float)(max_keys > 1u ? max_keys : 1u);
+  const float lim = (2147483647.0f - mk) / mk;
+  const float limit = lim < 268435456.0f ? lim : 268435456.0f;  // max |f| of class 0
+  const float r = limit / wmax;
+  uint32_t rb;
+  memcpy(&rb, &r, 4);
+  int e = (int)((rb >> 23) & 0xFFu) - 127;  // floor(log2 r), r normal
+  if (e > 100) e = 100;
+  if (e < -100) e = -100;
+  return e;
+}
+__host__ __device__ __forceinline__ float pow2f(int e) {
+  const uint32_t b = (uint32_t)(127 + e) << 23;
+  float f;
+  memcpy(&f, &b, 4);
+  return f;
+}
+// S for an index whose ads hold at most max_keys keys (0: no classes 1 and 2)
+inline int class_shift(uint32_t max_keys) {
+  int lg = 0;
+  while ((1u << lg) < std::max<uint32_t>(max_keys, 1u)) lg++;
+  return std::max(0, std::min(10, 12 - lg));
+}
+// The packed term of weight v (see above); s0 = 2^F, s1 = 2^(F+S), s2 = 2^(F+2S).
+__device__ __forceinline__ uint32_t pack_term(float v, float s0, float s1, float s2, bool cls12) {
+  if (v == 0.f) return 0u;
+  constexpr float kMin = (float)(1 << kFixMinBits);
+  const float a = fabsf(v);
+  float sc;
+  uint32_t c;
+  if (a * s0 >= kMin) {
+    sc = s0;
+    c = 0u;
+  } else if (cls12 && a * s1 >= kMin) {
+    sc = s1;
+    c = 1u;
+  } else if (cls12 && a * s2 >= kMin) {
+    sc = s2;
+    c = 2u;
+  } else {
+    return (__float_as_uint(v) & ~3u) | 3u;
+  }
+  return ((uint32_t)__float2int_rn(v * sc) << 2) | c;
 }
 
 // ------------------------------------------------------- embedding rows

@@ -17,11 +17,14 @@
 //       evict-first);
 //   decoders (2 teams x 5 warps): each team takes every other window; warps
 //       walk the window's blocks in chunks of 32 work units of one size group,
-//       gather w^[key] and add it into one of four fixed-point accumulators
-//       of 256 ads (one 32-bit integer atomic per real ad slot);
+//       gather the packed fixed-point term of w^[key] (made by the query
+//       expansion, see pack_term) and add it into the accumulator of its
+//       exponent class, one 32-bit integer atomic per real ad slot; at the
+//       end of the window they fold the classes into one FP32 wide term per
+//       ad (four accumulator buffers in flight);
 //   scorers (8 warps): one thread per row (two for 128-element rows) forms the
 //       inner product with its rotated copy of h_u held in registers, adds the
-//       window's accumulator (and the FP8 row scale), applies the filter and
+//       window's wide term (and the FP8 row scale), applies the filter and
 //       appends candidates; a radix select trims the buffer to the K best.
 // All hand-offs are mbarrier phases; every wait is bounded (2 s) and a CTA
 // that times out flags the request and drains its copies.
@@ -54,7 +57,7 @@ struct FusedArgs {
   const void *emb;
   const float *scale;
   const float *h_u;
-  const float *w_hat;  // dense over keys
+  const uint32_t *wq;  // dense over keys: packed fixed-point weight terms (pack_term)
   const uint32_t *wkey[kGroups];
   const uint8_t *wvals[kGroups];
   const uint32_t *win_ptr[kGroups];
@@ -65,12 +68,13 @@ struct FusedArgs {
   float *all_out;   // score-all mode
   float *wide_out;  // if set: the per-ad wide term is written here (FP32 rescoring needs it)
   uint32_t *hist;   // [kCandBins + 1] candidate-score histogram + top bin (zeroed per request)
-  const uint32_t *wmax_bits;  // max |w^| over the keys (FP32 bits), set by k_absmax
+  const int *fx_word;         // F of the packed terms (written with them)
   const float *wide_in;       // if set: the per-ad wide term, already summed (Algorithm 2
                               // scattered it); no window is decoded
   const uint32_t *route;      // if set: *route != 0 (decided on the device) ignores wide_in
-                              // and decodes the windows with w_hat after all
+                              // and decodes the windows with wq after all
   uint32_t max_keys;          // most keys of one ad
+  int cls_shift;              // S: exponent step between the integer term classes
 };
 
 template <typename Elt, int D>
@@ -101,34 +105,6 @@ struct SlotDesc {                // one window's staged segments
 };
 
 constexpr int kPrefetch = 4;  // producer reads window offsets this many windows ahead
-
-// The window accumulators hold each ad's wide term in two parts.  The main
-// part is 32-bit fixed point (shared-memory integer atomics are fast where
-// FP32 ones are not, and an integer sum does not depend on the order of the
-// additions): a slot adds f = round(w^ * 2^F) and the part is the sum times
-// 2^-F.  F is chosen per request as the largest power of two with
-// max|w^| * 2^F * (most keys of one ad) below 2^31, so no sum can overflow.
-// Rounding a term to the quantum 2^-F costs at most half a quantum, which is
-// small next to the term itself only when |f| is large: a term is kept in
-// fixed point only when |f| >= 2^kFixMinBits, so its relative error is below
-// 2^-(kFixMinBits+1).  Every other non-zero term (a weight far below the
-// request's largest) is added in FP32 to a second accumulator of the window.
-// So each ad's wide term is off by at most about 2^-19 of the sum of its
-// terms' magnitudes plus the FP32 error of its small terms: the bound follows
-// each ad's own weights, whatever the range of w^ over the request.
-constexpr int kFixMinBits = 18;
-__device__ __forceinline__ int fix_exponent(uint32_t wmax_bits, uint32_t max_keys) {
-  const float wmax = __uint_as_float(wmax_bits);
-  if (!(wmax > 0.f)) return 0;
-  const float mk = (float)max(max_keys, 1u);
-  const float limit = (2147483647.0f - mk) / mk;  // per-term bound of |w^| * 2^F
-  const float r = limit / wmax;
-  int e = (int)((__float_as_uint(r) >> 23) & 0xFFu) - 127;  // floor(log2 r), r normal
-  if (e > 100) e = 100;
-  if (e < -100) e = -100;
-  return e;
-}
-__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(127 + e) << 23); }
 
 // Candidate-score histogram shared by all CTAs (for a global K-th bound):
 // bins are the top 11 bits of the order-preserving score key (sign, 8
@@ -166,9 +142,13 @@ __device__ __forceinline__ uint64_t hist_top_threshold(const uint32_t *gh, uint3
   return 0ull;
 }
 
+struct AccBuf {         // one window's accumulators (see pack_term)
+  int cls[3][kWin];     // integer term classes 0, 1, 2
+  float fp[kWin];       // FP32 remainder
+};
+
 struct FusedSmem {
-  int acc[kAccBufs][kWin];
-  float accf[kAccBufs][kWin];  // FP32 part: terms too small for the fixed-point quantum
+  AccBuf acc[kAccBufs];
   uint32_t wp[kPrefetch][kGroups];  // producer's ring of window offsets
   uint32_t ctab[kTeams][kMaxChunkTab];  // per team: group << 16 | chunk within the group
   SlotDesc desc[kMaxIdxSlots];
@@ -206,14 +186,14 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
   const uint32_t w_end = (uint32_t)(((uint64_t)a.n_win * (blockIdx.x + 1)) / gridDim.x);
   const uint32_t my_wins = w_end - w_begin;
 
-  for (int i = tid; i < kAccBufs * kWin; i += kFusedThreads) {
-    (&sm.acc[0][0])[i] = 0;
-    (&sm.accf[0][0])[i] = 0.f;
-  }
+  for (int i = tid; i < kAccBufs * 4 * kWin; i += kFusedThreads)
+    reinterpret_cast<int *>(&sm.acc[0])[i] = 0;  // FP32 +0.0 has the same bits
   // whether the wide term comes precomputed (no window decoding) in this launch
   const bool pre = a.wide_in != nullptr && !(a.route && *a.route);
-  const int fx_e = fix_exponent(*a.wmax_bits, a.max_keys);
-  const float fx_scale = pow2f(fx_e), fx_unit = pow2f(-fx_e);
+  const int fx_e = *a.fx_word;
+  // unit of each accumulator class: 2^-(F + c S)
+  const float u0 = pow2f(-fx_e), u1 = pow2f(-fx_e - a.cls_shift),
+              u2 = pow2f(-fx_e - 2 * a.cls_shift);
   for (int i = tid; i < D; i += kFusedThreads) s_h[i] = a.h_u[i];
   for (int i = tid; i < kCandBins; i += kFusedThreads) sm.chist[i] = 0;
   if (tid == 0) {
@@ -428,11 +408,12 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
         tab[i] = (g << 16) | (i - cb);
       }
       named_sync(2 + team, kTeamThreads);
-      int *acc = sm.acc[b];
+      int *acc = &sm.acc[b].cls[0][0];
       // Branch-free loads: every chunk's loads are independent of the
-      // others', so the shared-memory reads and w^ gathers of a round overlap;
-      // the additions then branch on the chunk's size group (uniform across
-      // the warp), so a unit issues only the atomics its group can need.
+      // others', so the shared-memory reads and term gathers of a round
+      // overlap; the additions then branch on the chunk's size group (uniform
+      // across the warp), so a unit issues only the atomics its group can
+      // need, into the accumulator of its term's class.
       for (uint32_t c0 = tw; c0 < n_chunks; c0 += kChunksInFlight * kTeamWarps) {
         uint32_t word[kChunksInFlight], key[kChunksInFlight], gq[kChunksInFlight];
         bool first[kChunksInFlight], valid[kChunksInFlight];
@@ -457,55 +438,60 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
           first[q] = wi == 0;
           valid[q] = v;
         }
-        // fx[q]: the fixed-point term, or (bit q of `small` set) the FP32
-        // bits of a non-zero weight too small for the quantum
-        int fx[kChunksInFlight];
-        uint32_t small = 0;
+        uint32_t p[kChunksInFlight];
 #pragma unroll
-        for (int q = 0; q < kChunksInFlight; q++) {
-          const float wv = valid[q] ? __ldg(a.w_hat + key[q]) : 0.f;
-          const int f = __float2int_rn(wv * fx_scale);
-          const bool tiny = wv != 0.f && (f < (1 << kFixMinBits) && f > -(1 << kFixMinBits));
-          small |= (tiny ? 1u : 0u) << q;
-          fx[q] = tiny ? __float_as_int(wv) : f;
-        }
+        for (int q = 0; q < kChunksInFlight; q++) p[q] = valid[q] ? __ldg(a.wq + key[q]) : 0u;
+        uint32_t fl = 0;  // chunks whose term is FP32 (class 3)
 #pragma unroll
         for (int q = 0; q < kChunksInFlight; q++) {
           const uint32_t g = gq[q];
-          const bool add = fx[q] != 0 && !((small >> q) & 1u);
+          const uint32_t c = p[q] & 3u;
+          const bool add = p[q] != 0u && c != 3u;
+          fl |= (p[q] != 0u && c == 3u) ? (1u << q) : 0u;
+          const int f = (int)p[q] >> 2;
+          int *ac = acc + c * kWin;
           if (g >= 2 && g < (uint32_t)kGroups) {
 #pragma unroll
             for (int s2 = 0; s2 < 4; s2++) {
               const uint32_t l = (word[q] >> (8 * s2)) & 255u;
-              if (add && ((s2 == 0 && first[q]) || l != 0)) atomicAdd(&acc[l], fx[q]);
+              if (add && ((s2 == 0 && first[q]) || l != 0)) atomicAdd(&ac[l], f);
             }
           } else if (g == 1) {
-            if (add) atomicAdd(&acc[word[q] & 255u], fx[q]);  // slot 0 of a block is real
+            if (add) atomicAdd(&ac[word[q] & 255u], f);  // slot 0 of a block is real
             const uint32_t l = (word[q] >> 8) & 255u;
-            if (add && l != 0) atomicAdd(&acc[l], fx[q]);
+            if (add && l != 0) atomicAdd(&ac[l], f);
           } else if (g == 0) {
-            if (add) atomicAdd(&acc[word[q] & 255u], fx[q]);
+            if (add) atomicAdd(&ac[word[q] & 255u], f);
           }
         }
-        if (__any_sync(0xffffffffu, small != 0)) {
-          // rare: the same slots, FP32 additions of the small terms
-          float *accf = sm.accf[b];
+        if (__any_sync(0xffffffffu, fl != 0u)) {
+          // weights too small for every integer class: FP32 additions
+          float *af = sm.acc[b].fp;
 #pragma unroll
           for (int q = 0; q < kChunksInFlight; q++) {
-            if (!((small >> q) & 1u)) continue;
+            if (!((fl >> q) & 1u)) continue;
             const uint32_t g = gq[q];
-            const float wv = __int_as_float(fx[q]);
+            const float wv = __uint_as_float(p[q] & ~3u);
             const uint32_t ns = g >= 2 ? 4u : (g == 1 ? 2u : 1u);
             for (uint32_t s2 = 0; s2 < ns; s2++) {
               const uint32_t l = (word[q] >> (8 * s2)) & 255u;
-              if ((s2 == 0 && (first[q] || g < 2)) || l != 0) atomicAdd(&accf[l], wv);
+              if ((s2 == 0 && (first[q] || g < 2)) || l != 0) atomicAdd(&af[l], wv);
             }
           }
         }
       }
-      named_sync(2 + team, kTeamThreads);  // every read of the slot is done
+      named_sync(2 + team, kTeamThreads);  // every read of the slot and every addition done
       if (tt == 0) mbar_arrive(&sm.idx_empty[sl]);
-      mbar_arrive(&sm.acc_full[b]);  // release: this thread's additions into acc[b]
+      // fold the classes into one FP32 wide term per ad (in fp), and zero them
+      for (uint32_t l = tt; l < (uint32_t)kWin; l += kTeamThreads) {
+        AccBuf &ab = sm.acc[b];
+        ab.fp[l] = ((float)ab.cls[0][l] * u0 + (float)ab.cls[1][l] * u1) +
+                   ((float)ab.cls[2][l] * u2 + ab.fp[l]);
+        ab.cls[0][l] = 0;
+        ab.cls[1][l] = 0;
+        ab.cls[2][l] = 0;
+      }
+      mbar_arrive(&sm.acc_full[b]);  // release: this thread's part of acc[b]
     }
     return;
   }
@@ -538,7 +524,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
     if (sm.stop_acc) break;
     mbar_try_wait(&sm.acc_full[b], apar);  // per-thread acquire
     const uint32_t w = w_begin + j;
-    const int *acc = sm.acc[b];
+    const float *acc = sm.acc[b].fp;  // the window's wide terms, folded by the decoders
 #pragma unroll
     for (int ps = 0; ps < Sh::kPasses; ps++) {
       const uint32_t rw = ps * Sh::kRowsPerPass + prow;  // row within the window
@@ -579,8 +565,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       const bool leader = valid && qd == 0;
       float score = 0.f;
       if (leader) {
-        const float wide =
-            pre ? __ldg(a.wide_in + ad) : (float)acc[rw] * fx_unit + sm.accf[b][rw];
+        const float wide = pre ? __ldg(a.wide_in + ad) : acc[rw];
         score = dot;
         if (a.scale) score *= a.scale[ad];
         score += wide;
@@ -606,10 +591,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       }
     }
     gsync();  // the window's accumulator is fully read; appends visible
-    for (int i = tid; i < kWin; i += kDotThreads) {  // hand it back, zeroed
-      sm.acc[b][i] = 0;
-      sm.accf[b][i] = 0.f;
-    }
+    for (int i = tid; i < kWin; i += kDotThreads) sm.acc[b].fp[i] = 0.f;  // hand it back, zeroed
     mbar_arrive(&sm.acc_empty[b]);
     if (!ALL && sm.n + kWin > a.cap) {
       // trim the candidates to the K best: radix select, then a stable
@@ -695,7 +677,8 @@ static size_t fused_fixed_bytes(const ebr_index *ix, uint32_t d, uint32_t cap, u
   return (size_t)slots * *slot_bytes + (size_t)d * 4 + (size_t)cap * 8;
 }
 
-constexpr size_t kFusedSmemBudget = 204 * 1024;  // dynamic part; the static part is ~19 KB
+// dynamic part: what is left of 227 KB after the static part
+constexpr size_t kFusedSmemBudget = 227 * 1024 - sizeof(FusedSmem) - 512;
 
 static uint32_t fused_cap(uint32_t k) {
   return (std::max<uint32_t>(k, 1) + std::max<uint32_t>(k / 2, 1024) + 255) / 256 * 256;
@@ -773,6 +756,22 @@ __global__ void k_absmax(const float *__restrict__ w, uint32_t n, uint32_t *__re
   }
 }
 
+// Packs a dense w^ into the fixed-point terms the fused scan decodes
+// (pack_term), with F from max |w^| (*wmax_bits) and the index's most keys of
+// one ad; F goes to *fx_out.  With route set, does nothing unless *route
+// chose the window-major decode (the device decided the traversal).
+__global__ void k_pack(const float *__restrict__ w, uint32_t n,
+                       const uint32_t *__restrict__ wmax_bits, uint32_t max_keys, int cls_shift,
+                       const uint32_t *__restrict__ route, uint32_t *__restrict__ wq,
+                       int *__restrict__ fx_out) {
+  if (route && *route == 0u) return;
+  const int F = fix_exponent(__uint_as_float(*wmax_bits), max_keys);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *fx_out = F;
+  const float s0 = pow2f(F), s1 = pow2f(F + cls_shift), s2 = pow2f(F + 2 * cls_shift);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    wq[i] = pack_term(w[i], s0, s1, s2, cls_shift > 0);
+}
+
 // Whether the fused scan fits shared memory for top-k on this index; if not,
 // dense queries take the key-major path (Algorithm 2) instead.
 bool fused_fits(const ebr_index *ix, uint32_t k) {
@@ -785,18 +784,22 @@ bool fused_fits(const ebr_index *ix, uint32_t k) {
 
 // Launches the fused scan over all windows.  all_out != nullptr: write every
 // score instead of selecting.  Candidates go to cand_out (grid * k entries at
-// most) with counters in ctrl.
-int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
-                 const uint64_t *filter, uint32_t k, uint64_t *cand_out, Ctrl *ctrl,
-                 float *all_out, float *wide_out, uint32_t *hist, int max_grid,
-                 cudaStream_t st, bool wmax_ready, const float *wide_in,
-                 const uint32_t *route) {
+// most) with counters in ctrl.  The window decode reads packed terms from wq
+// with F in ctrl->fx: when `packed` is false they are made here from the
+// dense w_hat first (after max |w^| unless wmax_ready).  *n_launched counts
+// this library's kernels launched.
+int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat, uint32_t *wq,
+                 bool packed, const uint64_t *filter, uint32_t k, uint64_t *cand_out,
+                 Ctrl *ctrl, float *all_out, float *wide_out, uint32_t *hist, int max_grid,
+                 cudaStream_t st, bool wmax_ready, const float *wide_in, const uint32_t *route,
+                 int *n_launched) {
   FusedArgs a;
   memset(&a, 0, sizeof(a));
+  int launched = 0;
   a.emb = ix->dtype == EBR_F32 ? ix->emb_f32.p : ix->emb_q.p;
   a.scale = ix->dtype == EBR_FP8E4M3 ? (const float *)ix->emb_scale.p : nullptr;
   a.h_u = h_u;
-  a.w_hat = w_hat;
+  a.wq = wq;
   for (int g = 0; g < kGroups; g++) {
     a.wkey[g] = ix->wkey[g];
     a.wvals[g] = ix->wvals[g];
@@ -812,25 +815,39 @@ int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
   a.wide_out = wide_out;
   a.hist = hist;
   a.max_keys = std::max<uint32_t>(ix->max_keys_per_ad, 1);
-  // max |w^| for the accumulators' fixed-point scale (non-finite weights are
-  // flagged); the query expansion computes it on the way when it made w^
-  a.wmax_bits = &ctrl->pad;
+  a.cls_shift = class_shift(a.max_keys);
+  a.fx_word = reinterpret_cast<const int *>(&ctrl->fx);
   a.wide_in = wide_in;
   a.route = route;
-  if (!wmax_ready && (!wide_in || route)) {
-    EBR_CUDA_TRY(cudaMemsetAsync(&ctrl->pad, 0, sizeof(uint32_t), st));
-    k_absmax<<<std::max<uint32_t>(1, std::min<uint32_t>(64, (ix->n_keys + 1023) / 1024)), 256, 0,
-               st>>>(w_hat, ix->n_keys, &ctrl->pad, &ctrl->flags);
+  const bool decodes = !wide_in || route;  // the windows may be decoded
+  if (decodes && !packed) {
+    if (!wmax_ready) {
+      // max |w^| for the fixed-point scale (non-finite weights are flagged)
+      EBR_CUDA_TRY(cudaMemsetAsync(&ctrl->pad, 0, sizeof(uint32_t), st));
+      k_absmax<<<std::max<uint32_t>(1, std::min<uint32_t>(64, (ix->n_keys + 1023) / 1024)), 256,
+                 0, st>>>(w_hat, ix->n_keys, &ctrl->pad, &ctrl->flags);
+      EBR_CUDA_TRY(cudaGetLastError());
+      launched++;
+    }
+    k_pack<<<std::max<uint32_t>(1, std::min<uint32_t>(1024, (ix->n_keys + 255) / 256)), 256, 0,
+             st>>>(w_hat, ix->n_keys, &ctrl->pad, a.max_keys, a.cls_shift, route, wq,
+                   reinterpret_cast<int *>(&ctrl->fx));
     EBR_CUDA_TRY(cudaGetLastError());
+    launched++;
   }
+  int rc;
   if (all_out) {
-    if (ix->dtype == EBR_F32) return launch_fused_d<float, true>(ix, a, max_grid, st);
-    if (ix->dtype == EBR_BF16) return launch_fused_d<Bf16Tag, true>(ix, a, max_grid, st);
-    return launch_fused_d<Fp8Tag, true>(ix, a, max_grid, st);
+    if (ix->dtype == EBR_F32) rc = launch_fused_d<float, true>(ix, a, max_grid, st);
+    else if (ix->dtype == EBR_BF16) rc = launch_fused_d<Bf16Tag, true>(ix, a, max_grid, st);
+    else rc = launch_fused_d<Fp8Tag, true>(ix, a, max_grid, st);
+  } else {
+    if (ix->dtype == EBR_F32) rc = launch_fused_d<float, false>(ix, a, max_grid, st);
+    else if (ix->dtype == EBR_BF16) rc = launch_fused_d<Bf16Tag, false>(ix, a, max_grid, st);
+    else rc = launch_fused_d<Fp8Tag, false>(ix, a, max_grid, st);
   }
-  if (ix->dtype == EBR_F32) return launch_fused_d<float, false>(ix, a, max_grid, st);
-  if (ix->dtype == EBR_BF16) return launch_fused_d<Bf16Tag, false>(ix, a, max_grid, st);
-  return launch_fused_d<Fp8Tag, false>(ix, a, max_grid, st);
+  if (rc == EBR_OK) launched++;
+  if (n_launched) *n_launched = launched;
+  return rc;
 }
 
 }  // namespace ebr

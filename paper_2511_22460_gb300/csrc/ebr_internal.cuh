@@ -64,6 +64,7 @@ constexpr int kGroups = 9;
 struct Workspace {
   DevBuf wide;        // float [N] wide-score accumulator (Algorithm 2's score array)
   DevBuf w_dense;     // float [n_keys] expanded query (from user_vals)
+  DevBuf wq;          // uint32 [n_keys] packed fixed-point terms of w_dense (fused scan)
   DevBuf lens;        // uint2 [9 * n_q + 1] (units, nonempty) per (group, query entry)
   DevBuf scan;        // uint2 [9 * n_q + 1] exclusive scan of lens
   DevBuf work;        // WorkEntry [9 * n_q] compacted non-empty (group, entry)
@@ -85,7 +86,7 @@ struct Ctrl {
   unsigned int n_work;       // compacted work entries
   unsigned int pad;          // fused scan: max |w^| of the request (FP32 bits)
   unsigned int route;        // sparse list: 0 = Algorithm 2 scatter, 1 = window-major decode
-  unsigned int pad2;
+  int fx;                    // F of the packed weight terms of the fused scan
 };
 
 // Scratch of the batched (tensor-core) path.
@@ -154,6 +155,10 @@ struct ebr_index {
 
 struct ebr_cross {
   int device = 0;
+  // Bound on |w^| of any single-valued request: the largest, over ad fields j,
+  // of the sum over j's pairs of the pair's largest |w| (+inf if a weight is
+  // not finite); fixes the exponent of the packed terms before w^ is known.
+  float wbound = 0.f;
   uint32_t f_u = 0, f_a = 0, n_pairs = 0, n_keys = 0;
   ebr_wkind kind = EBR_W_HASHED;
   uint32_t hash_bits = 24;
@@ -166,11 +171,11 @@ struct ebr_cross {
 
 namespace ebr {
 constexpr int kMaxCtasPerSm = 4;  // bound on scan CTAs per SM (candidate buffer sizing)
-int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat,
-                 const uint64_t *filter, uint32_t k, uint64_t *cand_out, Ctrl *ctrl,
-                 float *all_out, float *wide_out, uint32_t *hist, int max_grid,
-                 cudaStream_t st, bool wmax_ready = false,
-                 const float *wide_in = nullptr, const uint32_t *route = nullptr);
+int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat, uint32_t *wq,
+                 bool packed, const uint64_t *filter, uint32_t k, uint64_t *cand_out,
+                 Ctrl *ctrl, float *all_out, float *wide_out, uint32_t *hist, int max_grid,
+                 cudaStream_t st, bool wmax_ready = false, const float *wide_in = nullptr,
+                 const uint32_t *route = nullptr, int *n_launched = nullptr);
 bool fused_fits(const ebr_index *ix, uint32_t k);
 constexpr size_t kHistWords = 4096;  // candidate-score histogram of the fused scan (2048 bins + top bin)
 // Launchers implemented in ebr_query.cu, used by the serving loop.

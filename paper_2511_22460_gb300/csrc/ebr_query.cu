@@ -76,10 +76,22 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 // user_ptr != nullptr (batch 1 only): multi-valued user fields, field i
 // holding users[user_ptr[i] .. user_ptr[i+1]); every value is one hit
 // feature, so a pair (i, j) adds w_ij(u, v) for each u of field i.
+// Packed terms (wq != nullptr, batch 1, single-valued user fields): each w^
+// is also written as the fixed-point term the fused scan decodes (pack_term)
+// with the exponent F given (chosen from the cross model's bound on |w^|,
+// so it is known before w^ is); |w^| above wlimit, which the bound excludes,
+// is flagged.
+struct PackOut {
+  uint32_t *wq;
+  int *fx_out;
+  int F, cls_shift;
+  float wlimit;
+};
+
 __global__ void k_expand(CrossView cv, const uint32_t *__restrict__ users, uint32_t batch,
                          float *__restrict__ w_hat, uint32_t *__restrict__ flags,
                          uint32_t *__restrict__ wmax, const uint32_t *__restrict__ user_ptr,
-                         uint32_t n_uv) {
+                         uint32_t n_uv, PackOut po) {
   extern __shared__ uint32_t s_mem[];
   __shared__ uint32_t s_seq_ok;
   uint32_t *s_off = s_mem;                    // key_off[f_a + 1]
@@ -120,6 +132,10 @@ __global__ void k_expand(CrossView cv, const uint32_t *__restrict__ users, uint3
   }
   const uint64_t total = (uint64_t)batch * cv.n_keys;
   uint32_t bad = 0, mx = 0;
+  const bool pack = po.wq != nullptr && batch == 1 && !multi;
+  const float s0 = pow2f(po.F), s1 = pow2f(po.F + po.cls_shift),
+              s2 = pow2f(po.F + 2 * po.cls_shift);
+  if (pack && blockIdx.x == 0 && threadIdx.x == 0) *po.fx_out = po.F;
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
        t += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t b = (uint32_t)(t / cv.n_keys), key = (uint32_t)(t % cv.n_keys);
@@ -177,6 +193,10 @@ __global__ void k_expand(CrossView cv, const uint32_t *__restrict__ users, uint3
       acc += w;
     }
     w_hat[t] = acc;
+    if (pack) {
+      if (!(fabsf(acc) <= po.wlimit)) bad |= DEVERR_RANGE;
+      po.wq[t] = pack_term(acc, s0, s1, s2, po.cls_shift > 0);
+    }
     mx = max(mx, __float_as_uint(acc) & 0x7FFFFFFFu);
   }
   if (bad) atomicOr(flags, bad);
@@ -962,6 +982,7 @@ int ws_prepare_one(ebr_index *ix, uint32_t n_q, uint32_t kcap) {
   Workspace &w = ix->ws;
   EBR_TRY(dev_reserve(w.wide, (size_t)ix->n_ads * 4));
   EBR_TRY(dev_reserve(w.w_dense, (size_t)ix->n_keys * 4));
+  EBR_TRY(dev_reserve(w.wq, (size_t)ix->n_keys * 4));
   const size_t entries = (size_t)kGroups * n_q + 1;
   EBR_TRY(dev_reserve(w.lens, entries * sizeof(LenPair)));
   EBR_TRY(dev_reserve(w.scan, entries * sizeof(LenPair)));
@@ -1088,7 +1109,8 @@ int expand_transposed(const ebr_cross *c, const uint32_t *users, uint32_t batch,
 
 static int expand_into(const ebr_cross *c, const uint32_t *users, uint32_t batch, float *w_hat,
                        uint32_t *flags, cudaStream_t st, uint32_t *wmax = nullptr,
-                       const uint32_t *user_ptr = nullptr, uint32_t n_uv = 0) {
+                       const uint32_t *user_ptr = nullptr, uint32_t n_uv = 0,
+                       PackOut po = PackOut{nullptr, nullptr, 0, 0, 0.f}) {
   CrossView cv = cross_view(c);
   const uint64_t total = (uint64_t)batch * cv.n_keys;
   const size_t smem =
@@ -1105,7 +1127,7 @@ static int expand_into(const ebr_cross *c, const uint32_t *users, uint32_t batch
     return EBR_EINVAL;
   }
   k_expand<<<launch_grid(total, 256, 65535), 256, smem, st>>>(cv, users, batch, w_hat, flags,
-                                                              wmax, user_ptr, n_uv);
+                                                              wmax, user_ptr, n_uv, po);
   EBR_CUDA_TRY(cudaGetLastError());
   return EBR_OK;
 }
@@ -1154,9 +1176,20 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
   const uint32_t *q_key = q.q_key;
   const float *q_w = q.q_w;
   uint32_t n_q = q.n_q;
+  bool packed = false;  // the expansion also wrote the fused scan's packed terms
   if (q.user_vals) {
+    // single-valued user fields: the packed terms' exponent follows from the
+    // cross model's bound on |w^|, so the expansion writes them directly;
+    // otherwise the fused scan's launch packs w^ after its max |w^|
+    PackOut po{nullptr, nullptr, 0, 0, 0.f};
+    const float wb = cross->wbound * 1.001f;
+    if (!q.user_ptr && wb < 3.0e38f && !(q.flags & EBR_QF_KEY_MAJOR)) {
+      const uint32_t mk = std::max<uint32_t>(ix->max_keys_per_ad, 1);
+      po = PackOut{(uint32_t *)w.wq.p, &ctrl->fx, fix_exponent(wb, mk), class_shift(mk), wb};
+      packed = true;
+    }
     EBR_TRY(expand_into(cross, q.user_vals, 1, (float *)w.w_dense.p, &ctrl->flags, st,
-                        &ctrl->pad, q.user_ptr, q.n_user_vals));  // + max |w^| for the fused scan
+                        &ctrl->pad, q.user_ptr, q.n_user_vals, po));  // + max |w^|
     ix->launches += 1;
     q_key = nullptr;
     q_w = (const float *)w.w_dense.p;
@@ -1188,10 +1221,12 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
     pm.mark(2, st);
     EBR_CUDA_TRY(cudaMemsetAsync(w.hist.p, 0, kHistWords * 4, st));
     const bool wmax_ready = q.user_vals != nullptr;  // the expansion reduced max |w^|
-    EBR_TRY(launch_fused(ix, q.h_u, q_w, q.filter, kscan, (uint64_t *)w.cand.p, ctrl, nullptr,
-                         quant ? (float *)w.wide.p : nullptr, (uint32_t *)w.hist.p,
-                         ix->num_sms * kMaxCtasPerSm, st, wmax_ready));
-    ix->launches += wmax_ready ? 1 : 2;  // (+ k_absmax) k_fused_window
+    int nl = 0;
+    EBR_TRY(launch_fused(ix, q.h_u, q_w, (uint32_t *)w.wq.p, packed, q.filter, kscan,
+                         (uint64_t *)w.cand.p, ctrl, nullptr, quant ? (float *)w.wide.p : nullptr,
+                         (uint32_t *)w.hist.p, ix->num_sms * kMaxCtasPerSm, st, wmax_ready,
+                         nullptr, nullptr, &nl));
+    ix->launches += nl;  // (k_absmax, k_pack) k_fused_window
   } else {
     float *w_dense = auto_route ? (float *)w.w_dense.p : nullptr;
     if (auto_route) EBR_CUDA_TRY(cudaMemsetAsync(w_dense, 0, (size_t)ix->n_keys * 4, st));
@@ -1207,12 +1242,14 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
       // Algorithm 2 has just scattered (no window decoding), or, when the
       // device chose the window-major decode, decoding w_dense's windows
       EBR_CUDA_TRY(cudaMemsetAsync(w.hist.p, 0, kHistWords * 4, st));
-      EBR_TRY(launch_fused(ix, q.h_u, w_dense, q.filter, kscan, (uint64_t *)w.cand.p, ctrl,
-                           nullptr, auto_route && quant ? (float *)w.wide.p : nullptr,
+      int nl = 0;
+      EBR_TRY(launch_fused(ix, q.h_u, w_dense, (uint32_t *)w.wq.p, false, q.filter, kscan,
+                           (uint64_t *)w.cand.p, ctrl, nullptr,
+                           auto_route && quant ? (float *)w.wide.p : nullptr,
                            (uint32_t *)w.hist.p, ix->num_sms * kMaxCtasPerSm, st,
                            !auto_route || planned, (const float *)w.wide.p,
-                           auto_route ? &ctrl->route : nullptr));
-      ix->launches += auto_route && !planned ? 2 : 1;  // (+ k_absmax) k_fused_window
+                           auto_route ? &ctrl->route : nullptr, &nl));
+      ix->launches += nl;  // (k_absmax, k_pack) k_fused_window
 
     } else {
       ScanArgs a;
@@ -1259,6 +1296,81 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
   return EBR_OK;
 }
 
+}  // namespace ebr
+
+namespace ebr {
+// Largest |w| (FP32 bits) of each table segment: segment y covers
+// table[off[y] .. off[y] + len[y]); out[y] must start at 0.
+__global__ void k_seg_absmax(const float *__restrict__ table, const uint64_t *__restrict__ off,
+                             const uint64_t *__restrict__ len, uint32_t *__restrict__ out) {
+  const uint32_t y = blockIdx.y;
+  const uint64_t o = off[y], n = len[y];
+  uint32_t m = 0;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    m = max(m, __float_as_uint(table[o + i]) & 0x7FFFFFFFu);
+  for (int k = 16; k; k >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, k));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out + y, m);
+}
+
+// The cross model's bound on |w^| of a single-valued request: for ad field j,
+// w^[(j, v)] sums one weight of each pair (i, j), so |w^| <= the sum over j's
+// pairs of their largest |w|; the bound is the largest such sum over j
+// (+inf when a weight is not finite).
+static int cross_bound(ebr_cross *c, const ebr_cross_desc *d, cudaStream_t st) {
+  const uint32_t nseg = d->kind == EBR_W_HASHED ? 1u : d->n_pairs;
+  if (nseg == 0) {
+    c->wbound = 0.f;
+    return EBR_OK;
+  }
+  std::vector<uint64_t> meta(2 * (size_t)nseg);
+  for (uint32_t y = 0; y < nseg; y++) {
+    if (d->kind == EBR_W_HASHED) {
+      meta[y] = 0;
+      meta[nseg + y] = 1ull << d->hash_bits;
+    } else {
+      meta[y] = d->w_off[y];
+      meta[nseg + y] = (uint64_t)d->vocab_u[d->pairs[2 * y]] * d->vocab_a[d->pairs[2 * y + 1]];
+    }
+  }
+  DevBuf dm, dout;
+  int rc = dev_alloc(dm, meta.size() * 8);
+  if (rc == EBR_OK) rc = dev_alloc(dout, (size_t)nseg * 4);
+  std::vector<uint32_t> mx(nseg, 0);
+  if (rc == EBR_OK) {
+    cudaError_t e = cudaMemcpyAsync(dm.p, meta.data(), meta.size() * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dout.p, 0, (size_t)nseg * 4, st);
+    if (e == cudaSuccess) {
+      const uint64_t *off = (const uint64_t *)dm.p;
+      k_seg_absmax<<<dim3(d->kind == EBR_W_HASHED ? 1024u : 8u, nseg), 256, 0, st>>>(
+          (const float *)c->table.p, off, off + nseg, (uint32_t *)dout.p);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mx.data(), dout.p, (size_t)nseg * 4,
+                                              cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      set_error("ebr_cross_create: %s", cudaGetErrorString(e));
+      rc = EBR_ECUDA;
+    }
+  }
+  dev_free(dm);
+  dev_free(dout);
+  if (rc != EBR_OK) return rc;
+  std::vector<double> field(d->f_a, 0.0);
+  bool finite = true;
+  for (uint32_t p = 0; p < d->n_pairs; p++) {
+    const uint32_t b = mx[d->kind == EBR_W_HASHED ? 0 : p];
+    if (b >= 0x7F800000u) finite = false;
+    float f;
+    memcpy(&f, &b, 4);
+    field[d->pairs[2 * p + 1]] += f;
+  }
+  double wb = 0.0;
+  for (double x : field) wb = std::max(wb, x);
+  c->wbound = finite && wb < 1e38 ? (float)wb : INFINITY;
+  return EBR_OK;
+}
 }  // namespace ebr
 
 using namespace ebr;
@@ -1349,6 +1461,7 @@ extern "C" int ebr_cross_create(const ebr_cross_desc *d, ebr_cross **out) {
       rc = EBR_ECUDA;
     }
   }
+  if (rc == EBR_OK) rc = cross_bound(c, d, st);
   cudaSetDevice(prev);
   if (rc != EBR_OK) {
     dev_free(c->table);
@@ -1612,8 +1725,9 @@ extern "C" int ebr_score_all(const ebr_index *cix, const ebr_cross *cross, const
   const bool fused = rc == EBR_OK && q_key == nullptr && !(q->flags & EBR_QF_KEY_MAJOR) &&
                      fused_fits(ix, 1);
   if (fused) {
-    rc = launch_fused(ix, q->h_u, q_w, nullptr, 1, nullptr, ctrl, out_scores, nullptr,
-                      (uint32_t *)ix->ws.hist.p, ix->num_sms * kMaxCtasPerSm, st);
+    rc = launch_fused(ix, q->h_u, q_w, (uint32_t *)ix->ws.wq.p, false, nullptr, 1, nullptr, ctrl,
+                      out_scores, nullptr, (uint32_t *)ix->ws.hist.p,
+                      ix->num_sms * kMaxCtasPerSm, st);
   } else {
     if (rc == EBR_OK) rc = run_wide(ix, q_key, q_w, n_q, ctrl, st);
     if (rc == EBR_OK) {
