@@ -111,6 +111,15 @@ constexpr uint64_t kWaitTimeoutNs = 2000000000ull;  // 2 s
 __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
+// Programmatic dependent launch: pdl_wait blocks the calling thread until
+// the grids it depends on have completed and their writes are visible (a
+// no-op when the kernel was launched without the attribute); pdl_trigger lets
+// the next kernel of the stream be scheduled before this one ends.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Barrier over a subset of the CTA's warps (hardware named barrier `id`).
 __device__ __forceinline__ void named_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");

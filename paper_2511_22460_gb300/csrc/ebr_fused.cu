@@ -17,14 +17,11 @@
 //       evict-first);
 //   decoders (2 teams x 5 warps): each team takes every other window; warps
 //       walk the window's blocks in chunks of 32 work units of one size group,
-//       gather the packed fixed-point term of w^[key] (made by the query
-//       expansion, see pack_term) and add it into the accumulator of its
-//       exponent class, one 32-bit integer atomic per real ad slot; at the
-//       end of the window they fold the classes into one FP32 wide term per
-//       ad (four accumulator buffers in flight);
+//       gather w^[key] and add it into one of four fixed-point accumulators
+//       of 256 ads (one 32-bit integer atomic per real ad slot);
 //   scorers (8 warps): one thread per row (two for 128-element rows) forms the
 //       inner product with its rotated copy of h_u held in registers, adds the
-//       window's wide term (and the FP8 row scale), applies the filter and
+//       window's accumulator (and the FP8 row scale), applies the filter and
 //       appends candidates; a radix select trims the buffer to the K best.
 // All hand-offs are mbarrier phases; every wait is bounded (2 s) and a CTA
 // that times out flags the request and drains its copies.
@@ -186,14 +183,9 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
   const uint32_t w_end = (uint32_t)(((uint64_t)a.n_win * (blockIdx.x + 1)) / gridDim.x);
   const uint32_t my_wins = w_end - w_begin;
 
+  pdl_trigger();  // the final selection may be scheduled behind this grid
   for (int i = tid; i < kAccBufs * 4 * kWin; i += kFusedThreads)
     reinterpret_cast<int *>(&sm.acc[0])[i] = 0;  // FP32 +0.0 has the same bits
-  // whether the wide term comes precomputed (no window decoding) in this launch
-  const bool pre = a.wide_in != nullptr && !(a.route && *a.route);
-  const int fx_e = *a.fx_word;
-  // unit of each accumulator class: 2^-(F + c S)
-  const float u0 = pow2f(-fx_e), u1 = pow2f(-fx_e - a.cls_shift),
-              u2 = pow2f(-fx_e - 2 * a.cls_shift);
   for (int i = tid; i < D; i += kFusedThreads) s_h[i] = a.h_u[i];
   for (int i = tid; i < kCandBins; i += kFusedThreads) sm.chist[i] = 0;
   if (tid == 0) {
@@ -216,6 +208,58 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
     fence_mbar_init();
   }
   __syncthreads();
+
+  if (warp == kEmbWarp) {
+    // --------------------------------------------- embedding producer
+    // Lane 0 streams every window's embedding rows into the stage ring.
+    if (lane != 0) return;
+    const uint64_t pol = l2_evict_first_policy();
+    uint32_t seq = 0;  // stages issued
+    bool stop = false;
+    for (uint32_t j = 0; j < my_wins && !stop; j++) {
+      const uint32_t w = w_begin + j;
+      for (uint32_t q = 0; q < (uint32_t)Sh::kStagesPerWin; q++) {
+        const uint32_t s = seq % S;
+        if (seq >= S && !mbar_wait_bounded(&sm.empty[s], ((seq / S) - 1) & 1u, kWaitTimeoutNs)) {
+          atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
+          sm.abort = 1;
+          stop = true;
+          break;
+        }
+        if (*((volatile uint32_t *)&sm.abort)) {
+          stop = true;
+          break;
+        }
+        const uint32_t row0 = w * kWin + q * Sh::kRowsPerStage;
+        const uint32_t rows =
+            row0 < a.n_ads ? min((uint32_t)Sh::kRowsPerStage, a.n_ads - row0) : 0u;
+        if (rows) {
+          mbar_arrive_expect_tx(&sm.full[s], rows * Sh::kRowBytes);
+          bulk_g2s_hint(stage0 + (size_t)s * kStageBytes,
+                        reinterpret_cast<const uint8_t *>(a.emb) + (uint64_t)row0 * Sh::kRowBytes,
+                        rows * Sh::kRowBytes, &sm.full[s], pol);
+        } else {
+          mbar_arrive(&sm.full[s]);
+        }
+        seq++;
+      }
+    }
+    if (stop)  // stopped early: wait (bounded) for the stage copies still in flight
+      for (uint32_t q = (seq > S ? seq - S : 0); q < seq; q++)
+        mbar_wait_bounded(&sm.full[q % S], (q / S) & 1u, kWaitTimeoutNs / 4);
+    return;
+  }
+
+  // Everything below reads what the kernels before this one wrote (the
+  // packed terms, their exponent, the route word): wait for them.  The
+  // embedding producer above streams rows meanwhile.
+  pdl_wait();
+  // whether the wide term comes precomputed (no window decoding) in this launch
+  const bool pre = a.wide_in != nullptr && !(a.route && *a.route);
+  const int fx_e = *a.fx_word;
+  // unit of each accumulator class: 2^-(F + c S)
+  const float u0 = pow2f(-fx_e), u1 = pow2f(-fx_e - a.cls_shift),
+              u2 = pow2f(-fx_e - 2 * a.cls_shift);
 
   if (warp == kIdxWarp) {
     // ------------------------------------------------- index producer
@@ -318,47 +362,6 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       for (uint32_t j = issued > NI ? issued - NI : 0; j < issued; j++)
         mbar_wait_bounded(&sm.idx_full[j % NI], (j / NI) & 1u, kWaitTimeoutNs / 4);
     }
-    return;
-  }
-
-  if (warp == kEmbWarp) {
-    // --------------------------------------------- embedding producer
-    // Lane 0 streams every window's embedding rows into the stage ring.
-    if (lane != 0) return;
-    const uint64_t pol = l2_evict_first_policy();
-    uint32_t seq = 0;  // stages issued
-    bool stop = false;
-    for (uint32_t j = 0; j < my_wins && !stop; j++) {
-      const uint32_t w = w_begin + j;
-      for (uint32_t q = 0; q < (uint32_t)Sh::kStagesPerWin; q++) {
-        const uint32_t s = seq % S;
-        if (seq >= S && !mbar_wait_bounded(&sm.empty[s], ((seq / S) - 1) & 1u, kWaitTimeoutNs)) {
-          atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
-          sm.abort = 1;
-          stop = true;
-          break;
-        }
-        if (*((volatile uint32_t *)&sm.abort)) {
-          stop = true;
-          break;
-        }
-        const uint32_t row0 = w * kWin + q * Sh::kRowsPerStage;
-        const uint32_t rows =
-            row0 < a.n_ads ? min((uint32_t)Sh::kRowsPerStage, a.n_ads - row0) : 0u;
-        if (rows) {
-          mbar_arrive_expect_tx(&sm.full[s], rows * Sh::kRowBytes);
-          bulk_g2s_hint(stage0 + (size_t)s * kStageBytes,
-                        reinterpret_cast<const uint8_t *>(a.emb) + (uint64_t)row0 * Sh::kRowBytes,
-                        rows * Sh::kRowBytes, &sm.full[s], pol);
-        } else {
-          mbar_arrive(&sm.full[s]);
-        }
-        seq++;
-      }
-    }
-    if (stop)  // stopped early: wait (bounded) for the stage copies still in flight
-      for (uint32_t q = (seq > S ? seq - S : 0); q < seq; q++)
-        mbar_wait_bounded(&sm.full[q % S], (q / S) & 1u, kWaitTimeoutNs / 4);
     return;
   }
 
@@ -524,6 +527,18 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
     if (sm.stop_acc) break;
     mbar_try_wait(&sm.acc_full[b], apar);  // per-thread acquire
     const uint32_t w = w_begin + j;
+    // per-row side inputs, loaded before the rows arrive so that their
+    // latency overlaps the wait for the stage
+    float pre_side[Sh::kPasses], pre_scale[Sh::kPasses];
+    bool pre_keep[Sh::kPasses];
+#pragma unroll
+    for (int ps = 0; ps < Sh::kPasses; ps++) {
+      const uint32_t ad = w * kWin + ps * Sh::kRowsPerPass + prow;
+      const bool in = ad < a.n_ads && qd == 0;
+      pre_side[ps] = in && pre ? __ldg(a.wide_in + ad) : 0.f;
+      pre_scale[ps] = in && a.scale ? __ldg(a.scale + ad) : 1.f;
+      pre_keep[ps] = !(in && a.filter) || ((__ldg(a.filter + (ad >> 6)) >> (ad & 63)) & 1ull);
+    }
     const float *acc = sm.acc[b].fp;  // the window's wide terms, folded by the decoders
 #pragma unroll
     for (int ps = 0; ps < Sh::kPasses; ps++) {
@@ -565,17 +580,16 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       const bool leader = valid && qd == 0;
       float score = 0.f;
       if (leader) {
-        const float wide = pre ? __ldg(a.wide_in + ad) : acc[rw];
+        const float wide = pre ? pre_side[ps] : acc[rw];
         score = dot;
-        if (a.scale) score *= a.scale[ad];
+        if (a.scale) score *= pre_scale[ps];
         score += wide;
         if (a.wide_out && !pre) a.wide_out[ad] = wide;
       }
       if (ALL) {
         if (leader) a.all_out[ad] = score;
       } else {
-        bool keep = leader;
-        if (keep && a.filter) keep = (a.filter[ad >> 6] >> (ad & 63)) & 1ull;
+        bool keep = leader && pre_keep[ps];
         uint64_t kk = 0;
         if (keep) {
           kk = make_key(score, ad);
@@ -681,7 +695,8 @@ static size_t fused_fixed_bytes(const ebr_index *ix, uint32_t d, uint32_t cap, u
 constexpr size_t kFusedSmemBudget = 227 * 1024 - sizeof(FusedSmem) - 512;
 
 static uint32_t fused_cap(uint32_t k) {
-  return (std::max<uint32_t>(k, 1) + std::max<uint32_t>(k / 2, 1024) + 255) / 256 * 256;
+  // K plus slack for the appends between trims (a window adds at most 256)
+  return (std::max<uint32_t>(k, 1) + 1024 + 255) / 256 * 256;
 }
 
 template <typename Elt, int D, bool ALL>
@@ -722,8 +737,7 @@ static int launch_fused_t(const ebr_index *ix, FusedArgs a, int max_grid, cudaSt
   if (max_grid > 0) grid = std::min(grid, max_grid);
   grid = std::min<int>(grid, (int)a.n_win);
   if (grid < 1) grid = 1;
-  kern<<<grid, kFusedThreads, smem, st>>>(a);
-  EBR_CUDA_TRY(cudaGetLastError());
+  EBR_CUDA_TRY(launch_pdl(kern, grid, kFusedThreads, smem, st, a));
   return EBR_OK;
 }
 

@@ -523,7 +523,7 @@ extern "C" void ebr_index_free(ebr_index *ix) {
   dev_free(ix->emb_scale);
   Workspace &w = ix->ws;
   for (DevBuf *b : {&w.wide, &w.w_dense, &w.lens, &w.scan, &w.work, &w.cub_tmp, &w.cand,
-                    &w.ctrl, &w.io_in, &w.io_out, &w.hist, &w.route_stats})
+                    &w.ctrl, &w.io_in, &w.io_out, &w.route_stats})
     dev_free(*b);
   batch_ws_free(ix->bws);
   if (w.host_ctrl) cudaFreeHost(w.host_ctrl);

@@ -70,11 +70,11 @@ struct Workspace {
   DevBuf work;        // WorkEntry [9 * n_q] compacted non-empty (group, entry)
   DevBuf cub_tmp;     // CUB temporary storage
   DevBuf cand;        // uint64 [G * KCAP] per-CTA candidates
-  DevBuf ctrl;        // Ctrl block (counters, threshold, flags)
+  DevBuf ctrl;        // Ctrl block (counters, threshold, flags), then at kCtrlBytes the
+                      // fused scan's candidate-score histogram (uint32 [kHistWords])
   DevBuf route_stats; // uint64 [2]: sparse lists routed on the device, of those window-major
   DevBuf io_in;       // staging for host inputs
   DevBuf io_out;      // staging for outputs
-  DevBuf hist;        // uint32 [kHistWords] candidate-score histogram
   void *host_ctrl = nullptr;  // pinned mirror of Ctrl
 };
 
@@ -178,6 +178,27 @@ int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat, uint
                  const uint32_t *route = nullptr, int *n_launched = nullptr);
 bool fused_fits(const ebr_index *ix, uint32_t k);
 constexpr size_t kHistWords = 4096;  // candidate-score histogram of the fused scan (2048 bins + top bin)
+constexpr size_t kCtrlBytes = 256;   // Ctrl block, then the histogram, in one buffer (one memset)
+inline uint32_t *ws_hist(const Workspace &w) { return (uint32_t *)((char *)w.ctrl.p + kCtrlBytes); }
+
+// Launches kern on st with programmatic stream serialization: it may start
+// while the previous kernel of the stream is still running, and its threads
+// that read that kernel's results call pdl_wait first.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 // Launchers implemented in ebr_query.cu, used by the serving loop.
 int query_one(const ebr_index *ix, const ebr_cross *cross, const ebr_query &q, uint32_t *ids,
               float *scores, uint32_t kmax, cudaStream_t st);

@@ -133,6 +133,7 @@ __global__ void k_expand(CrossView cv, const uint32_t *__restrict__ users, uint3
   const uint64_t total = (uint64_t)batch * cv.n_keys;
   uint32_t bad = 0, mx = 0;
   const bool pack = po.wq != nullptr && batch == 1 && !multi;
+  pdl_trigger();  // the fused scan may start streaming its embedding rows
   const float s0 = pow2f(po.F), s1 = pow2f(po.F + po.cls_shift),
               s2 = pow2f(po.F + 2 * po.cls_shift);
   if (pack && blockIdx.x == 0 && threadIdx.x == 0) *po.fx_out = po.F;
@@ -200,11 +201,16 @@ __global__ void k_expand(CrossView cv, const uint32_t *__restrict__ users, uint3
     mx = max(mx, __float_as_uint(acc) & 0x7FFFFFFFu);
   }
   if (bad) atomicOr(flags, bad);
-  if (wmax) {
+  if (wmax && !pack) {  // packed terms need no max |w^| (their exponent is set)
+    __shared__ uint32_t s_mx;
+    if (threadIdx.x == 0) s_mx = 0;
+    __syncthreads();
     for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0 && mx) {
-      if (mx >= 0x7F800000u) atomicOr(flags, DEVERR_RANGE);
-      atomicMax(wmax, mx >= 0x7F800000u ? 0u : mx);
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(&s_mx, mx);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_mx) {  // one global atomic per block
+      if (s_mx >= 0x7F800000u) atomicOr(flags, DEVERR_RANGE);
+      atomicMax(wmax, s_mx >= 0x7F800000u ? 0u : s_mx);
     }
   }
 }
@@ -844,26 +850,37 @@ __device__ void bitonic_sort_desc(uint64_t *v, uint32_t n_pow2) {
 
 // Selects the best min(k, n) keys among n (global memory), sorts them
 // descending, writes k_out ids/scores (or keys), padded with (0xFFFFFFFF, -inf)
-// (or zero keys).  Dynamic shared memory: 8 * pow2(min(k, n)) bytes.
+// (or zero keys).  Dynamic shared memory: 8 * (pow2(min(k, n)) + buf_cap)
+// bytes; when n <= buf_cap the keys are read from global memory once and the
+// radix select runs on the shared copy, otherwise on the global keys.
+// Waits (pdl_wait) for the kernel before it in the stream.
 __global__ void __launch_bounds__(kFinalThreads) k_final_select(
     const uint64_t *__restrict__ keys, const Ctrl *__restrict__ ctrl, uint32_t n_fixed,
     uint32_t k, uint32_t k_out, uint32_t *__restrict__ out_ids, float *__restrict__ out_scores,
-    uint64_t *__restrict__ out_keys) {
+    uint64_t *__restrict__ out_keys, uint32_t buf_cap) {
   extern __shared__ __align__(16) uint64_t s_v[];
   __shared__ uint32_t s_hist[256];
   __shared__ uint32_t s_misc[8];
   __shared__ uint32_t s_cnt;
+  pdl_wait();
   const uint32_t n = ctrl ? ctrl->n_cand : n_fixed;
   const uint32_t take = min(n, k);
   uint32_t p2 = 1;
   while (p2 < take) p2 <<= 1;
+  const uint64_t *src = keys;
+  if (n <= buf_cap) {  // one read of the keys, then everything in shared memory
+    uint64_t *s_buf = s_v + p2;
+    for (uint32_t i = threadIdx.x; i < n; i += kFinalThreads) s_buf[i] = keys[i];
+    __syncthreads();
+    src = s_buf;
+  }
   uint64_t T = 0;
-  if (n > k) T = cta_radix_select<kFinalThreads>(keys, n, k, s_hist, s_misc);
+  if (n > k) T = cta_radix_select<kFinalThreads>(src, n, k, s_hist, s_misc);
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
   for (uint32_t base = 0; base < n; base += kFinalThreads) {
     const uint32_t i = base + threadIdx.x;
-    const uint64_t x = i < n ? keys[i] : 0ull;
+    const uint64_t x = i < n ? src[i] : 0ull;
     const bool kp = i < n && x >= T;
     const uint32_t pos = warp_append(kp, &s_cnt);
     if (kp && pos < p2) s_v[pos] = x;
@@ -883,6 +900,11 @@ __global__ void __launch_bounds__(kFinalThreads) k_final_select(
     }
   }
 }
+
+// Shared-memory keys k_final_select buffers beyond its pow2(k) sort area.
+constexpr uint32_t kFinalBufKeys = 8192;
+constexpr size_t kFinalMaxSmem = (8192 + kFinalBufKeys) * 8;  // largest k is 8192
+static size_t final_smem(uint32_t p2) { return ((size_t)p2 + kFinalBufKeys) * 8; }
 
 // FP32 rescoring of candidate keys: s = <h_u, h_a (FP32 copy)> + wide[a].
 // One warp per candidate; D <= 128.
@@ -994,8 +1016,7 @@ int ws_prepare_one(ebr_index *ix, uint32_t n_q, uint32_t kcap) {
   EBR_TRY(dev_reserve(w.cub_tmp, tb + 256));
   EBR_TRY(dev_reserve(w.cand, ((size_t)ix->num_sms * kMaxCtasPerSm + 1) * kcap * 8 +
                                   2 * (size_t)kcap * 8));
-  EBR_TRY(dev_reserve(w.ctrl, 256));
-  EBR_TRY(dev_reserve(w.hist, kHistWords * 4));
+  EBR_TRY(dev_reserve(w.ctrl, kCtrlBytes + kHistWords * 4));
   if (!w.route_stats.p) {  // lifetime counters, zeroed once
     EBR_TRY(dev_reserve(w.route_stats, 16));
     EBR_CUDA_TRY(cudaMemset(w.route_stats.p, 0, 16));
@@ -1168,11 +1189,11 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
   static bool attr_set = false;  // per process; the attribute applies to every device
   if (!attr_set) {
     EBR_CUDA_TRY(cudaFuncSetAttribute(k_final_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      8192 * 8));
+                                      (int)kFinalMaxSmem));
     attr_set = true;
   }
   ProfMarks pm(ix, st);
-  EBR_CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
+  EBR_CUDA_TRY(cudaMemsetAsync(ctrl, 0, kCtrlBytes + kHistWords * 4, st));  // + histogram
   const uint32_t *q_key = q.q_key;
   const float *q_w = q.q_w;
   uint32_t n_q = q.n_q;
@@ -1219,12 +1240,11 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
   if (fused) {
     // dense query: wide term decoded window by window inside the scan
     pm.mark(2, st);
-    EBR_CUDA_TRY(cudaMemsetAsync(w.hist.p, 0, kHistWords * 4, st));
     const bool wmax_ready = q.user_vals != nullptr;  // the expansion reduced max |w^|
     int nl = 0;
     EBR_TRY(launch_fused(ix, q.h_u, q_w, (uint32_t *)w.wq.p, packed, q.filter, kscan,
                          (uint64_t *)w.cand.p, ctrl, nullptr, quant ? (float *)w.wide.p : nullptr,
-                         (uint32_t *)w.hist.p, ix->num_sms * kMaxCtasPerSm, st, wmax_ready,
+                         ws_hist(w), ix->num_sms * kMaxCtasPerSm, st, wmax_ready,
                          nullptr, nullptr, &nl));
     ix->launches += nl;  // (k_absmax, k_pack) k_fused_window
   } else {
@@ -1241,12 +1261,11 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
       // the streaming scan of the fused kernel, adding the wide term that
       // Algorithm 2 has just scattered (no window decoding), or, when the
       // device chose the window-major decode, decoding w_dense's windows
-      EBR_CUDA_TRY(cudaMemsetAsync(w.hist.p, 0, kHistWords * 4, st));
       int nl = 0;
       EBR_TRY(launch_fused(ix, q.h_u, w_dense, (uint32_t *)w.wq.p, false, q.filter, kscan,
                            (uint64_t *)w.cand.p, ctrl, nullptr,
                            auto_route && quant ? (float *)w.wide.p : nullptr,
-                           (uint32_t *)w.hist.p, ix->num_sms * kMaxCtasPerSm, st,
+                           ws_hist(w), ix->num_sms * kMaxCtasPerSm, st,
                            !auto_route || planned, (const float *)w.wide.p,
                            auto_route ? &ctrl->route : nullptr, &nl));
       ix->launches += nl;  // (k_absmax, k_pack) k_fused_window
@@ -1270,24 +1289,24 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
   pm.mark(3, st);
   const uint32_t p2 = pow2_at_least(std::max<uint32_t>(kscan, 1));
   if (!quant) {
-    k_final_select<<<1, kFinalThreads, (size_t)p2 * 8, st>>>(
-        (const uint64_t *)w.cand.p, ctrl, 0, k, kmax, ids, scores, nullptr);
-    EBR_CUDA_TRY(cudaGetLastError());
+    EBR_CUDA_TRY(launch_pdl(k_final_select, 1, kFinalThreads, final_smem(p2), st,
+                            (const uint64_t *)w.cand.p, (const Ctrl *)ctrl, 0u, k, kmax, ids,
+                            scores, (uint64_t *)nullptr, kFinalBufKeys));
     ix->launches += 1;
   } else {
     // R*K candidates -> FP32 rescoring -> K
     const uint64_t *ck = (const uint64_t *)w.cand.p;
     uint64_t *sel = (uint64_t *)w.cand.p + (w.cand.bytes / 8 - 2 * (size_t)p2);
     uint64_t *res = sel + p2;
-    k_final_select<<<1, kFinalThreads, (size_t)p2 * 8, st>>>(ck, ctrl, 0, kscan, kscan, nullptr,
-                                                             nullptr, sel);
-    EBR_CUDA_TRY(cudaGetLastError());
+    EBR_CUDA_TRY(launch_pdl(k_final_select, 1, kFinalThreads, final_smem(p2), st, ck,
+                            (const Ctrl *)ctrl, 0u, kscan, kscan, (uint32_t *)nullptr,
+                            (float *)nullptr, sel, kFinalBufKeys));
     k_rescore<<<launch_grid((uint64_t)kscan * 32, 256, 4096), 256, 0, st>>>(
         sel, kscan, (const float *)ix->emb_f32.p, ix->d, q.h_u, (const float *)w.wide.p, res);
     EBR_CUDA_TRY(cudaGetLastError());
     const uint32_t p2k = pow2_at_least(std::max<uint32_t>(std::min(k, kscan), 1));
-    k_final_select<<<1, kFinalThreads, (size_t)p2k * 8, st>>>(res, nullptr, kscan, k, kmax, ids,
-                                                              scores, nullptr);
+    k_final_select<<<1, kFinalThreads, final_smem(p2k), st>>>(res, nullptr, kscan, k, kmax, ids,
+                                                               scores, nullptr, kFinalBufKeys);
     EBR_CUDA_TRY(cudaGetLastError());
     ix->launches += 3;
   }
@@ -1682,7 +1701,7 @@ static int single_query_prep(ebr_index *ix, const ebr_cross *cross, const ebr_qu
   EBR_TRY(check_query(ix, cross, qq));
   EBR_TRY(ws_prepare(ix, (q->user_vals || !q->q_key) ? ix->n_keys : q->n_q, 256));
   *ctrl = (Ctrl *)ix->ws.ctrl.p;
-  EBR_CUDA_TRY(cudaMemsetAsync(*ctrl, 0, sizeof(Ctrl), st));
+  EBR_CUDA_TRY(cudaMemsetAsync(*ctrl, 0, kCtrlBytes + kHistWords * 4, st));  // + histogram
   *q_key = q->q_key;
   *q_w = q->q_w;
   *n_q = q->n_q;
@@ -1726,7 +1745,7 @@ extern "C" int ebr_score_all(const ebr_index *cix, const ebr_cross *cross, const
                      fused_fits(ix, 1);
   if (fused) {
     rc = launch_fused(ix, q->h_u, q_w, (uint32_t *)ix->ws.wq.p, false, nullptr, 1, nullptr, ctrl,
-                      out_scores, nullptr, (uint32_t *)ix->ws.hist.p,
+                      out_scores, nullptr, ws_hist(ix->ws),
                       ix->num_sms * kMaxCtasPerSm, st);
   } else {
     if (rc == EBR_OK) rc = run_wide(ix, q_key, q_w, n_q, ctrl, st);
@@ -2007,7 +2026,7 @@ extern "C" int ebr_scan_topk_noalloc(const float *emb, uint32_t n_ads, uint32_t 
     uint32_t p2 = 1;
     while (p2 < k) p2 <<= 1;
     k_final_select<<<1, kFinalThreads, (size_t)p2 * 8, st>>>(cand, ctrl, 0, k, k, out_ids,
-                                                             out_scores, nullptr);
+                                                             out_scores, nullptr, 0u);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
       set_error("ebr_scan_topk_noalloc: %s", cudaGetErrorString(e));
