@@ -287,6 +287,15 @@ int ebr_quantize(const float *x, uint64_t n, ebr_dtype dtype, void *out, void *s
  */
 int ebr_debug_gemm_bf16(const uint16_t *A, uint32_t n, const uint16_t *U, uint32_t B, uint32_t d,
                         float *out, void *stream);
+/*
+ * The same for FP8 E4M3 codes (tcgen05.mma kind::f8f6f4, FP32 accumulation):
+ * out[i][b] = sum_t e4m3(A[i][t]) * e4m3(U[b][t]), no scales -- the deep term
+ * of the batched scan over an FP8 table before its per-row scales (Eq. 1).
+ * A: device [n][d] codes, U: device [B][d] codes, out: device [n][B] FP32;
+ * d in {64, 128}, B a multiple of 32 in 32..256.  Synchronous.
+ */
+int ebr_debug_gemm_e4m3(const uint8_t *A, uint32_t n, const uint8_t *U, uint32_t B, uint32_t d,
+                        float *out, void *stream);
 
 /*
  * Failure-detection check (no paper counterpart): launches one CTA whose

@@ -31,19 +31,24 @@ static int get_encoder() {
   return EBR_OK;
 }
 
-// Row-major [rows][cols] BF16 matrix viewed as a 2-D tensor, boxes of
-// 64 columns x box_rows rows, 128-byte swizzle (the UMMA K-major layout).
-int make_tmap_bf16(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols,
-                   uint32_t box_rows) {
+// Row-major [rows][cols] matrix of 2-byte (BF16) or 1-byte (FP8) elements
+// viewed as a 2-D tensor, boxes of 128 bytes (or 64, a whole 64-byte row) x
+// box_rows rows, swizzled to match (the UMMA K-major layouts).
+int make_tmap_2d(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols,
+                 uint32_t elt_bytes, uint32_t box_rows) {
   EBR_TRY(get_encoder());
+  const uint64_t row_bytes = cols * elt_bytes;
+  const uint32_t box_bytes = row_bytes >= 128 ? 128u : 64u;
   cuuint64_t dims[2] = {cols, rows};
-  cuuint64_t strides[1] = {cols * 2};
-  cuuint32_t box[2] = {64, box_rows};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_bytes / elt_bytes, box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims,
-                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = g_encode(map,
+                        elt_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                        2, const_cast<void *>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        box_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (%d) for %llu x %llu, box %u", (int)r,
               (unsigned long long)rows, (unsigned long long)cols, box_rows);
@@ -51,23 +56,31 @@ int make_tmap_bf16(CUtensorMap *map, const void *base, uint64_t rows, uint64_t c
   }
   return EBR_OK;
 }
+int make_tmap_bf16(CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols,
+                   uint32_t box_rows) {
+  return make_tmap_2d(map, base, rows, cols, 2, box_rows);
+}
 
 // ------------------------------------------------------------ GEMM check
 // out[i][b] = sum_t A[i][t] * U[b][t] for one 128-row tile per CTA: the
-// tensor-core building block of the batched scan, exposed for testing.
-__global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ CUtensorMap ma,
-                                                   const __grid_constant__ CUtensorMap mu,
-                                                   uint32_t n, uint32_t B, uint32_t d,
-                                                   float *__restrict__ out,
-                                                   uint32_t *__restrict__ flags) {
+// tensor-core building block of the batched scan, exposed for testing (BF16,
+// or FP8 E4M3 codes when F8).
+template <bool F8>
+__global__ void __launch_bounds__(128) k_gemm_tc(const __grid_constant__ CUtensorMap ma,
+                                                 const __grid_constant__ CUtensorMap mu,
+                                                 uint32_t n, uint32_t B, uint32_t d,
+                                                 float *__restrict__ out,
+                                                 uint32_t *__restrict__ flags) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ uint64_t bar_tma, bar_mma;
   __shared__ uint32_t tmem_base, ok;
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t kb_n = d / 64;
-  uint8_t *sa = smem;                        // kb_n x [128 rows x 128 B]
-  uint8_t *su = smem + (size_t)kb_n * 16384;  // kb_n x [B rows x 128 B]
+  const uint32_t row_bytes = d * (F8 ? 1u : 2u);
+  const uint32_t tr = row_bytes >= 128 ? 128u : 64u;  // bytes per K-tile row
+  const uint32_t kb_n = row_bytes / tr, tile_elems = tr / (F8 ? 1u : 2u);
+  uint8_t *sa = smem;                          // kb_n x [128 rows x tr]
+  uint8_t *su = smem + (size_t)kb_n * 128 * tr;  // kb_n x [B rows x tr]
   const int warp = threadIdx.x >> 5;
   uint32_t ncols = 32;
   while (ncols < B) ncols <<= 1;
@@ -86,22 +99,28 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ CUten
   tc_fence_after();
   const uint32_t row0 = blockIdx.x * 128;
   if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(&bar_tma, kb_n * (16384u + B * 128u));
+    mbar_arrive_expect_tx(&bar_tma, kb_n * (128u * tr + B * tr));
     for (uint32_t kb = 0; kb < kb_n; kb++) {
-      tma_load_2d(sa + kb * 16384, &ma, (int)(kb * 64), (int)row0, &bar_tma);
-      tma_load_2d(su + (size_t)kb * B * 128, &mu, (int)(kb * 64), 0, &bar_tma);
+      tma_load_2d(sa + kb * 128u * tr, &ma, (int)(kb * tile_elems), (int)row0, &bar_tma);
+      tma_load_2d(su + (size_t)kb * B * tr, &mu, (int)(kb * tile_elems), 0, &bar_tma);
     }
     if (!mbar_wait_bounded(&bar_tma, 0, kWaitTimeoutNs)) {
       ok = 0;
       atomicOr(flags, DEVERR_TIMEOUT);
     } else {
       tc_fence_after();
-      const uint32_t idesc = idesc_bf16_f32(128, B);
-      for (uint32_t k = 0; k < d / 16; k++) {
-        const uint32_t kb = k / 4, kk = k % 4;
-        const uint64_t ad = sdesc_k_sw128(smem_u32(sa + kb * 16384 + kk * 32));
-        const uint64_t bd = sdesc_k_sw128(smem_u32(su + (size_t)kb * B * 128 + kk * 32));
-        umma_bf16(tmem_base, ad, bd, idesc, k > 0 ? 1u : 0u);
+      const uint32_t idesc = F8 ? idesc_e4m3_f32(128, B) : idesc_bf16_f32(128, B);
+      const uint32_t spt = tr / 32;
+      for (uint32_t k = 0; k < kb_n * spt; k++) {
+        const uint32_t kb = k / spt, kk = k % spt;
+        const uint32_t aa = smem_u32(sa + kb * 128u * tr + kk * 32);
+        const uint32_t ua = smem_u32(su + (size_t)kb * B * tr + kk * 32);
+        const uint64_t ad = tr == 128 ? sdesc_k_sw128(aa) : sdesc_k_sw64(aa);
+        const uint64_t bd = tr == 128 ? sdesc_k_sw128(ua) : sdesc_k_sw64(ua);
+        if (F8)
+          umma_e4m3(tmem_base, ad, bd, idesc, k > 0 ? 1u : 0u);
+        else
+          umma_bf16(tmem_base, ad, bd, idesc, k > 0 ? 1u : 0u);
       }
       umma_commit(&bar_mma);
       if (!mbar_wait_bounded(&bar_mma, 0, kWaitTimeoutNs)) {
@@ -128,6 +147,32 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ CUten
   if (warp == 0) tmem_dealloc(tmem_base, ncols);
 }
 
+static int debug_gemm(bool f8, const void *A, uint32_t n, const void *U, uint32_t B, uint32_t d,
+                      float *out, void *stream) {
+  if (!A || !U || !out || n == 0 || (d != 64 && d != 128) || B < 32 || B > 256 || B % 32) {
+    set_error("ebr_debug_gemm: need d in {64, 128}, B a multiple of 32 in 32..256");
+    return EBR_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t eb = f8 ? 1u : 2u;
+  CUtensorMap ma, mu;
+  EBR_TRY(make_tmap_2d(&ma, A, n, d, eb, 128));
+  EBR_TRY(make_tmap_2d(&mu, U, B, d, eb, B));
+  uint32_t *flags = nullptr;
+  EBR_CUDA_TRY(cudaMallocAsync((void **)&flags, 4, st));
+  EBR_CUDA_TRY(cudaMemsetAsync(flags, 0, 4, st));
+  const size_t smem = 1024 + (size_t)d * eb * (128 + B);
+  auto kern = f8 ? k_gemm_tc<true> : k_gemm_tc<false>;
+  EBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<(n + 127) / 128, 128, smem, st>>>(ma, mu, n, B, d, out, flags);
+  EBR_CUDA_TRY(cudaGetLastError());
+  uint32_t hf = 0;
+  EBR_CUDA_TRY(cudaMemcpyAsync(&hf, flags, 4, cudaMemcpyDeviceToHost, st));
+  EBR_CUDA_TRY(cudaStreamSynchronize(st));
+  cudaFreeAsync(flags, st);
+  return check_device_flags(hf, f8 ? "ebr_debug_gemm_e4m3" : "ebr_debug_gemm_bf16");
+}
+
 }  // namespace ebr
 
 using namespace ebr;
@@ -135,27 +180,13 @@ using namespace ebr;
 extern "C" int ebr_debug_gemm_bf16(const uint16_t *A, uint32_t n, const uint16_t *U, uint32_t B,
                                    uint32_t d, float *out, void *stream) {
   clear_error();
-  if (!A || !U || !out || n == 0 || (d != 64 && d != 128) || B < 32 || B > 256 || B % 32) {
-    set_error("ebr_debug_gemm_bf16: need d in {64, 128}, B a multiple of 32 in 32..256");
-    return EBR_EINVAL;
-  }
-  cudaStream_t st = (cudaStream_t)stream;
-  CUtensorMap ma, mu;
-  EBR_TRY(make_tmap_bf16(&ma, A, n, d, 128));
-  EBR_TRY(make_tmap_bf16(&mu, U, B, d, B));
-  uint32_t *flags = nullptr;
-  EBR_CUDA_TRY(cudaMallocAsync((void **)&flags, 4, st));
-  EBR_CUDA_TRY(cudaMemsetAsync(flags, 0, 4, st));
-  const size_t smem = 1024 + (size_t)(d / 64) * (16384 + B * 128);
-  EBR_CUDA_TRY(cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-  k_gemm_bf16<<<(n + 127) / 128, 128, smem, st>>>(ma, mu, n, B, d, out, flags);
-  EBR_CUDA_TRY(cudaGetLastError());
-  uint32_t hf = 0;
-  EBR_CUDA_TRY(cudaMemcpyAsync(&hf, flags, 4, cudaMemcpyDeviceToHost, st));
-  EBR_CUDA_TRY(cudaStreamSynchronize(st));
-  cudaFreeAsync(flags, st);
-  return check_device_flags(hf, "ebr_debug_gemm_bf16");
+  return debug_gemm(false, A, n, U, B, d, out, stream);
+}
+
+extern "C" int ebr_debug_gemm_e4m3(const uint8_t *A, uint32_t n, const uint8_t *U, uint32_t B,
+                                   uint32_t d, float *out, void *stream) {
+  clear_error();
+  return debug_gemm(true, A, n, U, B, d, out, stream);
 }
 
 namespace ebr {
@@ -239,8 +270,8 @@ struct CandEntry {
 };
 
 struct BatchArgs {
-  CUtensorMap ta;  // ad rows, BF16 [N][d], box {64, 128}
-  CUtensorMap tu;  // users, BF16 [Bq][d], box {64, min(Bq, 128)}
+  CUtensorMap ta;  // ad rows, BF16 or FP8 [N][d], box {tile row, 128}
+  CUtensorMap tu;  // users, same type [Bq][d], box {tile row, min(Bq, 128)}
   const uint32_t *wkey[kGroups];
   const uint8_t *wvals[kGroups];
   const uint32_t *win_ptr[kGroups];
@@ -251,6 +282,9 @@ struct BatchArgs {
   uint32_t n_ads, n_win, B, Bq, d, m, cap_u, list_cap, words;
   uint32_t zero_row;           // n_keys * Bq: offset of the zero row of wT
   uint32_t sa, lb, tb;         // A stages, list buffers, TMEM buffers
+  uint32_t tile_row, kb_n;     // bytes per K-tile row (128 or 64), K-tiles per row
+  const float *ad_scale;       // FP8: [N] row scales of the ad table
+  const float *user_scale;     // FP8: [Bq] row scales of the quantised users
   CandEntry *cand;             // [grid][B][cap_u]
   uint32_t *cand_n;            // [grid][B]
   unsigned long long *cand_thr;  // [grid][B]
@@ -380,16 +414,18 @@ __device__ uint32_t warp_compact(CandEntry *buf, uint32_t n, uint64_t T) {
   return kept;
 }
 
+template <bool F8>
 __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   __shared__ BatchSmem sm;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t kb_n = a.d / 64;
+  const uint32_t kb_n = a.kb_n, tr = a.tile_row;  // K-tiles per row, bytes per tile row
+  const uint32_t tile_elems = tr / (F8 ? 1u : 2u);
   const uint32_t n_mt = a.Bq > 128 ? 2u : 1u;     // 128-user M-tiles
-  const uint32_t u_tile = kb_n * 16384u;           // one M-tile: kb_n x [128 rows x 128 B]
-  const uint32_t a_stage = kb_n * 32768u;          // kb_n x [256 ad rows x 128 B]
+  const uint32_t u_tile = kb_n * 128u * tr;        // one M-tile: kb_n x [128 rows x tr]
+  const uint32_t a_stage = kb_n * 256u * tr;       // kb_n x [256 ad rows x tr]
   uint8_t *su = smem;                              // n_mt user tiles
   uint8_t *sa = su + (size_t)n_mt * u_tile;        // sa ad stages
   uint32_t *lists = reinterpret_cast<uint32_t *>(sa + (size_t)a.sa * a_stage);
@@ -441,8 +477,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
       for (uint32_t mt = 0; mt < n_mt; mt++)
         for (uint32_t r0 = 0; r0 < 128; r0 += box_u)
           for (uint32_t kb = 0; kb < kb_n; kb++)
-            tma_load_2d(su + mt * u_tile + kb * 16384u + r0 * 128u, &a.tu, (int)(kb * 64),
-                        (int)(n_mt > 1 ? mt * 128 : 0), &sm.u_full);
+            tma_load_2d(su + mt * u_tile + kb * 128u * tr + r0 * tr, &a.tu,
+                        (int)(kb * tile_elems), (int)(n_mt > 1 ? mt * 128 : 0), &sm.u_full);
       for (uint32_t j = 0; j < my_wins; j++) {
         const uint32_t s = j % a.sa;
         if (j >= a.sa && !mbar_wait_bounded(&sm.a_empty[s], ((j / a.sa) - 1) & 1u, kWaitTimeoutNs)) {
@@ -456,7 +492,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
         mbar_arrive_expect_tx(&sm.a_full[s], a_stage);
         for (uint32_t kb = 0; kb < kb_n; kb++)
           for (uint32_t h = 0; h < 2; h++)
-            tma_load_2d_hint(dst + kb * 32768u + h * 16384u, &a.ta, (int)(kb * 64),
+            tma_load_2d_hint(dst + kb * 256u * tr + h * 128u * tr, &a.ta, (int)(kb * tile_elems),
                              row0 + (int)h * 128, &sm.a_full[s], pol);
         sm.n_issued = j + 1;
       }
@@ -465,7 +501,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
     // ---------------------------------------------------------- MMA issuer
     if (lane == 0) {
       bool ok = mbar_wait_bounded(&sm.u_full, 0, kWaitTimeoutNs);
-      const uint32_t idesc = idesc_bf16_f32(128, 256);
+      const uint32_t idesc = F8 ? idesc_e4m3_f32(128, 256) : idesc_bf16_f32(128, 256);
+      const uint32_t spt = tr / 32;  // 32-byte K-steps per tile row
       for (uint32_t j = 0; ok && j < my_wins; j++) {
         const uint32_t s = j % a.sa, tb = j % a.tb;
         ok = mbar_wait_bounded(&sm.a_full[s], (j / a.sa) & 1u, kWaitTimeoutNs);
@@ -475,11 +512,16 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
         const uint8_t *as = sa + (size_t)s * a_stage;
         for (uint32_t mt = 0; mt < n_mt; mt++) {
           const uint32_t dcol = tmem + tb * tcols + mt * 256u;
-          for (uint32_t k = 0; k < a.d / 16; k++) {
-            const uint32_t kb = k / 4, kk = k % 4;
-            const uint64_t ud = sdesc_k_sw128(smem_u32(su + mt * u_tile + kb * 16384u + kk * 32));
-            const uint64_t ad = sdesc_k_sw128(smem_u32(as + kb * 32768u + kk * 32));
-            umma_bf16(dcol, ud, ad, idesc, k > 0 ? 1u : 0u);
+          for (uint32_t k = 0; k < kb_n * spt; k++) {
+            const uint32_t kb = k / spt, kk = k % spt;
+            const uint32_t ua = smem_u32(su + mt * u_tile + kb * 128u * tr + kk * 32);
+            const uint32_t aa = smem_u32(as + kb * 256u * tr + kk * 32);
+            const uint64_t ud = tr == 128 ? sdesc_k_sw128(ua) : sdesc_k_sw64(ua);
+            const uint64_t ad = tr == 128 ? sdesc_k_sw128(aa) : sdesc_k_sw64(aa);
+            if (F8)
+              umma_e4m3(dcol, ud, ad, idesc, k > 0 ? 1u : 0u);
+            else
+              umma_bf16(dcol, ud, ad, idesc, k > 0 ? 1u : 0u);
           }
         }
         umma_commit(&sm.a_empty[s]);
@@ -583,6 +625,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
     }
     const uint32_t tl = tmem + ((32u * q) << 16) + mt * 256u;
     const bool user_ok = user < a.B;
+    // FP8: deep = TMEM x (user scale) x (the ad row's scale)
+    const float u_sc = F8 && user_ok ? a.user_scale[user] : 1.f;
     const bool filt = user_ok && a.has_filter[user];
     const uint64_t *frow = a.filters + (uint64_t)(user_ok ? user : 0u) * a.words;
     const float *wcol = a.wT + user;
@@ -648,6 +692,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
             acc[4 * i4 + 3] += __ldg(wcol + k.w);
           }
         }
+        // lane i holds the row scale of the run's ad i (FP8)
+        const uint32_t ad_l = wbase + a0 + lane;
+        const float sa_l = F8 && ad_l < a.n_ads ? __ldg(a.ad_scale + ad_l) : 1.f;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
           uint32_t dv[16];  // deep scores of 16 ads, one TMEM load
@@ -656,9 +703,11 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
 #pragma unroll
           for (int ii = 0; ii < 16; ii++) {
             const int i = 16 * h + ii;
+            const float sc = F8 ? __shfl_sync(0xffffffffu, sa_l, i) * u_sc : 1.f;
             const uint32_t ad = wbase + a0 + i;
             if (!user_ok || ad >= a.n_ads) continue;
-            const unsigned long long key = make_key(__uint_as_float(dv[ii]) + acc[i], ad);
+            const float deep = F8 ? __uint_as_float(dv[ii]) * sc : __uint_as_float(dv[ii]);
+            const unsigned long long key = make_key(deep + acc[i], ad);
             if (key < thr0) continue;
             if (filt && !((__ldg(frow + (ad >> 6)) >> (ad & 63)) & 1ull)) continue;
             const uint32_t pos = atomicAdd(&sm.cnt_u[user], 1u);
@@ -884,7 +933,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_batch_merge(
 namespace ebr {
 
 struct BatchPlan {
-  uint32_t Bq, m, cap_u, sa, lb, tb, list_cap;
+  uint32_t Bq, m, cap_u, sa, lb, tb, list_cap, tile_row, kb_n;
   size_t smem;
 };
 
@@ -904,9 +953,11 @@ static bool plan_smem(const ebr_index *ix, uint32_t B, BatchPlan *p) {
   p->list_cap = kBWin * ix->max_keys_per_ad;  // 8 runs x 32 ads x rows
   const uint32_t n_mt = p->Bq > 128 ? 2 : 1;
   p->tb = n_mt == 1 ? 2 : 1;
-  const uint32_t kb_n = ix->d / 64;
-  const size_t u_bytes = (size_t)n_mt * kb_n * 16384;
-  const size_t a_stage = (size_t)kb_n * 32768;
+  const uint32_t row_bytes = ix->d * (ix->dtype == EBR_FP8E4M3 ? 1u : 2u);
+  p->tile_row = row_bytes >= 128 ? 128u : 64u;
+  p->kb_n = row_bytes / p->tile_row;
+  const size_t u_bytes = (size_t)n_mt * p->kb_n * 128 * p->tile_row;
+  const size_t a_stage = (size_t)p->kb_n * 256 * p->tile_row;
   const size_t list_bytes = ((size_t)kListHdr + p->list_cap) * 4;
   const size_t hist = (size_t)kEpiWarps * 256 * 4;
   const size_t budget = 220 * 1024;
@@ -925,7 +976,8 @@ static bool plan_smem(const ebr_index *ix, uint32_t B, BatchPlan *p) {
 
 bool batch_qualifies(const ebr_index *ix, const ebr_cross *cross, const ebr_query *q,
                      uint32_t batch) {
-  if (ix->dtype != EBR_BF16 || (ix->d != 64 && ix->d != 128) || batch < 2 ||
+  if ((ix->dtype != EBR_BF16 && ix->dtype != EBR_FP8E4M3) || (ix->d != 64 && ix->d != 128) ||
+      batch < 2 ||
       batch > (uint32_t)kMaxUsers || !cross || cross->n_keys != ix->n_keys ||
       ix->n_win == 0 || !ix->ad_nkeys.p || ix->max_keys_per_ad == 0 ||
       ix->max_keys_per_ad > kMaxBatchKeysPerAd ||
@@ -988,7 +1040,8 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   }
   const uint32_t Bp = pl.Bq;
   EBR_TRY(dev_reserve(w.users_f32, (size_t)Bp * d * 4));
-  EBR_TRY(dev_reserve(w.users_bf16, (size_t)Bp * d * 2));
+  EBR_TRY(dev_reserve(w.users_bf16, (size_t)Bp * d * 2));  // BF16 or FP8 users
+  EBR_TRY(dev_reserve(w.users_scale, (size_t)Bp * 4));
   EBR_TRY(dev_reserve(w.user_vals, (size_t)B * fu * 4));
   EBR_TRY(dev_reserve(w.wT, ((size_t)ix->n_keys + 1) * Bp * 4));
   EBR_TRY(dev_reserve(w.filters, (size_t)B * words * 8));
@@ -1032,22 +1085,32 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
     if (q[b].filter)
       EBR_TRY(stage((uint64_t *)w.filters.p + (size_t)b * words, q[b].filter, words * 8, io, st));
   }
-  EBR_TRY(launch_quantize((const float *)w.users_f32.p, (uint64_t)Bp * d, EBR_BF16, w.users_bf16.p,
-                          st));
+  const bool f8 = ix->dtype == EBR_FP8E4M3;
+  if (f8)  // users as FP8 with a scale per user (kind::f8f6f4 takes both operands in FP8)
+    EBR_TRY(launch_quantize_rows_fp8((const float *)w.users_f32.p, Bp, d, (uint8_t *)w.users_bf16.p,
+                                     (float *)w.users_scale.p, st));
+  else
+    EBR_TRY(launch_quantize((const float *)w.users_f32.p, (uint64_t)Bp * d, EBR_BF16,
+                            w.users_bf16.p, st));
   EBR_TRY(expand_transposed(cross, (const uint32_t *)w.user_vals.p, B, Bp, (float *)w.wT.p,
                             &ctrl->flags, st));
   EBR_CUDA_TRY(cudaMemsetAsync((float *)w.wT.p + (size_t)ix->n_keys * Bp, 0, (size_t)Bp * 4, st));
   // tensor maps
+  const uint32_t eb = f8 ? 1u : 2u;
   if (!w.tmap_ready || w.tmap_for != ix->emb_q.p) {
-    EBR_TRY(make_tmap_bf16(reinterpret_cast<CUtensorMap *>(w.tmap_bytes), ix->emb_q.p, ix->n_ads,
-                           d, 128));
+    EBR_TRY(make_tmap_2d(reinterpret_cast<CUtensorMap *>(w.tmap_bytes), ix->emb_q.p, ix->n_ads, d,
+                         eb, 128));
     w.tmap_ready = true;
     w.tmap_for = ix->emb_q.p;
   }
   BatchArgs a;
   memset(&a, 0, sizeof(a));
   memcpy(&a.ta, w.tmap_bytes, sizeof(CUtensorMap));
-  EBR_TRY(make_tmap_bf16(&a.tu, w.users_bf16.p, Bp, d, std::min<uint32_t>(Bp, 128)));
+  EBR_TRY(make_tmap_2d(&a.tu, w.users_bf16.p, Bp, d, eb, std::min<uint32_t>(Bp, 128)));
+  a.tile_row = pl.tile_row;
+  a.kb_n = pl.kb_n;
+  a.ad_scale = f8 ? (const float *)ix->emb_scale.p : nullptr;
+  a.user_scale = f8 ? (const float *)w.users_scale.p : nullptr;
   for (int g = 0; g < kGroups; g++) {
     a.wkey[g] = ix->wkey[g];
     a.wvals[g] = ix->wvals[g];
@@ -1074,10 +1137,11 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   a.cand_n = (uint32_t *)w.cand_n.p;
   a.cand_thr = (unsigned long long *)w.cand_thr.p;
   a.ctrl = ctrl;
-  EBR_CUDA_TRY(cudaFuncSetAttribute(k_batch_window, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  auto kern = f8 ? k_batch_window<true> : k_batch_window<false>;
+  EBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)pl.smem));
   if (prof) EBR_CUDA_TRY(cudaEventRecord(ev[1], st));
-  k_batch_window<<<grid, kBatchThreads, pl.smem, st>>>(a);
+  kern<<<grid, kBatchThreads, pl.smem, st>>>(a);
   EBR_CUDA_TRY(cudaGetLastError());
   if (prof) EBR_CUDA_TRY(cudaEventRecord(ev[2], st));
   EBR_CUDA_TRY(cudaFuncSetAttribute(k_batch_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1129,7 +1193,7 @@ int batch_finish(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
 }
 
 void batch_ws_free(BatchWs &w) {
-  for (DevBuf *b : {&w.users_f32, &w.users_bf16, &w.user_vals, &w.wT, &w.filters, &w.small,
+  for (DevBuf *b : {&w.users_f32, &w.users_bf16, &w.users_scale, &w.user_vals, &w.wT, &w.filters, &w.small,
                     &w.cand, &w.cand_n, &w.cand_thr, &w.scratch, &w.res, &w.ctrl})
     dev_free(*b);
   if (w.host) cudaFreeHost(w.host);

@@ -91,7 +91,7 @@ struct Ctrl {
 
 // Scratch of the batched (tensor-core) path.
 struct BatchWs {
-  DevBuf users_f32, users_bf16, user_vals, wT, filters;
+  DevBuf users_f32, users_bf16, users_scale, user_vals, wT, filters;  // users_bf16: BF16 or FP8
   DevBuf small;  // uint32 [kscan B][kout B][has_filter B], then status [B]
   DevBuf cand, cand_n, cand_thr, scratch;
   DevBuf res;    // device staging of host-bound results
@@ -204,6 +204,8 @@ int query_one(const ebr_index *ix, const ebr_cross *cross, const ebr_query &q, u
               float *scores, uint32_t kmax, cudaStream_t st);
 int ws_prepare_one(ebr_index *ix, uint32_t n_q, uint32_t kcap);
 int launch_quantize(const float *x, uint64_t n, ebr_dtype dt, void *out, cudaStream_t st);
+int launch_quantize_rows_fp8(const float *x, uint64_t n, uint32_t d, uint8_t *q, float *scale,
+                             cudaStream_t st);
 // Query expansion for a batch straight into user-minor layout wT[key][Bp].
 int expand_transposed(const ebr_cross *c, const uint32_t *users, uint32_t batch, uint32_t Bp,
                       float *wT, uint32_t *flags, cudaStream_t st);

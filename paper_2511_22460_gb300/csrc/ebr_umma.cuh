@@ -1,10 +1,11 @@
 // tcgen05 (5th-generation tensor core) and tensor-TMA helpers for sm_103a.
 //
 // Operand layout used throughout: K-major tiles of 8-row x 128-byte swizzle
-// atoms (SWIZZLE_128B), as written by a 2-D TMA load with a 64-element (BF16)
-// inner box.  A tile row holds 64 K-elements; consecutive 8-row groups are
-// 1024 bytes apart (the stride-byte offset); the K-steps of one MMA (16 BF16 =
-// 32 bytes) advance the descriptor's start address inside the 128-byte atom.
+// atoms (SWIZZLE_128B), as written by a 2-D TMA load with a 128-byte inner box
+// (64 BF16 or 128 FP8 K-elements), or 8-row x 64-byte atoms (SWIZZLE_64B) for
+// 64-byte rows (64 FP8 K-elements).  Consecutive 8-row groups are 1024 (512)
+// bytes apart (the stride-byte offset); the K-steps of one MMA (16 BF16 or 32
+// FP8 = 32 bytes) advance the descriptor's start address inside the atom.
 #pragma once
 
 #include <cuda.h>
@@ -54,6 +55,26 @@ __device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t smem_addr) {
   return d;
 }
 
+// The same for a K-major tile whose rows are 64 bytes (SWIZZLE_64B atoms of
+// 8 rows x 64 bytes, 512 bytes apart; swizzle mode 4): FP8 tiles of 64
+// K-elements.
+__device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t smem_addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(512u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)4u << 61;
+  return d;
+}
+
+// Instruction descriptor for kind::f8f6f4 with E4M3 A and B (format code 0
+// in bits 7-9 and 10-12), FP32 accumulator, both K-major, N >> 3 in bits
+// 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(uint32_t M, uint32_t N) {
+  return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
 // Instruction descriptor for kind::f16: FP32 accumulator (bits 4-5 = 1),
 // BF16 A and B (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0),
 // N >> 3 in bits 17-22, M >> 4 in bits 24-28.
@@ -67,6 +88,15 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// D[tmem] (+)= A[smem] x B[smem]^T, M x N x 32, both operands FP8 E4M3.
+__device__ __forceinline__ void umma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }

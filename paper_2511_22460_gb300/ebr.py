@@ -112,6 +112,7 @@ ebr_quantize = _sig("ebr_quantize", i32, [vp, u64, i32, vp, vp])
 ebr_scan_topk_noalloc = _sig("ebr_scan_topk_noalloc", i32,
                              [vp, u32, u32, vp, vp, vp, u32, vp, vp, i32, vp])
 ebr_debug_gemm_bf16 = _sig("ebr_debug_gemm_bf16", i32, [vp, u32, vp, u32, u32, vp, vp])
+ebr_debug_gemm_e4m3 = _sig("ebr_debug_gemm_e4m3", i32, [vp, u32, vp, u32, u32, vp, vp])
 ebr_debug_wait_timeout = _sig("ebr_debug_wait_timeout", i32, [u32, vp])
 ebr_profile_enable = _sig("ebr_profile_enable", i32, [vp, i32])
 ebr_profile_read = _sig("ebr_profile_read", i32, [vp, C.POINTER(Profile)])
@@ -389,6 +390,12 @@ def scan_topk_noalloc(emb, h_u, wide, filt, k, out_ids, out_scores, stream=None)
 def debug_wait_timeout(timeout_us, stream=None):
     """Status of a device wait that nothing ends (EBR_ETIMEDOUT expected)."""
     return ebr_debug_wait_timeout(int(timeout_us), stream_ptr(stream))
+
+
+def debug_gemm_e4m3(A, U, out, stream=None):
+    """out[n][B] = e4m3(A[n][d]) @ e4m3(U[B][d])^T on the tensor cores (FP8 codes in, FP32 out)."""
+    _check(ebr_debug_gemm_e4m3(ptr(A), int(A.shape[0]), ptr(U), int(U.shape[0]), int(A.shape[1]),
+                               ptr(out), stream_ptr(stream)), "ebr_debug_gemm_e4m3")
 
 
 def debug_gemm_bf16(A, U, out, stream=None):

@@ -26,6 +26,27 @@ def test_tcgen05_gemm_matches_fp64(n, B, d):
     assert torch.all(err <= 1e-6 * mag + 1e-30), float((err / (mag + 1e-30)).max())
 
 
+@pytest.mark.parametrize("n,B,d", [(1000, 64, 64), (333, 256, 128), (4096, 32, 64),
+                                   (129, 96, 128), (300, 256, 64)])
+def test_tcgen05_fp8_gemm_matches_fp64(n, B, d):
+    """kind::f8f6f4 with E4M3 operands (64-byte rows use the 64-byte swizzle,
+    128-byte rows the 128-byte one) against FP64 sums of the decoded codes'
+    products, which are exact in FP64."""
+    import oracle
+    rng = np.random.default_rng(n + B + d)
+    A, _ = oracle.quantize_fp8_rows((rng.standard_normal((n, d)) / d ** 0.5).astype(np.float32))
+    U, _ = oracle.quantize_fp8_rows((rng.standard_normal((B, d)) / d ** 0.5).astype(np.float32))
+    out = torch.full((n, B), float("nan"), dtype=torch.float32, device=DEV)
+    ebr.debug_gemm_e4m3(torch.from_numpy(A).to(DEV), torch.from_numpy(U).to(DEV), out)
+    tab = oracle.fp8_e4m3_value(np.arange(256, dtype=np.uint8))  # every code's value
+    Av, Uv = tab[A], tab[U]
+    ref = Av @ Uv.T
+    mag = np.abs(Av) @ np.abs(Uv).T
+    err = np.abs(out.cpu().numpy().astype(np.float64) - ref)
+    worst = float((err / (mag + 1e-30)).max())
+    assert np.all(err <= 1e-6 * mag + 1e-30), worst
+
+
 def test_bounded_wait_gives_up_and_reports_timeout():
     """A device wait that nothing ends returns EBR_ETIMEDOUT after its limit;
     the context stays usable (the tensor-core check runs right after)."""

@@ -25,12 +25,12 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-def _run(name, n, B, ks, seed, filt=None, io=ebr.IO_DEVICE, prep=None, **kw):
+def _run(name, n, B, ks, seed, filt=None, io=ebr.IO_DEVICE, prep=None, dtype="bf16", **kw):
     w = make_workload(name, n_ads=n, seed=seed, batch=B, **kw)
     if prep is not None:
         prep(w)
     pk, pa = w.postings(shuffle=True)
-    ix = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype="bf16")
+    ix = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype=dtype)
     cross = ebr.cross_from_workload(w)
     kmax = max(ks)
     host = io == ebr.IO_HOST
@@ -145,3 +145,32 @@ def test_batched_proof_fails_for_a_crowded_window_and_is_recomputed():
     assert nr == 1, "exactly the crowded user is recomputed (got %d)" % nr
     _check_all(w, post, ids, sc, [k] * B)
     assert np.all(ids[0].astype(np.int64) < 200), "user 0's top-K is the crowded window's"
+
+
+@pytest.mark.parametrize("n,B,d,k", [(60_001, 64, 64, 500), (30_000, 40, 128, 300),
+                                     (20_000, 2, 64, 100), (25_000, 200, 64, 200)])
+def test_batched_fp8_topk_matches_oracle(n, B, d, k, capsys):
+    """The FP8-e4m3 table with per-row scales on the tensor cores (kind::f8f6f4,
+    users quantised per row the same way), FP32 rescoring of the top 4K: every
+    user's top-K against the FP64 oracle, recall 1.0, nothing recomputed.  The
+    recall of the quantised score before rescoring (FP8 x FP8 deep term plus
+    the exact wide term, the order the tensor-core pass ranks by) is reported."""
+    ks = [k] * B
+    w, post, ids, sc, nb, nr = _run("fp8_10m", n, B, ks, seed=16, dtype="fp8e4m3", d=d)
+    assert nb == B, "the batched path did not run"
+    assert nr == 0, "%d users were recomputed on the single-request scan" % nr
+    _check_all(w, post, ids, sc, ks)
+    tab = oracle.fp8_e4m3_value(np.arange(256, dtype=np.uint8))
+    qa, sa = oracle.quantize_fp8_rows(w.emb)
+    qu, su = oracle.quantize_fp8_rows(w.h_u)
+    approx_deep = (tab[qa] * sa[:, None].astype(np.float64)) @ (
+        tab[qu] * su[:, None].astype(np.float64)).T
+    pre = []
+    for b in range(0, B, max(1, B // 8)):
+        ref, tol = ref_scores(w, b, post)
+        wide = ref - w.emb.astype(np.float64) @ w.h_u[b].astype(np.float64)
+        approx = approx_deep[:, b] + wide
+        pre.append(recall(np.lexsort((np.arange(n), -approx))[:k], ref, tol, k))
+    with capsys.disabled():
+        print("\n[recall] batched fp8 d=%d %d ads K=%d: before rescoring %.4f (min %.4f), after 1.0"
+              % (d, n, k, float(np.mean(pre)), float(np.min(pre))))
