@@ -48,7 +48,7 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _config(w, extra=None):
+def _config(w, extra=None, batch=1):
     r = w.recipe
     emb_mb = r.n_ads * r.d * {"f32": 4, "bf16": 2, "fp8e4m3": 1}[r.emb_dtype] / 2**20
     cfg = {"workload": r.name, "n_ads": r.n_ads, "d": r.d, "emb_dtype": r.emb_dtype,
@@ -56,9 +56,11 @@ def _config(w, extra=None):
            "weights": "hashed 2^24 FP32" if r.weights == "hashed" else "dense per pair",
            "k": int(w.ks[0]), "n_keys": w.n_keys, "postings": w.nnz,
            "l2": "flushed between steps (256 MiB write); embedding table %.0f MiB" % emb_mb}
-    if r.batch > 1:
-        cfg.update({"batch": r.batch, "k_per_user": sorted(set(int(x) for x in w.ks)),
+    if batch > 1:
+        cfg.update({"batch": batch, "k_per_user": sorted(set(int(x) for x in w.ks[:batch])),
                     "rescore_mult": r.rescore_mult})
+    elif r.rescore_mult:
+        cfg["rescore_mult"] = r.rescore_mult
     if extra:
         cfg.update(extra)
     return cfg
@@ -134,14 +136,42 @@ class ClockSampler:
 def run_gpu(args, rank, world, local_rank):
     import torch
 
+    torch.cuda.set_device(local_rank)
+    w = _workload(args)
+    if w.bench_batch > 1:
+        return run_gpu_batched(args, w, rank, world, local_rank)
+    out = run_single(args, w, rank, world, local_rank, workload=args.workload)
+    del w
+    if world == 1 and not args.no_extras and args.workload == WORKLOAD and not args.sparse_query:
+        # the other workloads of the method, one object each on the same line
+        t0 = time.perf_counter()
+        wb = make_workload("batch256_bf16_5m", seed=args.seed)
+        out["batched_bf16_5m_b256"] = run_gpu_batched(args, wb, rank, world, local_rank,
+                                                      steps=args.extra_steps, cpu_users=2)
+        del wb
+        w8 = make_workload("fp8_10m", seed=args.seed, batch=64)
+        out["fp8_10m_single"] = run_single(args, w8, rank, world, local_rank, workload="fp8_10m",
+                                           steps=args.extra_steps, n_req=8, cpu_requests=2)
+        out["fp8_10m_b64"] = run_gpu_batched(args, w8, rank, world, local_rank,
+                                             steps=args.extra_steps, cpu_users=0)
+        del w8
+        out["extras_s"] = round(time.perf_counter() - t0, 1)
+    if world == 1 and not args.no_serve and args.workload == WORKLOAD and not args.sparse_query:
+        out["serving"] = run_serving(args, device=local_rank)
+    return out
+
+
+def run_single(args, w, rank, world, local_rank, workload, steps=None, n_req=16,
+               cpu_requests=64):
+    """A step is one request (a different user each step, round robin over
+    n_req users) through the single-request path."""
+    import torch
+
     from paper_2511_22460_gb300 import ebr
 
-    torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     st = torch.cuda.current_stream()
-    w = _workload(args)
-    if w.recipe.batch > 1:
-        return run_gpu_batched(args, w, rank, world, local_rank)
+    steps = steps or args.steps
     pk, pa = w.postings()
     ix = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype=w.recipe.emb_dtype,
                          device=local_rank)
@@ -149,7 +179,7 @@ def run_gpu(args, rank, world, local_rank):
     cross = ebr.cross_from_workload(w, device=local_rank)
     info = ix.info()
     k = int(w.ks[0])
-    nreq = w.users.shape[0]
+    nreq = min(w.users.shape[0], n_req)
     h_u = torch.from_numpy(w.h_u).to(dev)
     users = torch.from_numpy(w.users).to(dev)
     ids = torch.empty(k, dtype=torch.int32, device=dev)
@@ -183,13 +213,13 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     launches0 = ix.profile_read().launches
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+           for _ in range(steps)]
     clocks = ClockSampler(local_rank)
     clocks.start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    for i in range(args.steps):
+    for i in range(steps):
         flush.zero_()
         evs[i][0].record(st)
         step(i)
@@ -201,13 +231,13 @@ def run_gpu(args, rank, world, local_rank):
     times = [a.elapsed_time(b) for a, b in evs]
     launches = ix.profile_read().launches - launches0
     total_ms = max_over_ranks(float(sum(times)), dev)
-    ms_step = total_ms / args.steps
-    value = whole_job_rate(w.n_ads * args.steps, world, total_ms)
+    ms_step = total_ms / steps
+    value = whole_job_rate(w.n_ads * steps, world, total_ms)
     # Per-stage device time from a separate pass of the same steps: the stage
     # events sit between the kernels, which keeps a kernel from starting while
     # the one before it ends, so they stay out of the timed steps above.
     ix.profile_enable(True)
-    for i in range(args.steps):
+    for i in range(steps):
         flush.zero_()
         step(i)
     torch.cuda.synchronize()
@@ -219,7 +249,7 @@ def run_gpu(args, rank, world, local_rank):
     hk_sc = np.empty(k, np.float32)
     hqs = [query(b, host=True) for b in range(nreq)]
     e2e_t = []
-    for i in range(args.warmup + args.steps):
+    for i in range(args.warmup + steps):
         b = i % nreq
         flush.zero_()
         torch.cuda.synchronize()
@@ -249,8 +279,8 @@ def run_gpu(args, rank, world, local_rank):
             n_win_r = int(prof.window_routed)
             n_key_r = int(prof.auto_routed - prof.window_routed)
         else:
-            n_win_r = args.steps if args.sparse_route == "window" else 0
-            n_key_r = args.steps - n_win_r
+            n_win_r = steps if args.sparse_route == "window" else 0
+            n_key_r = steps - n_win_r
         routes = {"window_major": n_win_r, "key_major": n_key_r}
         key_bytes = emb_bytes + 4 * w.n_ads
         kern_bytes = ((n_win_r * kern_bytes + n_key_r * key_bytes) /
@@ -266,12 +296,12 @@ def run_gpu(args, rank, world, local_rank):
     if os.path.exists(tr_path):
         with open(tr_path) as f:
             tr = json.load(f)
-        if (tr.get("workload") == args.workload and tr.get("kernel_rev") == KERNEL_REV and
+        if (tr.get("workload") == workload and tr.get("kernel_rev") == KERNEL_REV and
                 not sparse):
             traffic = tr.get("bytes_per_launch")
-    launches_per_step = launches / max(args.steps, 1)
+    launches_per_step = launches / max(steps, 1)
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": w.recipe.emb_dtype,
         "data": "synthetic",
@@ -298,15 +328,13 @@ def run_gpu(args, rank, world, local_rank):
                 "h2d_bytes_per_step": int(w.recipe.d * 4 + (8 * args.sparse_query if sparse
                                                             else w.recipe.f_u * 4)),
                 "d2h_bytes_per_step": int(k * 8)},
-        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "gpu_launches": int(round(launches_per_step * steps)),
         "gpu_launches_per_step": launches_per_step,
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and cpu_requests:
+        out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget, max_req=cpu_requests)
     del ix, h_u, users, flush
-    if world == 1 and not args.no_serve and args.workload == WORKLOAD and not sparse:
-        out["serving"] = run_serving(args, device=local_rank)
     return out
 
 
@@ -317,21 +345,28 @@ ALU_ADD_PEAK_T = 152 * 128 * 2.07e9 / 1e12
 
 
 def _workload(args):
+    """The workload's arrays; a single-request run draws 16 users (one per
+    step, round robin), a batched run the batch's users."""
+    from paper_2511_22460_gb300.datagen import RECIPES
     kw = {}
     if args.n_ads:
         kw["n_ads"] = args.n_ads
-    if args.batch:
-        kw["batch"] = args.batch
-    return make_workload(args.workload, seed=args.seed, **kw)
+    batch = args.batch or RECIPES[args.workload].batch
+    kw["batch"] = batch if batch > 1 else 16
+    w = make_workload(args.workload, seed=args.seed, **kw)
+    w.bench_batch = batch
+    return w
 
 
-def run_gpu_batched(args, w, rank, world, local_rank):
+def run_gpu_batched(args, w, rank, world, local_rank, steps=None, cpu_users=None):
     """A step is one batched call: every user of the batch against the whole
     inventory (tensor-core deep term, wide term from the compressed lists,
     per-user top-K with FP32 rescoring)."""
     import torch
 
     from paper_2511_22460_gb300 import ebr
+
+    steps = steps or args.steps
 
     dev = torch.device("cuda", local_rank)
     st = torch.cuda.current_stream()
@@ -341,8 +376,8 @@ def run_gpu_batched(args, w, rank, world, local_rank):
     del pk, pa
     cross = ebr.cross_from_workload(w, device=local_rank)
     info = ix.info()
-    B = w.recipe.batch
-    ks = [int(x) for x in w.ks]
+    B = getattr(w, "bench_batch", w.recipe.batch)
+    ks = [int(x) for x in w.ks[:B]]
     kmax = max(ks)
     h_u = torch.from_numpy(w.h_u).to(dev)
     users = torch.from_numpy(w.users).to(dev)
@@ -362,13 +397,13 @@ def run_gpu_batched(args, w, rank, world, local_rank):
     ix.profile_enable(True)
     p0 = ix.profile_read()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+           for _ in range(steps)]
     clocks = ClockSampler(local_rank)
     clocks.start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    for i in range(args.steps):
+    for i in range(steps):
         flush.zero_()
         evs[i][0].record(st)
         step()
@@ -381,8 +416,8 @@ def run_gpu_batched(args, w, rank, world, local_rank):
     prof = ix.profile_read()
     ix.profile_enable(False)
     total_ms = max_over_ranks(float(sum(times)), dev)
-    ms_step = total_ms / args.steps
-    value = whole_job_rate(w.n_ads * B * args.steps, world, total_ms)
+    ms_step = total_ms / steps
+    value = whole_job_rate(w.n_ads * B * steps, world, total_ms)
     # end to end with host buffers: requests in, B x K results out
     hq = [ebr.Query(h_u=np.ascontiguousarray(w.h_u[b]), k=ks[b],
                     user_vals=np.ascontiguousarray(w.users[b]),
@@ -391,7 +426,7 @@ def run_gpu_batched(args, w, rank, world, local_rank):
     hids = np.empty((B, kmax), np.uint32)
     hsc = np.empty((B, kmax), np.float32)
     e2e_t = []
-    for i in range(args.warmup + args.steps):
+    for i in range(args.warmup + steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -404,17 +439,19 @@ def run_gpu_batched(args, w, rank, world, local_rank):
     scan_ms = prof.ms_batch_scan / calls
     adds = B * info.nnz_unique  # the wide term's FP32 adds of one batched scan
     achieved = adds / (scan_ms / 1e3) / 1e12
+    gemm_flop = 2.0 * B * w.n_ads * w.recipe.d  # the deep term on the tensor cores
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": w.recipe.emb_dtype, "data": "synthetic",
-        "config": _config(w, {"replicas": world, "units": "user x ad pairs scored"}),
+        "config": _config(w, {"replicas": world, "units": "user x ad pairs scored"}, batch=B),
         "req_per_s": B * 1e3 / ms_step * world,
         "latency_ms": {"p50": float(np.percentile(times, 50)),
                        "p99": float(np.percentile(times, 99))},
         "stage_ms": {"stage_expand": prof.ms_batch_stage / calls, "scan": scan_ms,
                      "merge_rescore": prof.ms_batch_merge / calls},
         "recomputed_users": int(prof.recomputed - p0.recomputed),
+        "tensor_tflops": gemm_flop / (scan_ms / 1e3) / 1e12,
         "roofline": {"kernel": "k_batch_window", "bound": "alu", "achieved": achieved,
                      "peak": ALU_ADD_PEAK_T, "unit": "Tadd/s", "frac": achieved / ALU_ADD_PEAK_T,
                      "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
@@ -423,12 +460,12 @@ def run_gpu_batched(args, w, rank, world, local_rank):
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(B * kmax * 8)},
         "gpu_launches": int(prof.launches - p0.launches),
-        "gpu_launches_per_step": (prof.launches - p0.launches) / max(args.steps, 1),
+        "gpu_launches_per_step": (prof.launches - p0.launches) / max(steps, 1),
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(w, budget_s=args.cpu_budget)
-        out["cpu_baseline"] = cb
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and cpu_users != 0:
+        out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget, max_req=cpu_users or 64)
+    del ix
     return out
 
 
@@ -455,9 +492,10 @@ def run_serving(args, device=0):
              np.ascontiguousarray(w.filters[b])) for b in range(pool)]
     srv = ebr.Server(ix, cross, max_batch=args.serve_batch, max_slots=4096, k_max=1000)
 
-    def drive(rate, duration):
+    def drive(rate, duration, keep=None):
         # one thread: submit every request whose arrival time has passed, then
-        # retire whatever the server reports finished (no lock, no GIL contention)
+        # retire whatever the server reports finished (no lock, no GIL contention);
+        # `keep` collects (user, K, ids) of the first results of distinct users
         arr = poisson_arrivals(rate, duration, seed=args.seed + int(rate))
         outstanding = {}
         n_done = rejected = failed = 0
@@ -481,10 +519,13 @@ def run_serving(args, device=0):
                 b = outstanding.pop(int(t))
                 busy = True
                 try:
-                    srv.poll(int(t), ks[b])
+                    res = srv.poll(int(t), ks[b])
                 except ebr.EbrError:
                     failed += 1
                     continue
+                if keep is not None and len(keep) < args.serve_check and \
+                        all(kb != b for kb, _, _ in keep):
+                    keep.append((b, ks[b], res[0].copy()))
                 n_done += 1
                 last = time.perf_counter()
             if not busy:
@@ -493,15 +534,17 @@ def run_serving(args, device=0):
         return len(arr), n_done, rejected + failed, span
 
     drive(2000.0, 0.3)  # warm-up
-    rows = []
+    rows, checks = [], []
     for rate in args.serve_rates:
         srv.reset_stats()
-        offered, n_done, rejected, span = drive(rate, args.serve_seconds)
+        keep = []
+        offered, n_done, rejected, span = drive(rate, args.serve_seconds, keep)
         st = srv.stats()
         rows.append({"offered_req_s": rate, "submitted": offered, "completed": n_done,
                      "rejected": rejected, "req_per_s": n_done / span,
                      "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
                      "mean_batch": st.batched_requests / max(st.batches, 1)})
+        checks.append(keep)
     srv_stats = srv.stats()
     srv.close()
     # the plain per-request FP32 path on the same inventory, host buffers
@@ -522,6 +565,17 @@ def run_serving(args, device=0):
     fp32_rps = n32 / (time.perf_counter() - t0)
     del ix32
     torch.cuda.synchronize()
+    # recall@K of the served results against the FP64 oracle (after the timed
+    # region; the oracle runs on every host core)
+    t_chk = time.perf_counter()
+    rec = served_recall(w, [x for keep in checks for x in keep], pk, pa)
+    i = 0
+    for row, keep in zip(rows, checks):
+        r = rec[i:i + len(keep)]
+        i += len(keep)
+        row["recall_checked"] = len(keep)
+        row["recall_min"] = float(min(r)) if r else None
+        row["recall_mean"] = float(np.mean(r)) if r else None
     best = max(rows, key=lambda r: r["req_per_s"])
     return {"workload": "serve_bf16_5m", "n_ads": w.n_ads, "d": w.recipe.d,
             "emb_dtype": "bf16 + FP32 rescoring (R=4)", "ad_fields": w.recipe.f_a,
@@ -529,30 +583,112 @@ def run_serving(args, device=0):
             "filter_fraction": "U[0.01, 1] per request", "request_pool": pool,
             "max_batch": srv_stats.max_batch, "rates": rows,
             "max_req_per_s": best["req_per_s"],
-            "recall": "1.0 after FP32 rescoring: tests/test_gpu_serve.py checks served results "
-                      "against the FP64 oracle",
+            "recall": {"checked": len(rec), "min": float(min(rec)) if rec else None,
+                       "definition": "|S_gpu & S_oracle| / K against the FP64 oracle, ids "
+                                     "within the 1e-5 condition-scale tolerance of the K-th "
+                                     "score counted as hits; the first results of distinct "
+                                     "users at each rate",
+                       "check_s": round(time.perf_counter() - t_chk, 1)},
+            "seconds_per_rate": args.serve_seconds,
             "fp32_per_request_req_per_s": fp32_rps,
             "speedup_vs_fp32_per_request": best["req_per_s"] / fp32_rps,
             "datagen_s": round(gen_s, 1)}
 
 
-def cpu_baseline(w, budget_s=15.0):
-    """FP64 oracle (expansion + postings walk + dot + full sort) on the host."""
+def served_recall(w, samples, pk, pa):
+    """recall@K of each (user, K, ids) against the FP64 oracle (Z8 tolerance
+    for ties at the K-th score), one oracle call per thread."""
+    import concurrent.futures as cf
+
+    import oracle
+    if not samples:
+        return []
+    cr = oracle.Cross.from_workload(w)
+    cr_abs = oracle.Cross(w.vocab_u, w.vocab_a, w.pairs, np.abs(w.w_table), w.w_off,
+                          hashed=cr.hashed, hash_bits=cr.hash_bits)
+    emb_abs = np.abs(w.emb)
+
+    def one(item):
+        b, k, ids = item
+        wh = oracle.expand(cr, w.users[b])
+        keys = np.nonzero(wh)[0].astype(np.uint32)
+        s = oracle.scores_postings(w.h_u[b], w.emb, w.n_keys, pk, pa, keys, wh[keys],
+                                   assume_unique=True)
+        wa = oracle.expand(cr_abs, w.users[b])
+        ka = np.nonzero(wa)[0].astype(np.uint32)
+        cond = oracle.scores_postings(np.abs(w.h_u[b]), emb_abs, w.n_keys, pk, pa, ka, wa[ka],
+                                      assume_unique=True)
+        tol = 1e-5 * np.maximum(np.abs(s), cond)
+        elig = np.ones(w.n_ads, bool)
+        if w.filters is not None:
+            elig = np.unpackbits(w.filters[b].view(np.uint8), bitorder="little")[:w.n_ads] > 0
+        r = np.where(elig, s, -np.inf)
+        take = min(k, int(elig.sum()))
+        if take == 0:
+            return 1.0
+        kth = np.partition(r, r.size - take)[r.size - take]
+        got = np.asarray(ids[:take]).astype(np.int64)
+        ok = (got >= 0) & (got < w.n_ads)
+        got = got[ok]
+        hit = int(np.sum(elig[got] & (s[got] >= kth - tol[got])))
+        return hit / take
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        return list(ex.map(one, samples))
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or 'unknown'."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_baseline(w, budget_s=15.0, max_req=64):
+    """FP64 oracle (expansion + postings walk + dot + full sort) on the host:
+    one thread, then every core (one request per thread at a time; the C
+    oracle releases the GIL)."""
+    import concurrent.futures as cf
+
     import oracle
     cross = oracle.Cross.from_workload(w)
     pk, pa = w.postings()
     k = int(w.ks[0])
-    t_total, n = 0.0, 0
-    while t_total < budget_s and n < 64:
-        b = n % w.users.shape[0]
-        t0 = time.perf_counter()
+    nu = w.users.shape[0]
+
+    def one(b):
         s = oracle.score_query(w, b, cross, (pk, pa))
         oracle.topk(s, k)
+
+    t_total, n = 0.0, 0
+    while t_total < budget_s and n < max_req:
+        t0 = time.perf_counter()
+        one(n % nu)
         t_total += time.perf_counter() - t0
         n += 1
-    return {"value": w.n_ads * n / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d full requests of the %s workload (%d ads each), single thread" % (
-                n, w.recipe.name, w.n_ads)}
+    single = w.n_ads * n / t_total
+    cores = os.cpu_count() or 1
+    n_all = min(max(cores, 2 * n), 4 * max(cores, 1))
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(one, [i % nu for i in range(n_all)]))
+    allc = w.n_ads * n_all / (time.perf_counter() - t0)
+    return {"value": allc, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_value": single, "cpu_model": cpu_model(),
+            "sample": "%d full requests of the %s workload (%d ads each) on one thread, then %d "
+                      "on %d threads" % (n, w.recipe.name, w.n_ads, n_all, cores)}
 
 
 def run_reference(args):
@@ -592,6 +728,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched BF16, FP8 single and FP8 batched lines")
+    ap.add_argument("--extra-steps", type=int, default=10,
+                    help="timed steps of each extra line")
     ap.add_argument("--n-ads", type=int, default=0, help="override the workload's inventory size")
     ap.add_argument("--batch", type=int, default=0, help="override the workload's users per step")
     ap.add_argument("--sparse-query", type=int, default=0,
@@ -601,10 +741,12 @@ def main():
                          "work (auto), Algorithm 2's key-major scatter, or the window-major "
                          "decode inside the fused scan")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[2000, 5000, 10000, 20000])
-    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-batch", type=int, default=128)
-    ap.add_argument("--serve-pool", type=int, default=64)
-    ap.add_argument("--serve-fp32-requests", type=int, default=30)
+    ap.add_argument("--serve-pool", type=int, default=256)
+    ap.add_argument("--serve-check", type=int, default=16,
+                    help="served results per rate checked against the FP64 oracle")
+    ap.add_argument("--serve-fp32-requests", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
