@@ -139,6 +139,25 @@ __device__ __forceinline__ uint64_t hist_top_threshold(const uint32_t *gh, uint3
   return 0ull;
 }
 
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint4 lds_v4(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void red_add_s32(uint32_t a, int v) {
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_f32(uint32_t a, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
 struct AccBuf {         // one window's accumulators (see pack_term)
   int cls[3][kWin];     // integer term classes 0, 1, 2
   float fp[kWin];       // FP32 remainder
@@ -148,6 +167,10 @@ struct FusedSmem {
   AccBuf acc[kAccBufs];
   uint32_t wp[kPrefetch][kGroups];  // producer's ring of window offsets
   uint32_t ctab[kTeams][kMaxChunkTab];  // per team: group << 16 | chunk within the group
+  // per team and size group of the current window: shared address of its
+  // block keys (packed terms), of its value bytes, its units, and
+  // unit shift | (value-load shift << 8)
+  uint4 gtab[kTeams][kGroups];
   SlotDesc desc[kMaxIdxSlots];
   uint32_t hist[256];
   uint32_t chist[kCandBins];  // this CTA's candidates per score bin since the last flush
@@ -393,7 +416,8 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       const SlotDesc &dsc = sm.desc[sl];
       // chunk prefix over the groups (chunks of 32 units never straddle groups)
       // and a chunk -> group table, one entry per thread, so the hot loop
-      // below needs no search
+      // below needs no search; per group the shared addresses and sizes the
+      // hot loop reads with one 16-byte load
       uint32_t cpre[kGroups + 1];
       cpre[0] = 0;
 #pragma unroll
@@ -410,8 +434,18 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
         for (int t = 0; t < kGroups; t++) cb = (t == (int)g) ? cpre[t] : cb;
         tab[i] = (g << 16) | (i - cb);
       }
+      if (tt < (uint32_t)kGroups) {
+        const uint32_t g = tt, us = unit_shift_f(g);
+        const uint32_t s_slot = smem_u32(slot);
+        // a unit's value bytes start at byte (unit << vs) of the group's values:
+        // one byte (g = 0), two (g = 1), or a 4-byte word (g >= 2)
+        const uint32_t vs = g >= 2 ? 2u : g;
+        sm.gtab[team][g] = make_uint4(s_slot + dsc.key_off[g], s_slot + dsc.val_off[g],
+                                      dsc.nblk[g] << us, us | (vs << 8));
+      }
       named_sync(2 + team, kTeamThreads);
-      int *acc = &sm.acc[b].cls[0][0];
+      const uint32_t s_tab = smem_u32(tab), s_gtab = smem_u32(&sm.gtab[team][0]);
+      const uint32_t s_acc = smem_u32(&sm.acc[b]);
       // Branch-free loads: every chunk's loads are independent of the
       // others', so the shared-memory reads and term gathers of a round
       // overlap; the additions then branch on the chunk's size group (uniform
@@ -424,21 +458,20 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
         for (int q = 0; q < kChunksInFlight; q++) {
           const uint32_t c = c0 + q * kTeamWarps;  // warp-uniform
           const bool cv = c < n_chunks;
-          const uint32_t e = tab[cv ? c : 0u];
+          const uint32_t e = lds_u32(s_tab + 4 * (cv ? c : 0u));
           const uint32_t g = e >> 16;
-          const uint32_t us = unit_shift_f(g);
+          const uint4 gt = lds_v4(s_gtab + 16 * g);
+          const uint32_t us = gt.w & 0xFFu, vs = gt.w >> 8;
           const uint32_t u = ((e & 0xFFFFu) << 5) + lane;
-          const bool v = cv && u < (dsc.nblk[g] << us);
+          const bool v = cv && u < gt.z;
           const uint32_t bk = v ? (u >> us) : 0u;
-          const uint32_t wi = v ? (u & ((1u << us) - 1u)) : 0u;
-          key[q] = *reinterpret_cast<const uint32_t *>(slot + dsc.key_off[g] + 4 * bk);
+          key[q] = lds_u32(gt.x + 4 * bk);
           // the aligned 32-bit word holding this unit's 1, 2 or 4 value bytes
-          const uint32_t off = dsc.val_off[g] + (bk << g) + 4 * wi;
-          const uint32_t w32 = *reinterpret_cast<const uint32_t *>(slot + (off & ~3u));
-          const uint32_t sh = 8 * (off & 3u);
-          word[q] = g >= 2 ? w32 : ((w32 >> sh) & (g == 1 ? 0xFFFFu : 0xFFu));
+          const uint32_t va = gt.y + ((v ? u : 0u) << vs);
+          const uint32_t w32 = lds_u32(va & ~3u);
+          word[q] = (w32 >> ((va & 3u) << 3)) & (0xFFFFFFFFu >> (32u - (8u << vs)));
           gq[q] = cv ? g : 0xFFu;
-          first[q] = wi == 0;
+          first[q] = (u & ((1u << us) - 1u)) == 0u;
           valid[q] = v;
         }
         uint32_t p[kChunksInFlight];
@@ -452,24 +485,25 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
           const bool add = p[q] != 0u && c != 3u;
           fl |= (p[q] != 0u && c == 3u) ? (1u << q) : 0u;
           const int f = (int)p[q] >> 2;
-          int *ac = acc + c * kWin;
+          const uint32_t ac = s_acc + (c << 10);  // class c's 256 words
           if (g >= 2 && g < (uint32_t)kGroups) {
 #pragma unroll
             for (int s2 = 0; s2 < 4; s2++) {
-              const uint32_t l = (word[q] >> (8 * s2)) & 255u;
-              if (add && ((s2 == 0 && first[q]) || l != 0)) atomicAdd(&ac[l], f);
+              const uint32_t l4 =
+                  s2 == 0 ? (word[q] << 2) & 0x3FCu : (word[q] >> (8 * s2 - 2)) & 0x3FCu;
+              if (add && ((s2 == 0 && first[q]) || l4 != 0u)) red_add_s32(ac + l4, f);
             }
           } else if (g == 1) {
-            if (add) atomicAdd(&ac[word[q] & 255u], f);  // slot 0 of a block is real
-            const uint32_t l = (word[q] >> 8) & 255u;
-            if (add && l != 0) atomicAdd(&ac[l], f);
+            if (add) red_add_s32(ac + ((word[q] << 2) & 0x3FCu), f);  // slot 0 is real
+            const uint32_t l4 = (word[q] >> 6) & 0x3FCu;
+            if (add && l4 != 0u) red_add_s32(ac + l4, f);
           } else if (g == 0) {
-            if (add) atomicAdd(&ac[word[q] & 255u], f);
+            if (add) red_add_s32(ac + ((word[q] << 2) & 0x3FCu), f);
           }
         }
         if (__any_sync(0xffffffffu, fl != 0u)) {
           // weights too small for every integer class: FP32 additions
-          float *af = sm.acc[b].fp;
+          const uint32_t af = s_acc + 3u * 1024u;
 #pragma unroll
           for (int q = 0; q < kChunksInFlight; q++) {
             if (!((fl >> q) & 1u)) continue;
@@ -478,7 +512,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
             const uint32_t ns = g >= 2 ? 4u : (g == 1 ? 2u : 1u);
             for (uint32_t s2 = 0; s2 < ns; s2++) {
               const uint32_t l = (word[q] >> (8 * s2)) & 255u;
-              if ((s2 == 0 && (first[q] || g < 2)) || l != 0) atomicAdd(&af[l], wv);
+              if ((s2 == 0 && (first[q] || g < 2)) || l != 0) red_add_f32(af + 4 * l, wv);
             }
           }
         }
