@@ -9,16 +9,15 @@
 // values[g] (the low bytes) in (k, h) order, and keys[g], the row pointer
 // giving each key's first block (keys[g][k] = group-g blocks with key < k).
 //
-// The radix sort, the duplicate removal and the prefix sums are CUB device
-// primitives; the grouping and storage steps are the kernels below.
-#include <cub/device/device_radix_sort.cuh>
-#include <cub/device/device_scan.cuh>
-#include <cub/device/device_select.cuh>
+// The radix sort, the duplicate removal and the prefix sums are this
+// library's own device primitives (ebr_prims.cuh); the grouping and storage
+// steps are the kernels below.
 
 #include <cstring>
 #include <vector>
 
 #include "ebr_internal.cuh"
+#include "ebr_prims.cuh"
 
 namespace ebr {
 int launch_quantize(const float *x, uint64_t n, ebr_dtype dt, void *out, cudaStream_t st);
@@ -243,8 +242,8 @@ static int build_impl(const ebr_index_desc *desc, ebr_index *ix, cudaStream_t st
     uint32_t nb = 0;
     unsigned long long gc[kGroups] = {0};
     uint32_t hflags = 0;
-    int *d_num = nullptr;
-    size_t tbytes = 0, need = 0;
+    uint32_t *d_num = nullptr;
+    size_t need = 0;
     const uint32_t *pk = desc->post_key, *pa = desc->post_ad;
     int end_bit = 32;
     EmitArgs ea;
@@ -277,32 +276,21 @@ static int build_impl(const ebr_index_desc *desc, ebr_index *ix, cudaStream_t st
     // key bits needed: 32 + ceil(log2 n_keys)
     while (end_bit < 64 && ((uint64_t)1 << (end_bit - 32)) < n_keys) end_bit++;
     {
-      cub::DoubleBuffer<uint64_t> db((uint64_t *)w0.p, (uint64_t *)w1.p);
-      BCUDA(cub::DeviceRadixSort::SortKeys(nullptr, tbytes, db, (int)nnz, 0, end_bit, st));
-      need = tbytes;
-      size_t t2 = 0;
-      BCUDA(cub::DeviceSelect::Unique(nullptr, t2, (uint64_t *)w0.p, (uint64_t *)w1.p, d_num,
-                                      (int)nnz, st));
-      need = std::max(need, t2);
-      BCUDA(cub::DeviceScan::InclusiveSum(nullptr, t2, (uint32_t *)nullptr,
-                                          (uint32_t *)nullptr, (int)nnz, st));
-      need = std::max(need, t2);
-      BCUDA(cub::DeviceRadixSort::SortPairs(nullptr, t2, (uint8_t *)nullptr, (uint8_t *)nullptr,
-                                            (uint32_t *)nullptr, (uint32_t *)nullptr, (int)nnz,
-                                            0, 4, st));
-      need = std::max(need, t2);
-      BCUDA(cub::DeviceScan::ExclusiveSum(nullptr, t2, (uint32_t *)nullptr, (uint32_t *)nullptr,
-                                          (int)(n_keys + 1), st));
-      need = std::max(need, t2);
+      // scratch of every primitive below: the sort's counts, the scans' tile
+      // sums, the unique's flags, and a word for the unique count
+      need = std::max<size_t>(prims::sort_scratch(nnz),
+                              (nnz + prims::scan_scratch(nnz) + 64) * 4);
+      need = std::max<size_t>(need, (prims::scan_scratch((uint64_t)n_keys + 1) + 64) * 4);
       BTRY(dev_alloc(tmp, need + 256));
-      d_num = (int *)((char *)tmp.p + align_up(need, 16));
-      tbytes = need;
-      BCUDA(cub::DeviceRadixSort::SortKeys(tmp.p, tbytes, db, (int)nnz, 0, end_bit, st));
-      uint64_t *sorted = db.Current();
-      uint64_t *other = db.Alternate();
-      tbytes = need;
-      BCUDA(cub::DeviceSelect::Unique(tmp.p, tbytes, sorted, other, d_num, (int)nnz, st));
-      int m_i = 0;
+      d_num = (uint32_t *)((char *)tmp.p + align_up(need, 16));
+      bool in_alt = false;
+      BTRY(prims::radix_sort<uint64_t>((uint64_t *)w0.p, (uint64_t *)w1.p, nullptr, nullptr, nnz,
+                                       end_bit, tmp.p, &in_alt, st));
+      uint64_t *sorted = in_alt ? (uint64_t *)w1.p : (uint64_t *)w0.p;
+      uint64_t *other = in_alt ? (uint64_t *)w0.p : (uint64_t *)w1.p;
+      uint32_t *uflags = (uint32_t *)tmp.p;
+      BTRY(prims::unique_sorted(sorted, other, nnz, uflags, uflags + nnz, d_num, st));
+      uint32_t m_i = 0;
       BCUDA(cudaMemcpyAsync(&m_i, d_num, 4, cudaMemcpyDeviceToHost, st));
       BCUDA(cudaMemcpyAsync(&hflags, flags.p, 4, cudaMemcpyDeviceToHost, st));
       BCUDA(cudaStreamSynchronize(st));
@@ -339,9 +327,9 @@ static int build_impl(const ebr_index_desc *desc, ebr_index *ix, cudaStream_t st
       BTRY(dev_alloc(bid, (size_t)m * 4));
       k_block_flags<<<grid_for(m), 256, 0, st>>>(x, m, (uint32_t *)bs.p);
       BCUDA(cudaGetLastError());
-      tbytes = need;
-      BCUDA(cub::DeviceScan::InclusiveSum(tmp.p, tbytes, (uint32_t *)bs.p, (uint32_t *)bid.p,
-                                          (int)m, st));
+      BTRY((prims::scan<uint32_t, prims::AddU32, true>((const uint32_t *)bs.p, (uint32_t *)bid.p, m,
+                                                       prims::AddU32(), 0u, (uint32_t *)tmp.p,
+                                                       nullptr, st)));
       BCUDA(cudaMemcpyAsync(&nb, (uint32_t *)bid.p + (m - 1), 4, cudaMemcpyDeviceToHost, st));
       BCUDA(cudaStreamSynchronize(st));
       BTRY(dev_alloc(start, ((size_t)nb + 1) * 4));
@@ -359,19 +347,24 @@ static int build_impl(const ebr_index_desc *desc, ebr_index *ix, cudaStream_t st
       BCUDA(cudaGetLastError());
       k_iota<<<grid_for(nb), 256, 0, st>>>((uint32_t *)perm.p, nb);
       BCUDA(cudaGetLastError());
-      tbytes = need;
-      BCUDA(cub::DeviceRadixSort::SortPairs(tmp.p, tbytes, (const uint8_t *)grp.p,
-                                            (uint8_t *)grp2.p, (const uint32_t *)perm.p,
-                                            (uint32_t *)perm2.p, (int)nb, 0, 4, st));
+      {
+        // blocks by size group, stably (one 8-bit pass: grp2 / perm2 hold the result)
+        bool alt = false;
+        BTRY(prims::radix_sort<uint8_t>((uint8_t *)grp.p, (uint8_t *)grp2.p, (uint32_t *)perm.p,
+                                        (uint32_t *)perm2.p, nb, 8, tmp.p, &alt, st));
+        if (!alt) {  // a single block: nothing moved
+          BCUDA(cudaMemcpyAsync(grp2.p, grp.p, nb, cudaMemcpyDeviceToDevice, st));
+          BCUDA(cudaMemcpyAsync(perm2.p, perm.p, (size_t)nb * 4, cudaMemcpyDeviceToDevice, st));
+        }
+      }
     }
     // per-key row pointers: exclusive scan of counts over n_keys + 1 entries
     BTRY(dev_alloc(ix->mem_keys, (size_t)kGroups * (n_keys + 1) * 4));
     for (int g = 0; g < kGroups; g++) {
-      tbytes = need;
-      BCUDA(cub::DeviceScan::ExclusiveSum(tmp.p, tbytes,
-                                          (uint32_t *)cnt.p + (size_t)g * (n_keys + 1),
-                                          (uint32_t *)ix->mem_keys.p + (size_t)g * (n_keys + 1),
-                                          (int)(n_keys + 1), st));
+      BTRY((prims::scan<uint32_t, prims::AddU32, false>(
+          (const uint32_t *)cnt.p + (size_t)g * (n_keys + 1),
+          (uint32_t *)ix->mem_keys.p + (size_t)g * (n_keys + 1), (uint64_t)n_keys + 1,
+          prims::AddU32(), 0u, (uint32_t *)tmp.p, nullptr, st)));
       ix->keys[g] = (uint32_t *)ix->mem_keys.p + (size_t)g * (n_keys + 1);
     }
     BCUDA(cudaMemcpyAsync(gc, gcount.p, sizeof(gc), cudaMemcpyDeviceToHost, st));
@@ -437,27 +430,26 @@ static int build_impl(const ebr_index_desc *desc, ebr_index *ix, cudaStream_t st
                                                 (const uint8_t *)grp2.p, nb, (uint64_t *)skey.p,
                                                 (uint32_t *)sval.p);
         BCUDA(cudaGetLastError());
-        size_t t3 = 0;
-        BCUDA(cub::DeviceRadixSort::SortPairs(nullptr, t3, (const uint64_t *)skey.p,
-                                              (uint64_t *)skey2.p, (const uint32_t *)sval.p,
-                                              (uint32_t *)sval2.p, (int)nb, 0, 60, st));
-        BTRY(dev_reserve(tmp, t3 + 256));
-        BCUDA(cub::DeviceRadixSort::SortPairs(tmp.p, t3, (const uint64_t *)skey.p,
-                                              (uint64_t *)skey2.p, (const uint32_t *)sval.p,
-                                              (uint32_t *)sval2.p, (int)nb, 0, 60, st));
+        BTRY(dev_reserve(tmp, std::max<size_t>(prims::sort_scratch(nb),
+                                               (prims::scan_scratch((uint64_t)n_win + 1) + 64) * 4) +
+                                  256));
+        bool alt = false;
+        BTRY(prims::radix_sort<uint64_t>((uint64_t *)skey.p, (uint64_t *)skey2.p,
+                                         (uint32_t *)sval.p, (uint32_t *)sval2.p, nb, 60, tmp.p,
+                                         &alt, st));
+        if (!alt) {  // the result ended in the first buffers
+          std::swap(skey, skey2);
+          std::swap(sval, sval2);
+        }
         k_wm_emit<<<grid_for(nb), 256, 0, st>>>((const uint64_t *)skey2.p,
                                                 (const uint32_t *)sval2.p, nb, wa);
         BCUDA(cudaGetLastError());
       }
-      size_t t4 = 0;
-      BCUDA(cub::DeviceScan::ExclusiveSum(nullptr, t4, (uint32_t *)nullptr, (uint32_t *)nullptr,
-                                          (int)(n_win + 1), st));
-      BTRY(dev_reserve(tmp, t4 + 256));
-      for (int g = 0; g < kGroups; g++) {
-        size_t t5 = t4;
-        BCUDA(cub::DeviceScan::ExclusiveSum(tmp.p, t5, (uint32_t *)wcnt.p + (size_t)g * (n_win + 1),
-                                            ix->win_ptr[g], (int)(n_win + 1), st));
-      }
+      BTRY(dev_reserve(tmp, (prims::scan_scratch((uint64_t)n_win + 1) + 64) * 4 + 256));
+      for (int g = 0; g < kGroups; g++)
+        BTRY((prims::scan<uint32_t, prims::AddU32, false>(
+            (const uint32_t *)wcnt.p + (size_t)g * (n_win + 1), ix->win_ptr[g],
+            (uint64_t)n_win + 1, prims::AddU32(), 0u, (uint32_t *)tmp.p, nullptr, st)));
       {
         WinPtrs wp;
         for (int g = 0; g < kGroups; g++) wp.p[g] = ix->win_ptr[g];
@@ -522,7 +514,7 @@ extern "C" void ebr_index_free(ebr_index *ix) {
   dev_free(ix->emb_q);
   dev_free(ix->emb_scale);
   Workspace &w = ix->ws;
-  for (DevBuf *b : {&w.wide, &w.w_dense, &w.lens, &w.scan, &w.work, &w.cub_tmp, &w.cand,
+  for (DevBuf *b : {&w.wide, &w.w_dense, &w.lens, &w.scan, &w.work, &w.scan_tmp, &w.cand,
                     &w.ctrl, &w.io_in, &w.io_out, &w.route_stats})
     dev_free(*b);
   batch_ws_free(ix->bws);

@@ -68,7 +68,7 @@ struct Workspace {
   DevBuf lens;        // uint2 [9 * n_q + 1] (units, nonempty) per (group, query entry)
   DevBuf scan;        // uint2 [9 * n_q + 1] exclusive scan of lens
   DevBuf work;        // WorkEntry [9 * n_q] compacted non-empty (group, entry)
-  DevBuf cub_tmp;     // CUB temporary storage
+  DevBuf scan_tmp;    // tile sums of the scan of lens
   DevBuf cand;        // uint64 [G * KCAP] per-CTA candidates
   DevBuf ctrl;        // Ctrl block (counters, threshold, flags), then at kCtrlBytes the
                       // fused scan's candidate-score histogram (uint32 [kHistWords])

@@ -1,7 +1,6 @@
 // Query path: expansion of user features into (k, w^), the key-major wide
 // scatter of Algorithm 2, the streaming inner product fused with the wide add
 // and a per-CTA radix-select top-K, the final merge, and FP32 rescoring.
-#include <cub/device/device_scan.cuh>
 
 #include <algorithm>
 #include <array>
@@ -11,6 +10,7 @@
 
 #include "ebr_device.cuh"
 #include "ebr_internal.cuh"
+#include "ebr_prims.cuh"
 
 namespace ebr {
 
@@ -1009,11 +1009,7 @@ int ws_prepare_one(ebr_index *ix, uint32_t n_q, uint32_t kcap) {
   EBR_TRY(dev_reserve(w.lens, entries * sizeof(LenPair)));
   EBR_TRY(dev_reserve(w.scan, entries * sizeof(LenPair)));
   EBR_TRY(dev_reserve(w.work, entries * sizeof(WorkEntry)));
-  size_t tb = 0;
-  EBR_CUDA_TRY(cub::DeviceScan::ExclusiveScan(nullptr, tb, (LenPair *)nullptr,
-                                              (LenPair *)nullptr, LenPairSum(), LenPair{0, 0, 0},
-                                              (int)entries));
-  EBR_TRY(dev_reserve(w.cub_tmp, tb + 256));
+  EBR_TRY(dev_reserve(w.scan_tmp, prims::scan_scratch(entries) * sizeof(LenPair) + 256));
   EBR_TRY(dev_reserve(w.cand, ((size_t)ix->num_sms * kMaxCtasPerSm + 1) * kcap * 8 +
                                   2 * (size_t)kcap * 8));
   EBR_TRY(dev_reserve(w.ctrl, kCtrlBytes + kHistWords * 4));
@@ -1061,10 +1057,9 @@ static int run_wide(ebr_index *ix, const uint32_t *q_key, const float *q_w, uint
   k_wide_lens<<<launch_grid(entries, 256, 65535), 256, 0, st>>>(
       iv, q_key, q_w, n_q, (LenPair *)w.lens.p, &ctrl->flags);
   EBR_CUDA_TRY(cudaGetLastError());
-  size_t tb = w.cub_tmp.bytes;
-  EBR_CUDA_TRY(cub::DeviceScan::ExclusiveScan(w.cub_tmp.p, tb, (const LenPair *)w.lens.p,
-                                              (LenPair *)w.scan.p, LenPairSum(),
-                                              LenPair{0, 0, 0}, (int)entries, st));
+  EBR_TRY((prims::scan<LenPair, LenPairSum, false>((const LenPair *)w.lens.p, (LenPair *)w.scan.p,
+                                                   entries, LenPairSum(), LenPair{0, 0, 0},
+                                                   (LenPair *)w.scan_tmp.p, nullptr, st)));
   k_wide_compact<<<launch_grid(entries, 256, 65535), 256, 0, st>>>(
       iv, q_key, q_w, n_q, (const LenPair *)w.lens.p, (const LenPair *)w.scan.p,
       (WorkEntry *)w.work.p, ctrl, w_dense ? index_units(ix) : 0ull,
