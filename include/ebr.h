@@ -197,9 +197,10 @@ int ebr_expand_query_seq(const ebr_cross *c, const uint32_t *user_ptr, const uin
  *     cross pair is one hit feature with x = 1 (HitMatch equation, Sec. 3.3),
  *     so w^[key_off[j] + v] = sum over pairs (i, j) and values u of field i
  *     of w_ij(u, v).  user_ptr must start at 0, not decrease and end at
- *     n_user_vals; a violation or a value outside its vocabulary is a
- *     device-side input error (EBR_EDATA).  Such requests take the
- *     single-request scan, also inside a batch;
+ *     n_user_vals; a violation or a value outside its vocabulary is an
+ *     input error (EBR_EDATA; the offsets of host requests in a batch are
+ *     checked on the host, the rest on the device).  A batch may mix such
+ *     requests with single-valued ones;
  *   - a dense weight vector: q_key == NULL, q_w[n_keys] indexed by key;
  *   - a sparse list: q_key[n_q], q_w[n_q] (duplicates add, keys must be < n_keys).
  * filter: targeting bitmap, bit a of word a >> 6 keeps ad a (NULL keeps all).
@@ -355,7 +356,7 @@ int ebr_scan_topk_noalloc(const float *emb, uint32_t n_ads, uint32_t d, const fl
 typedef struct {
   uint64_t calls;          /* requests profiled */
   uint64_t launches;       /* kernels of this library launched by those requests */
-  uint64_t lib_launches;   /* device-library (CUB scan) kernels launched */
+  uint64_t lib_launches;   /* device-library kernels launched: always 0 (none are used) */
   double ms_expand, ms_wide, ms_scan, ms_final;
   uint64_t batched;        /* requests served by the batched tensor-core scan */
   uint64_t recomputed;     /* of those, recomputed by the single-request scan because the
@@ -396,6 +397,8 @@ typedef struct {
   uint32_t max_slots;         /* admitted requests at once, queued + running (0: 4 * max_batch) */
   uint32_t k_max;             /* largest K a request may ask for (0: 1000) */
   uint32_t queue_timeout_ms;  /* a request still queued after this long fails with EBR_ETIMEDOUT (0: never) */
+  uint32_t max_user_vals;     /* user field values one request may carry, multi-valued (user_ptr)
+                                 requests included; sizes every slot (0: 8 * f_u) */
 } ebr_server_cfg;
 
 typedef struct {
@@ -418,6 +421,9 @@ int ebr_server_create(ebr_index *ix, const ebr_cross *cross, const ebr_server_cf
 /*
  * q: HOST pointers (h_u[d], user_vals[f_u], optional filter bitmap of
  * ceil(N/64) words); q->k in 1..k_max; q_key/q_w are not accepted here.
+ * A multi-valued request (user_ptr[f_u + 1], user_vals[n_user_vals], as in
+ * ebr_query) may carry up to the server's max_user_vals values; its offsets
+ * and values are checked here (EBR_EINVAL), like the single-valued fields.
  * The request is copied before the call returns.  *ticket identifies it.
  */
 int ebr_submit(ebr_server *s, const ebr_query *q, uint64_t *ticket);

@@ -414,6 +414,99 @@ __device__ uint32_t warp_compact(CandEntry *buf, uint32_t n, uint64_t T) {
   return kept;
 }
 
+// The same selection and compaction on a buffer of at most 32 * NPL entries,
+// read once into registers: the eight digit passes then touch only the
+// shared-memory histogram, and the survivors are written back in one sweep.
+// Returns how many were kept; *T_out = the selected cut.
+constexpr int kSelNpl = 18;  // entries per lane of the register form (576 per buffer)
+template <int NPL>
+__device__ uint32_t warp_trim_regs(CandEntry *buf, uint32_t n, uint32_t need, uint32_t *hist,
+                                   uint64_t *T_out) {
+  const int lane = threadIdx.x & 31;
+  uint64_t x[NPL];
+  float wd[NPL];
+#pragma unroll
+  for (int e = 0; e < NPL; e++) {
+    const uint32_t i = lane + 32u * e;
+    x[e] = 0ull;
+    wd[e] = 0.f;
+    if (i < n) {
+      const CandEntry c = buf[i];
+      x[e] = c.key;
+      wd[e] = c.wide;
+    }
+  }
+  uint64_t prefix = 0;
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int i = lane; i < 256; i += 32) hist[i] = 0;
+    __syncwarp();
+    const uint64_t hi_mask = (shift == 56) ? 0ull : (~0ull << (shift + 8));
+#pragma unroll
+    for (int e = 0; e < NPL; e++)
+      if (lane + 32u * e < n && (x[e] & hi_mask) == prefix)
+        atomicAdd(&hist[(x[e] >> shift) & 255u], 1u);
+    __syncwarp();
+    uint32_t c[8], tot = 0;
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+      c[e] = hist[255 - 8 * lane - e];
+      tot += c[e];
+    }
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    uint32_t acc = incl - tot, dg = 0, nn = 0, whole = 0;
+    bool found = false;
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+      if (!found && acc < need && need <= acc + c[e]) {
+        found = true;
+        dg = 255 - 8 * lane - e;
+        nn = need - acc;
+        whole = (need - acc == c[e]) ? 1u : 0u;
+      }
+      acc += c[e];
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, found);
+    const int src = __ffs(bal) - 1;
+    dg = __shfl_sync(0xffffffffu, dg, src);
+    need = __shfl_sync(0xffffffffu, nn, src);
+    whole = __shfl_sync(0xffffffffu, whole, src);
+    prefix |= (uint64_t)dg << shift;
+    __syncwarp();
+    if (whole) break;
+  }
+  uint32_t kept = 0;
+#pragma unroll
+  for (int e = 0; e < NPL; e++) {
+    const bool kp = lane + 32u * e < n && x[e] >= prefix;
+    const uint32_t bal = __ballot_sync(0xffffffffu, kp);
+    if (kp) {
+      CandEntry c;
+      c.key = x[e];
+      c.wide = wd[e];
+      c.pad = 0;
+      buf[kept + __popc(bal & ((1u << lane) - 1u))] = c;
+    }
+    kept += __popc(bal);
+  }
+  __syncwarp();
+  *T_out = prefix;
+  return kept;
+}
+
+// Exact top-`need` of a per-user buffer, in place; returns how many were kept.
+__device__ __forceinline__ uint32_t warp_trim(CandEntry *buf, uint32_t n, uint32_t need,
+                                              uint32_t *hist, uint64_t *T_out) {
+  if (n <= 32u * kSelNpl) return warp_trim_regs<kSelNpl>(buf, n, need, hist, T_out);
+  const uint64_t T = warp_radix_select(buf, n, need, hist);
+  *T_out = T;
+  return warp_compact(buf, n, T);
+}
+
 template <bool F8>
 __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_constant__ BatchArgs a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -735,8 +828,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
         if (n + kBWin <= a.cap_u) continue;
         CandEntry *buf = a.cand + ((uint64_t)blockIdx.x * a.B + b) * a.cap_u;
         const uint32_t nn = min(n, a.cap_u);
-        const uint64_t T = warp_radix_select(buf, nn, a.m, hist);
-        const uint32_t kept = warp_compact(buf, nn, T);
+        uint64_t T;
+        const uint32_t kept = warp_trim(buf, nn, a.m, hist, &T);
         if (lane == 0) {
           sm.cnt_u[b] = kept;
           sm.thr_u[b] = T;
@@ -752,8 +845,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
         const uint32_t n = min(sm.cnt_u[b], a.cap_u);
         if (n <= a.m) continue;
         CandEntry *buf = a.cand + ((uint64_t)blockIdx.x * a.B + b) * a.cap_u;
-        const uint64_t T = warp_radix_select(buf, n, a.m, hist);
-        const uint32_t kept = warp_compact(buf, n, T);
+        uint64_t T;
+        const uint32_t kept = warp_trim(buf, n, a.m, hist, &T);
         if (lane == 0) {
           sm.cnt_u[b] = kept;
           sm.thr_u[b] = T > sm.thr_u[b] ? T : sm.thr_u[b];
@@ -932,6 +1025,79 @@ __global__ void __launch_bounds__(kMergeThreads) k_batch_merge(
 // =====================================================================
 namespace ebr {
 
+// Pointers of one request's inputs (device memory), gathered by
+// k_stage_requests into the batch's contiguous arrays.
+struct ReqSrc {
+  const float *h_u;
+  const uint32_t *vals;    // [n] user field values
+  const uint64_t *filter;  // null: no filter
+  const uint32_t *ptr;     // [f_u + 1] field offsets into vals; null: one value per field
+  uint32_t n, base;        // values, and their first position in the batch's value array
+};
+constexpr uint32_t kStageWords = 8192;  // filter words per block of the gather
+
+// Block (b, y): request b's user vector, field values and field offsets
+// (y == 0) and words [y * kStageWords, +kStageWords) of its filter.  With
+// uptr set, the offsets are written (relative to the request's base, base[b]
+// beside them) after a check that they start at 0, do not decrease and end
+// at n; offsets that fail it are flagged and every field is left empty.
+__global__ void __launch_bounds__(256) k_stage_requests(const ReqSrc *__restrict__ src,
+                                                        uint32_t d, uint32_t fu, uint32_t words,
+                                                        float *__restrict__ users,
+                                                        uint32_t *__restrict__ vals,
+                                                        uint32_t *__restrict__ uptr,
+                                                        uint32_t *__restrict__ base,
+                                                        uint64_t *__restrict__ filters,
+                                                        uint32_t *__restrict__ flags) {
+  __shared__ uint32_t s_ok;
+  const uint32_t b = blockIdx.x;
+  const ReqSrc r = src[b];
+  if (blockIdx.y == 0) {
+    for (uint32_t t = threadIdx.x; t < d; t += blockDim.x) users[(size_t)b * d + t] = r.h_u[t];
+    for (uint32_t t = threadIdx.x; t < r.n; t += blockDim.x) vals[(size_t)r.base + t] = r.vals[t];
+    if (uptr) {
+      if (threadIdx.x == 0) {
+        uint32_t ok = 1;
+        if (r.ptr) {
+          uint32_t prev = 0;
+          for (uint32_t i = 0; i <= fu; i++) {
+            const uint32_t x = r.ptr[i];
+            if ((i == 0 && x != 0) || x < prev || (i == fu && x != r.n)) ok = 0;
+            prev = x;
+          }
+        }
+        if (!ok) atomicOr(flags, DEVERR_BAD_USER);
+        s_ok = ok;
+        base[b] = r.base;
+      }
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i <= fu; i += blockDim.x)
+        uptr[(size_t)b * (fu + 1) + i] = !s_ok ? 0u : (r.ptr ? r.ptr[i] : i);
+    }
+  }
+  if (r.filter) {
+    const uint32_t w0 = blockIdx.y * kStageWords;
+    const uint32_t w1 = min(words, w0 + kStageWords);
+    for (uint32_t t = w0 + threadIdx.x; t < w1; t += blockDim.x)
+      filters[(size_t)b * words + t] = r.filter[t];
+  }
+}
+
+// Layout of the batch's user field values: request b's n[b] values start at
+// base[b] (one value per field without user_ptr); returns the total.
+static uint64_t user_vals_layout(const ebr_query *q, uint32_t B, uint32_t fu,
+                                 std::vector<uint32_t> *n, std::vector<uint32_t> *base) {
+  uint64_t t = 0;
+  n->resize(B);
+  base->resize(B);
+  for (uint32_t b = 0; b < B; b++) {
+    (*n)[b] = q[b].user_ptr ? q[b].n_user_vals : fu;
+    (*base)[b] = (uint32_t)t;
+    t += (*n)[b];
+  }
+  return t;
+}
+
 struct BatchPlan {
   uint32_t Bq, m, cap_u, sa, lb, tb, list_cap, tile_row, kb_n;
   size_t smem;
@@ -974,21 +1140,24 @@ static bool plan_smem(const ebr_index *ix, uint32_t B, BatchPlan *p) {
   return false;
 }
 
+bool batch_index_ok(const ebr_index *ix, const ebr_cross *cross, uint32_t batch) {
+  BatchPlan p;
+  return (ix->dtype == EBR_BF16 || ix->dtype == EBR_FP8E4M3) && (ix->d == 64 || ix->d == 128) &&
+         batch >= 2 && batch <= (uint32_t)kMaxUsers && cross && cross->n_keys == ix->n_keys &&
+         ix->n_win > 0 && ix->ad_nkeys.p && ix->max_keys_per_ad > 0 &&
+         ix->max_keys_per_ad <= kMaxBatchKeysPerAd &&
+         (uint64_t)(ix->n_keys + 1) * users_pow2(batch) < (1ull << 32) &&
+         plan_smem(ix, batch, &p);
+}
+
 bool batch_qualifies(const ebr_index *ix, const ebr_cross *cross, const ebr_query *q,
                      uint32_t batch) {
-  if ((ix->dtype != EBR_BF16 && ix->dtype != EBR_FP8E4M3) || (ix->d != 64 && ix->d != 128) ||
-      batch < 2 ||
-      batch > (uint32_t)kMaxUsers || !cross || cross->n_keys != ix->n_keys ||
-      ix->n_win == 0 || !ix->ad_nkeys.p || ix->max_keys_per_ad == 0 ||
-      ix->max_keys_per_ad > kMaxBatchKeysPerAd ||
-      (uint64_t)(ix->n_keys + 1) * users_pow2(batch) >= (1ull << 32))
-    return false;
+  if (!batch_index_ok(ix, cross, batch)) return false;
   for (uint32_t b = 0; b < batch; b++) {
-    if (!q[b].user_vals || q[b].user_ptr || (q[b].flags & EBR_QF_KEY_MAJOR)) return false;
+    if (!q[b].user_vals || (q[b].flags & EBR_QF_KEY_MAJOR)) return false;
     if ((uint64_t)q[b].k * ix->rescore_mult > 8192) return false;
   }
-  BatchPlan p;
-  return plan_smem(ix, batch, &p);
+  return true;
 }
 
 static bool plan_batch(const ebr_index *ix, uint32_t B, uint32_t kscan_max, int grid,
@@ -998,6 +1167,94 @@ static bool plan_batch(const ebr_index *ix, uint32_t B, uint32_t kscan_max, int 
   p->m = std::max<uint32_t>(64, (2 * per_cta + 32 + 31) / 32 * 32);
   p->cap_u = 2 * p->m + kBWin;
   return (uint64_t)grid * p->m <= kMergeCap;
+}
+
+// Device bytes of every buffer of one batched call (B users, scan depth up to
+// kscan_max), in one place for the reservation below and the serving loop's
+// memory budget.  The pinned host mirror holds [kscan B][kout B][has_filter B]
+// [status B] words, then the request pointer table.
+struct BatchSizes {
+  BatchPlan pl;
+  int grid;
+  size_t users_f32, users_q, users_scale, user_vals, user_ptr, wT, filters, small, cand, cand_n,
+      cand_thr, scratch, ctrl, req, host;
+  size_t total() const {
+    size_t t = 0;
+    for (size_t b : {users_f32, users_q, users_scale, user_vals, user_ptr, wT, filters, small,
+                     cand, cand_n, cand_thr, scratch, ctrl, req})
+      t += (b + 255) / 256 * 256;
+    return t;
+  }
+};
+
+static size_t host_table_off(uint32_t B) { return ((size_t)4 * B * 4 + 15) / 16 * 16; }
+
+static bool batch_sizes(const ebr_index *ix, const ebr_cross *cross, uint32_t B,
+                        uint32_t kscan_max, uint64_t n_vals, BatchSizes *z) {
+  if (n_vals == 0) n_vals = (uint64_t)B * cross->f_u;
+  z->grid = std::max(1, std::min<int>(ix->num_sms, (int)ix->n_win));
+  if (!plan_batch(ix, B, kscan_max, z->grid, &z->pl)) return false;
+  const size_t Bp = z->pl.Bq, d = ix->d, words = (ix->n_ads + 63) / 64;
+  z->users_f32 = Bp * d * 4;
+  z->users_q = Bp * d * 2;  // BF16 or FP8 users
+  z->users_scale = Bp * 4;
+  z->user_vals = (size_t)n_vals * 4;
+  z->user_ptr = (size_t)B * (cross->f_u + 2) * 4;  // offsets [B][f_u + 1], then base [B]
+  z->wT = ((size_t)ix->n_keys + 1) * Bp * 4;
+  z->filters = (size_t)B * words * 8;
+  z->small = small_bytes(B);
+  z->cand = (size_t)z->grid * B * z->pl.cap_u * sizeof(CandEntry);
+  z->cand_n = (size_t)z->grid * B * 4;
+  z->cand_thr = (size_t)z->grid * B * 8;
+  z->scratch = (size_t)B * (kMergeCap + 8192) * 8;
+  z->ctrl = sizeof(Ctrl);
+  z->req = (size_t)B * sizeof(ReqSrc);
+  // after the words: the pointer table (device requests) or the packed user
+  // vectors and field values (host requests)
+  z->host = host_table_off(B) + std::max(z->req, (size_t)B * d * 4 + z->user_ptr + z->user_vals);
+  return true;
+}
+
+size_t batch_ws_bytes(const ebr_index *ix, const ebr_cross *cross, uint32_t B,
+                      uint32_t kscan_max, uint64_t n_vals) {
+  BatchSizes z;
+  return batch_sizes(ix, cross, B, kscan_max, n_vals, &z) ? z.total() : 0;
+}
+
+int batch_ws_reserve(const ebr_index *ix, const ebr_cross *cross, uint32_t B,
+                     uint32_t kscan_max, uint64_t n_vals, BatchWs &w) {
+  BatchSizes z;
+  if (!batch_sizes(ix, cross, B, kscan_max, n_vals, &z)) {
+    set_error("batched scan: per-window key tables (%u keys per ad) do not fit shared memory",
+              ix->max_keys_per_ad);
+    return EBR_EINVAL;
+  }
+  EBR_TRY(dev_reserve(w.users_f32, z.users_f32));
+  EBR_TRY(dev_reserve(w.users_bf16, z.users_q));
+  EBR_TRY(dev_reserve(w.users_scale, z.users_scale));
+  EBR_TRY(dev_reserve(w.user_vals, z.user_vals));
+  EBR_TRY(dev_reserve(w.user_ptr, z.user_ptr));
+  EBR_TRY(dev_reserve(w.wT, z.wT));
+  EBR_TRY(dev_reserve(w.filters, z.filters));
+  EBR_TRY(dev_reserve(w.small, z.small));
+  EBR_TRY(dev_reserve(w.cand, z.cand));
+  EBR_TRY(dev_reserve(w.cand_n, z.cand_n));
+  EBR_TRY(dev_reserve(w.cand_thr, z.cand_thr));
+  EBR_TRY(dev_reserve(w.scratch, z.scratch));
+  EBR_TRY(dev_reserve(w.ctrl, z.ctrl));
+  EBR_TRY(dev_reserve(w.req, z.req));
+  if (w.host_bytes < z.host) {
+    if (w.host) cudaFreeHost(w.host);
+    w.host = nullptr;
+    w.host_bytes = 0;
+    if (cudaMallocHost(&w.host, z.host) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("batched scan: pinned host allocation of %zu bytes failed", z.host);
+      return EBR_ENOMEM;
+    }
+    w.host_bytes = z.host;
+  }
+  return EBR_OK;
 }
 
 static int stage(void *dst, const void *src, size_t bytes, int io, cudaStream_t st) {
@@ -1018,6 +1275,26 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   uint32_t kscan_max = 1;
   for (uint32_t b = 0; b < B; b++)
     kscan_max = std::max(kscan_max, std::min<uint32_t>(q[b].k * ix->rescore_mult, ix->n_ads));
+  std::vector<uint32_t> nv, vbase;
+  const uint64_t n_vals = user_vals_layout(q, B, fu, &nv, &vbase);
+  bool multi = false;
+  for (uint32_t b = 0; b < B; b++) multi |= q[b].user_ptr != nullptr;
+  if (io == EBR_IO_HOST)  // offsets of host requests are checked here, before anything is queued
+    for (uint32_t b = 0; b < B; b++) {
+      const uint32_t *p = q[b].user_ptr;
+      if (!p) continue;
+      for (uint32_t i = 0; i <= fu; i++)
+        if ((i == 0 && p[0] != 0) || (i > 0 && p[i] < p[i - 1]) || (i == fu && p[i] != nv[b])) {
+          set_error("ebr_score_topk: request %u: user_ptr must start at 0, not decrease and end "
+                    "at n_user_vals",
+                    b);
+          return EBR_EDATA;
+        }
+    }
+  if (n_vals >= (1ull << 32)) {
+    set_error("batched scan: %llu user values in one batch", (unsigned long long)n_vals);
+    return EBR_EINVAL;
+  }
   // profiling events (ebr_profile_enable): before staging, before the scan,
   // after the scan, after the merge
   std::array<cudaEvent_t, 5> ev{};
@@ -1031,39 +1308,14 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
     }
     EBR_CUDA_TRY(cudaEventRecord(ev[0], st));
   }
-  const int grid = std::max(1, std::min<int>(ix->num_sms, (int)ix->n_win));
-  BatchPlan pl;
-  if (!plan_batch(ix, B, kscan_max, grid, &pl)) {
-    set_error("batched scan: per-window key tables (%u keys per ad) do not fit shared memory",
-              ix->max_keys_per_ad);
-    return EBR_EINVAL;
-  }
+  EBR_TRY(batch_ws_reserve(ix, cross, B, kscan_max, n_vals, w));
+  BatchSizes z;
+  batch_sizes(ix, cross, B, kscan_max, n_vals, &z);
+  const int grid = z.grid;
+  const BatchPlan pl = z.pl;
   const uint32_t Bp = pl.Bq;
-  EBR_TRY(dev_reserve(w.users_f32, (size_t)Bp * d * 4));
-  EBR_TRY(dev_reserve(w.users_bf16, (size_t)Bp * d * 2));  // BF16 or FP8 users
-  EBR_TRY(dev_reserve(w.users_scale, (size_t)Bp * 4));
-  EBR_TRY(dev_reserve(w.user_vals, (size_t)B * fu * 4));
-  EBR_TRY(dev_reserve(w.wT, ((size_t)ix->n_keys + 1) * Bp * 4));
-  EBR_TRY(dev_reserve(w.filters, (size_t)B * words * 8));
-  EBR_TRY(dev_reserve(w.small, small_bytes(B)));
-  EBR_TRY(dev_reserve(w.cand, (size_t)grid * B * pl.cap_u * sizeof(CandEntry)));
-  EBR_TRY(dev_reserve(w.cand_n, (size_t)grid * B * 4));
-  EBR_TRY(dev_reserve(w.cand_thr, (size_t)grid * B * 8));
-  EBR_TRY(dev_reserve(w.scratch, (size_t)B * (kMergeCap + 8192) * 8));
-  EBR_TRY(dev_reserve(w.ctrl, sizeof(Ctrl)));
-  const size_t host_need = (size_t)4 * B * 4;
-  if (w.host_bytes < host_need) {
-    if (w.host) cudaFreeHost(w.host);
-    w.host = nullptr;
-    w.host_bytes = 0;
-    if (cudaMallocHost(&w.host, host_need) != cudaSuccess) {
-      cudaGetLastError();
-      set_error("batched scan: pinned host allocation of %zu bytes failed", host_need);
-      return EBR_ENOMEM;
-    }
-    w.host_bytes = host_need;
-  }
-  // pinned host mirror: [kscan B][kout B][has_filter B] in, then [status B] out
+  // pinned host mirror: [kscan B][kout B][has_filter B] in, then [status B]
+  // out, then the request table
   uint32_t *h_in = reinterpret_cast<uint32_t *>(w.host);
   for (uint32_t b = 0; b < B; b++) {
     h_in[b] = std::min<uint32_t>(q[b].k * ix->rescore_mult, ix->n_ads);
@@ -1077,13 +1329,49 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   EBR_CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
   EBR_CUDA_TRY(cudaMemcpyAsync(kk, h_in, (size_t)3 * B * 4, cudaMemcpyHostToDevice, st));
   EBR_CUDA_TRY(cudaMemsetAsync(status, 0, B * 4, st));
-  // request inputs
-  EBR_CUDA_TRY(cudaMemsetAsync(w.users_f32.p, 0, (size_t)Bp * d * 4, st));
-  for (uint32_t b = 0; b < B; b++) {
-    EBR_TRY(stage((float *)w.users_f32.p + (size_t)b * d, q[b].h_u, d * 4, io, st));
-    EBR_TRY(stage((uint32_t *)w.user_vals.p + (size_t)b * fu, q[b].user_vals, fu * 4, io, st));
-    if (q[b].filter)
-      EBR_TRY(stage((uint64_t *)w.filters.p + (size_t)b * words, q[b].filter, words * 8, io, st));
+  // request inputs: device-resident requests are gathered by one kernel
+  // through a table of their pointers; host requests are packed into the
+  // pinned mirror and copied in two transfers (filters one per request)
+  if (Bp > B)
+    EBR_CUDA_TRY(cudaMemsetAsync((float *)w.users_f32.p + (size_t)B * d, 0,
+                                 (size_t)(Bp - B) * d * 4, st));
+  bool any_filter = false;
+  for (uint32_t b = 0; b < B; b++) any_filter |= q[b].filter != nullptr;
+  uint32_t *d_uptr = multi ? (uint32_t *)w.user_ptr.p : nullptr;
+  uint32_t *d_base = multi ? d_uptr + (size_t)B * (fu + 1) : nullptr;
+  if (io == EBR_IO_HOST) {
+    // [user vectors B x d][offsets B x (f_u + 1)][base B][values], checked here
+    float *hu = reinterpret_cast<float *>((char *)w.host + host_table_off(B));
+    uint32_t *hp = reinterpret_cast<uint32_t *>(hu + (size_t)B * d);
+    uint32_t *hv = hp + (size_t)B * (fu + 2);
+    for (uint32_t b = 0; b < B; b++) {
+      memcpy(hu + (size_t)b * d, q[b].h_u, (size_t)d * 4);
+      memcpy(hv + vbase[b], q[b].user_vals, (size_t)nv[b] * 4);
+      if (!multi) continue;
+      uint32_t *up = hp + (size_t)b * (fu + 1);
+      for (uint32_t i = 0; i <= fu; i++) up[i] = q[b].user_ptr ? q[b].user_ptr[i] : i;
+      hp[(size_t)B * (fu + 1) + b] = vbase[b];
+    }
+    EBR_CUDA_TRY(cudaMemcpyAsync(w.users_f32.p, hu, (size_t)B * d * 4, cudaMemcpyHostToDevice, st));
+    if (multi)
+      EBR_CUDA_TRY(cudaMemcpyAsync(d_uptr, hp, (size_t)B * (fu + 2) * 4, cudaMemcpyHostToDevice, st));
+    EBR_CUDA_TRY(cudaMemcpyAsync(w.user_vals.p, hv, n_vals * 4, cudaMemcpyHostToDevice, st));
+    for (uint32_t b = 0; b < B; b++)
+      if (q[b].filter)
+        EBR_TRY(stage((uint64_t *)w.filters.p + (size_t)b * words, q[b].filter, words * 8, io, st));
+  } else {
+    ReqSrc *tab = reinterpret_cast<ReqSrc *>((char *)w.host + host_table_off(B));
+    for (uint32_t b = 0; b < B; b++)
+      tab[b] = ReqSrc{q[b].h_u, q[b].user_vals, q[b].filter, q[b].user_ptr, nv[b], vbase[b]};
+    EBR_CUDA_TRY(cudaMemcpyAsync(w.req.p, tab, (size_t)B * sizeof(ReqSrc), cudaMemcpyHostToDevice,
+                                 st));
+    const uint32_t ys = any_filter ? (words + kStageWords - 1) / kStageWords : 1u;
+    k_stage_requests<<<dim3(B, ys), 256, 0, st>>>((const ReqSrc *)w.req.p, d, fu, words,
+                                                  (float *)w.users_f32.p,
+                                                  (uint32_t *)w.user_vals.p, d_uptr, d_base,
+                                                  (uint64_t *)w.filters.p, &ctrl->flags);
+    EBR_CUDA_TRY(cudaGetLastError());
+    ix->launches += 1;
   }
   const bool f8 = ix->dtype == EBR_FP8E4M3;
   if (f8)  // users as FP8 with a scale per user (kind::f8f6f4 takes both operands in FP8)
@@ -1092,8 +1380,8 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   else
     EBR_TRY(launch_quantize((const float *)w.users_f32.p, (uint64_t)Bp * d, EBR_BF16,
                             w.users_bf16.p, st));
-  EBR_TRY(expand_transposed(cross, (const uint32_t *)w.user_vals.p, B, Bp, (float *)w.wT.p,
-                            &ctrl->flags, st));
+  EBR_TRY(expand_transposed(cross, (const uint32_t *)w.user_vals.p, d_uptr, d_base, B, Bp,
+                            (float *)w.wT.p, &ctrl->flags, st));
   EBR_CUDA_TRY(cudaMemsetAsync((float *)w.wT.p + (size_t)ix->n_keys * Bp, 0, (size_t)Bp * 4, st));
   // tensor maps
   const uint32_t eb = f8 ? 1u : 2u;
@@ -1175,11 +1463,16 @@ int batch_finish(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   EBR_CUDA_TRY(cudaStreamSynchronize(st));
   EBR_TRY(check_device_flags(hc.flags, "ebr_score_topk (batched)"));
   const uint32_t *h_status = reinterpret_cast<const uint32_t *>(w.host) + 3 * B;
+  std::vector<uint32_t> nv, vbase;
+  user_vals_layout(q, B, fu, &nv, &vbase);
   for (uint32_t b = 0; b < B; b++) {
     if (!h_status[b]) continue;
     ebr_query dq = q[b];
     dq.h_u = (const float *)w.users_f32.p + (size_t)b * d;
-    dq.user_vals = (const uint32_t *)w.user_vals.p + (size_t)b * fu;
+    dq.user_vals = (const uint32_t *)w.user_vals.p + vbase[b];
+    // the checked offsets staged for the batch (device memory)
+    dq.user_ptr = q[b].user_ptr ? (const uint32_t *)w.user_ptr.p + (size_t)b * (fu + 1) : nullptr;
+    dq.n_user_vals = nv[b];
     dq.filter = q[b].filter ? (const uint64_t *)w.filters.p + (size_t)b * words : nullptr;
     EBR_TRY(ws_prepare_one(ix, ix->n_keys, 8192));
     EBR_TRY(query_one(ix, cross, dq, d_ids + (size_t)b * kmax, d_scores + (size_t)b * kmax, kmax,
@@ -1193,8 +1486,9 @@ int batch_finish(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
 }
 
 void batch_ws_free(BatchWs &w) {
-  for (DevBuf *b : {&w.users_f32, &w.users_bf16, &w.users_scale, &w.user_vals, &w.wT, &w.filters, &w.small,
-                    &w.cand, &w.cand_n, &w.cand_thr, &w.scratch, &w.res, &w.ctrl})
+  for (DevBuf *b : {&w.users_f32, &w.users_bf16, &w.users_scale, &w.user_vals, &w.user_ptr, &w.wT,
+                    &w.filters, &w.small, &w.cand, &w.cand_n, &w.cand_thr, &w.scratch, &w.res,
+                    &w.ctrl, &w.req})
     dev_free(*b);
   if (w.host) cudaFreeHost(w.host);
   w.host = nullptr;

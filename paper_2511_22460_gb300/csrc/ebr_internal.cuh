@@ -92,10 +92,12 @@ struct Ctrl {
 // Scratch of the batched (tensor-core) path.
 struct BatchWs {
   DevBuf users_f32, users_bf16, users_scale, user_vals, wT, filters;  // users_bf16: BF16 or FP8
+  DevBuf user_ptr;  // multi-valued users: field offsets [B][f_u + 1], then base [B]
   DevBuf small;  // uint32 [kscan B][kout B][has_filter B], then status [B]
   DevBuf cand, cand_n, cand_thr, scratch;
   DevBuf res;    // device staging of host-bound results
   DevBuf ctrl;   // Ctrl of this batch
+  DevBuf req;    // pointer table of device-resident requests (staging gather)
   void *host = nullptr;  // pinned mirror of `small`
   size_t host_bytes = 0;
   bool tmap_ready = false;
@@ -207,14 +209,27 @@ int launch_quantize(const float *x, uint64_t n, ebr_dtype dt, void *out, cudaStr
 int launch_quantize_rows_fp8(const float *x, uint64_t n, uint32_t d, uint8_t *q, float *scale,
                              cudaStream_t st);
 // Query expansion for a batch straight into user-minor layout wT[key][Bp].
-int expand_transposed(const ebr_cross *c, const uint32_t *users, uint32_t batch, uint32_t Bp,
-                      float *wT, uint32_t *flags, cudaStream_t st);
+// uptr/base null: users[b * f_u + i]; else user b's field i holds
+// users[base[b] + uptr[b][i] .. base[b] + uptr[b][i + 1]) (checked offsets).
+int expand_transposed(const ebr_cross *c, const uint32_t *users, const uint32_t *uptr,
+                      const uint32_t *base, uint32_t batch, uint32_t Bp, float *wT,
+                      uint32_t *flags, cudaStream_t st);
 // Batched tensor-core path; returns EBR_EINVAL (nothing launched) when the
 // batch does not qualify, so the caller can fall back to per-request scans.
 bool batch_qualifies(const ebr_index *ix, const ebr_cross *cross, const ebr_query *q,
                      uint32_t batch);
+// The index-level part of that test (dtype, dimension, key lists, sizes).
+bool batch_index_ok(const ebr_index *ix, const ebr_cross *cross, uint32_t batch);
 int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint32_t batch,
                 uint32_t *out_ids, float *out_scores, uint32_t kmax, int io, cudaStream_t st);
+// Device bytes of a batched call's workspace (0: the batch does not fit the
+// kernel's shared memory), and its reservation (grow-only, with the pinned
+// host mirror) for B users and scan depth up to kscan_max;
+// n_vals: user field values of the whole batch (0: one per field).
+size_t batch_ws_bytes(const ebr_index *ix, const ebr_cross *cross, uint32_t B,
+                      uint32_t kscan_max, uint64_t n_vals);
+int batch_ws_reserve(const ebr_index *ix, const ebr_cross *cross, uint32_t B,
+                     uint32_t kscan_max, uint64_t n_vals, BatchWs &w);
 // The same in two halves, for callers that keep several batches in flight:
 // batch_launch queues everything on st (w must stay untouched until
 // batch_finish returns); batch_finish waits, checks and recomputes.

@@ -1073,8 +1073,16 @@ static int run_wide(ebr_index *ix, const uint32_t *q_key, const float *q_w, uint
 }
 
 // w_hat transposed: wT[key][b] for b < Bp (zero for padding users b >= batch).
-__global__ void k_expand_T(CrossView cv, const uint32_t *__restrict__ users, uint32_t batch,
-                           uint32_t Bp, float *__restrict__ wT, uint32_t *__restrict__ flags) {
+// User b's field values are users[base[b] + uptr[b][i] .. base[b] +
+// uptr[b][i+1]) for field i (MULTI; offsets already checked); without MULTI
+// every field holds one value, users[b * f_u + i].  Pairs are summed in pair
+// order and a field's values in their order, as in the single-request
+// expansion, so both give the same FP32 w^.
+template <bool MULTI>
+__global__ void k_expand_T(CrossView cv, const uint32_t *__restrict__ users,
+                           const uint32_t *__restrict__ uptr, const uint32_t *__restrict__ base,
+                           uint32_t batch, uint32_t Bp, float *__restrict__ wT,
+                           uint32_t *__restrict__ flags) {
   extern __shared__ uint32_t s_off2[];
   for (uint32_t j = threadIdx.x; j <= cv.f_a; j += blockDim.x) s_off2[j] = cv.key_off[j];
   __syncthreads();
@@ -1091,20 +1099,26 @@ __global__ void k_expand_T(CrossView cv, const uint32_t *__restrict__ users, uin
         if (s_off2[mid] <= key) lo = mid; else hi = mid;
       }
       const uint32_t j = lo, v = key - s_off2[j];
+      const uint32_t *up = MULTI ? uptr + (uint64_t)b * (cv.f_u + 1) : nullptr;
+      const uint32_t ub = MULTI ? __ldg(base + b) : b * cv.f_u;
       for (uint32_t q = cv.pair_ptr[j]; q < cv.pair_ptr[j + 1]; q++) {
         const uint32_t p = cv.pair_of[q];
         const uint32_t i = cv.pair_user[p];
-        const uint32_t u = users[(uint64_t)b * cv.f_u + i];
-        if (u >= cv.vocab_u[i]) { bad |= DEVERR_BAD_USER; continue; }
-        float w;
-        if (cv.hashed) {
-          const uint64_t x = ((uint64_t)p << 40) | ((uint64_t)u << 20) | (uint64_t)v;
-          w = cv.table[splitmix64(x) & ((1ull << cv.hash_bits) - 1ull)];
-        } else {
-          const uint64_t off = ((uint64_t)cv.w_hi[p] << 32) | cv.w_lo[p];
-          w = cv.table[off + (uint64_t)u * cv.vocab_a[j] + v];
+        const uint32_t r0 = MULTI ? ub + __ldg(up + i) : ub + i;
+        const uint32_t r1 = MULTI ? ub + __ldg(up + i + 1) : r0 + 1;
+        for (uint32_t r = r0; r < r1; r++) {
+          const uint32_t u = __ldg(users + r);
+          if (u >= cv.vocab_u[i]) { bad |= DEVERR_BAD_USER; continue; }
+          float w;
+          if (cv.hashed) {
+            const uint64_t x = ((uint64_t)p << 40) | ((uint64_t)u << 20) | (uint64_t)v;
+            w = cv.table[splitmix64(x) & ((1ull << cv.hash_bits) - 1ull)];
+          } else {
+            const uint64_t off = ((uint64_t)cv.w_hi[p] << 32) | cv.w_lo[p];
+            w = cv.table[off + (uint64_t)u * cv.vocab_a[j] + v];
+          }
+          acc += w;
         }
-        acc += w;
       }
     }
     wT[t] = acc;
@@ -1112,13 +1126,19 @@ __global__ void k_expand_T(CrossView cv, const uint32_t *__restrict__ users, uin
   if (bad) atomicOr(flags, bad);
 }
 
-int expand_transposed(const ebr_cross *c, const uint32_t *users, uint32_t batch, uint32_t Bp,
-                      float *wT, uint32_t *flags, cudaStream_t st) {
+int expand_transposed(const ebr_cross *c, const uint32_t *users, const uint32_t *uptr,
+                      const uint32_t *base, uint32_t batch, uint32_t Bp, float *wT,
+                      uint32_t *flags, cudaStream_t st) {
   CrossView cv = cross_view(c);
   const uint64_t total = (uint64_t)cv.n_keys * Bp;
   uint64_t blocks = (total + 255) / 256;
   if (blocks > 65535) blocks = 65535;
-  k_expand_T<<<(int)blocks, 256, (c->f_a + 1) * 4, st>>>(cv, users, batch, Bp, wT, flags);
+  const size_t smem = (c->f_a + 1) * 4;
+  if (uptr)
+    k_expand_T<true><<<(int)blocks, 256, smem, st>>>(cv, users, uptr, base, batch, Bp, wT, flags);
+  else
+    k_expand_T<false><<<(int)blocks, 256, smem, st>>>(cv, users, nullptr, nullptr, batch, Bp, wT,
+                                                      flags);
   EBR_CUDA_TRY(cudaGetLastError());
   return EBR_OK;
 }
@@ -1248,8 +1268,9 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
     bool planned = false;
     EBR_TRY(run_wide(ix, q_key, q_w, n_q, ctrl, st, w_dense, &planned));
     if (n_q) {
-      ix->launches += planned ? 2 : 3;
-      ix->lib_launches += planned ? 0 : 2;
+      // planned: k_wide_plan, k_wide_scatter; else k_wide_lens, the three
+      // kernels of the scan of lens, k_wide_compact, k_wide_scatter
+      ix->launches += planned ? 2 : 6;
     }
     pm.mark(2, st);
     if (fused_fits(ix, kscan)) {

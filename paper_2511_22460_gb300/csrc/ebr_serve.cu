@@ -37,11 +37,14 @@ struct Slot {
   double t_submit = 0.0;
   int rc = EBR_OK;
   std::string err;
+  uint32_t n_uv = 0;       // user field values held (f_u when single-valued)
+  bool has_ptr = false;    // multi-valued: field offsets in d_uptr
   float *d_hu = nullptr;
-  uint32_t *d_uv = nullptr;
+  uint32_t *d_uv = nullptr;    // [max_user_vals]
+  uint32_t *d_uptr = nullptr;  // [f_u + 1]
   uint64_t *d_filter = nullptr;
   float *h_hu = nullptr;
-  uint32_t *h_uv = nullptr;
+  uint32_t *h_uv = nullptr;    // [max_user_vals], then the offsets [f_u + 1]
   uint64_t *h_filter = nullptr;
   uint32_t *h_ids = nullptr;
   float *h_scores = nullptr;
@@ -70,25 +73,6 @@ size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
 
-// Device bytes one batched call of B users may reserve in its workspace.
-static size_t batch_ws_bytes(const ebr_index *ix, const ebr_cross *cross, uint32_t B,
-                             uint32_t kscan) {
-  uint32_t Bq = 32;
-  while (Bq < B) Bq <<= 1;
-  const uint64_t grid = std::max(1, std::min<int>(ix->num_sms, (int)ix->n_win));
-  const uint64_t per_cta = (kscan + grid - 1) / grid;
-  const uint64_t m = std::max<uint64_t>(64, (2 * per_cta + 32 + 31) / 32 * 32);
-  const uint64_t cap_u = 2 * m + 256;
-  const uint64_t words = (ix->n_ads + 63) / 64;
-  size_t t = 0;
-  t += round256((size_t)Bq * ix->d * 4) + round256((size_t)Bq * ix->d * 2);
-  t += round256((size_t)B * cross->f_u * 4) + round256(((size_t)ix->n_keys + 1) * Bq * 4);
-  t += round256((size_t)B * words * 8) + round256(small_bytes(B));
-  t += round256(grid * B * cap_u * 16) + round256(grid * B * 4) + round256(grid * B * 8);
-  t += round256((size_t)B * (32768 + 8192) * 8) + 256;
-  return t;
-}
-
 }  // namespace ebr
 
 using namespace ebr;
@@ -104,6 +88,7 @@ struct ebr_server {
   int device = 0;
   uint32_t d = 0;                // embedding dimension (the same for every index served)
   uint32_t max_batch = 64, max_slots = 256, k_max = 1000, timeout_ms = 0;
+  uint32_t max_user_vals = 0;    // user field values one request may carry
   uint32_t words = 0;
   bool batched_ok = false;
   std::vector<Slot> slots;
@@ -153,6 +138,8 @@ int pipe_launch(ebr_server *s, int p, const std::vector<int> &take) {
     ebr_query &q = P.qs[i];
     q.h_u = sl.d_hu;
     q.user_vals = sl.d_uv;
+    q.user_ptr = sl.has_ptr ? sl.d_uptr : nullptr;
+    q.n_user_vals = sl.has_ptr ? sl.n_uv : 0;
     q.filter = sl.has_filter ? sl.d_filter : nullptr;
     q.k = sl.k;
     P.kmax = std::max(P.kmax, sl.k);
@@ -313,26 +300,10 @@ void server_free(ebr_server *s) {
 // that serving allocates nothing after creation.
 int pipe_reserve(ebr_server *s, Pipe &P) {
   ebr_index *ix = s->ix;
-  const uint32_t B = s->max_batch, d = ix->d, fu = s->cross->f_u;
-  uint32_t Bq = 32;
-  while (Bq < B) Bq <<= 1;
+  const uint32_t B = s->max_batch;
   const uint32_t kscan = std::min<uint32_t>(s->k_max * ix->rescore_mult, ix->n_ads);
-  const int grid = std::max(1, std::min<int>(ix->num_sms, (int)ix->n_win));
-  const uint64_t per_cta = (kscan + grid - 1) / grid;
-  const uint64_t m = std::max<uint64_t>(64, (2 * per_cta + 32 + 31) / 32 * 32);
-  const uint64_t cap_u = 2 * m + 256;
-  const size_t words = s->words;
-  EBR_TRY(dev_reserve(P.ws.users_f32, (size_t)Bq * d * 4));
-  EBR_TRY(dev_reserve(P.ws.users_bf16, (size_t)Bq * d * 2));
-  EBR_TRY(dev_reserve(P.ws.user_vals, (size_t)B * fu * 4));
-  EBR_TRY(dev_reserve(P.ws.wT, ((size_t)ix->n_keys + 1) * Bq * 4));
-  EBR_TRY(dev_reserve(P.ws.filters, (size_t)B * words * 8));
-  EBR_TRY(dev_reserve(P.ws.small, small_bytes(B)));
-  EBR_TRY(dev_reserve(P.ws.cand, (size_t)grid * B * cap_u * 16));
-  EBR_TRY(dev_reserve(P.ws.cand_n, (size_t)grid * B * 4));
-  EBR_TRY(dev_reserve(P.ws.cand_thr, (size_t)grid * B * 8));
-  EBR_TRY(dev_reserve(P.ws.scratch, (size_t)B * (32768 + 8192) * 8));
-  EBR_TRY(dev_reserve(P.ws.ctrl, sizeof(Ctrl)));
+  if (s->batched_ok)
+    EBR_TRY(batch_ws_reserve(ix, s->cross, B, kscan, (uint64_t)B * s->max_user_vals, P.ws));
   const size_t ob = round256((size_t)B * s->k_max * 4);
   EBR_TRY(dev_reserve(P.out, 2 * ob));
   if (cudaMallocHost((void **)&P.h_ids, (size_t)B * s->k_max * 4) != cudaSuccess ||
@@ -387,12 +358,19 @@ extern "C" int ebr_server_create(ebr_index *ix, const ebr_cross *cross, const eb
     cudaMemGetInfo(&fr, &tot);
     budget = fr / 2;
   }
-  s->slot_bytes = round256((size_t)s->words * 8) + round256((size_t)ix->d * 4) +
-                  round256((size_t)cross->f_u * 4);
+  s->max_user_vals = c.max_user_vals ? c.max_user_vals : 8 * cross->f_u;
+  const size_t uv_bytes = round256((size_t)(s->max_user_vals + cross->f_u + 1) * 4);
+  s->slot_bytes = round256((size_t)s->words * 8) + round256((size_t)ix->d * 4) + uv_bytes;
   const uint32_t kscan = std::min<uint32_t>(c.k_max * ix->rescore_mult, ix->n_ads);
+  s->batched_ok = c.max_batch >= 2 && batch_index_ok(ix, cross, std::min<uint32_t>(c.max_batch, 256)) &&
+                  (uint64_t)c.k_max * ix->rescore_mult <= 8192;
   uint32_t mb = c.max_batch;
   auto pipes_bytes = [&](uint32_t B) {
-    return 2 * (batch_ws_bytes(ix, cross, B, kscan) + 2 * round256((size_t)B * c.k_max * 4));
+    const size_t ws = s->batched_ok ? batch_ws_bytes(ix, cross, std::max<uint32_t>(B, 2), kscan,
+                                                     (uint64_t)std::max<uint32_t>(B, 2) *
+                                                         s->max_user_vals)
+                                    : 0;
+    return 2 * (ws + 2 * round256((size_t)B * c.k_max * 4));
   };
   while (mb > 1 && pipes_bytes(mb) + (uint64_t)mb * s->slot_bytes > budget) mb >>= 1;
   if (pipes_bytes(mb) + (uint64_t)mb * s->slot_bytes > budget) {
@@ -409,12 +387,11 @@ extern "C" int ebr_server_create(ebr_index *ix, const ebr_cross *cross, const eb
   const uint32_t want = c.max_slots ? c.max_slots : 4 * mb;
   n_slots = std::min<uint64_t>(n_slots, want);
   s->max_slots = (uint32_t)std::max<uint64_t>(n_slots, 1);
-  s->batched_ok = ix->dtype == EBR_BF16;
   s->lat.assign(65536, 0.f);
   // slots: device memory and pinned host staging
   int rc = dev_alloc(s->slot_mem, (size_t)s->max_slots * s->slot_bytes);
   const size_t host_slot = round256((size_t)s->words * 8) + round256((size_t)ix->d * 4) +
-                           round256((size_t)cross->f_u * 4) + 2 * round256((size_t)c.k_max * 4);
+                           uv_bytes + 2 * round256((size_t)c.k_max * 4);
   if (rc == EBR_OK && cudaMallocHost(&s->slot_host, (size_t)s->max_slots * host_slot) != cudaSuccess) {
     cudaGetLastError();
     set_error("ebr_server_create: pinned host allocation failed");
@@ -432,13 +409,14 @@ extern "C" int ebr_server_create(ebr_index *ix, const ebr_cross *cross, const eb
       sl.d_filter = (uint64_t *)dp;
       sl.d_hu = (float *)(dp + round256((size_t)s->words * 8));
       sl.d_uv = (uint32_t *)(dp + round256((size_t)s->words * 8) + round256((size_t)ix->d * 4));
+      sl.d_uptr = sl.d_uv + s->max_user_vals;
       char *hp = (char *)s->slot_host + (size_t)i * host_slot;
       sl.h_filter = (uint64_t *)hp;
       hp += round256((size_t)s->words * 8);
       sl.h_hu = (float *)hp;
       hp += round256((size_t)ix->d * 4);
       sl.h_uv = (uint32_t *)hp;
-      hp += round256((size_t)cross->f_u * 4);
+      hp += uv_bytes;
       sl.h_ids = (uint32_t *)hp;
       hp += round256((size_t)c.k_max * 4);
       sl.h_scores = (float *)hp;
@@ -469,17 +447,34 @@ extern "C" int ebr_submit(ebr_server *s, const ebr_query *q, uint64_t *ticket) {
     set_error("ebr_submit: needs a server, h_u and user_vals (host pointers) and a ticket");
     return EBR_EINVAL;
   }
-  if (q->k == 0 || q->k > s->k_max || q->q_key || q->q_w || q->user_ptr) {
-    set_error("ebr_submit: k must be 1..%u; q_key/q_w and multi-valued user fields "
-              "(user_ptr) are not accepted", s->k_max);
+  if (q->k == 0 || q->k > s->k_max || q->q_key || q->q_w) {
+    set_error("ebr_submit: k must be 1..%u; q_key/q_w are not accepted", s->k_max);
     return EBR_EINVAL;
   }
-  for (uint32_t f = 0; f < s->cross->f_u; f++)
-    if (q->user_vals[f] >= s->cross->vocab_u_host[f]) {
-      set_error("ebr_submit: user field %u value %u outside its vocabulary of %u", f,
-                q->user_vals[f], s->cross->vocab_u_host[f]);
+  const uint32_t fu = s->cross->f_u;
+  const uint32_t n_uv = q->user_ptr ? q->n_user_vals : fu;
+  if (q->user_ptr) {
+    if (n_uv > s->max_user_vals) {
+      set_error("ebr_submit: %u user field values exceed the server's max_user_vals of %u", n_uv,
+                s->max_user_vals);
       return EBR_EINVAL;
     }
+    for (uint32_t f = 0; f <= fu; f++)
+      if ((f == 0 && q->user_ptr[0] != 0) || (f > 0 && q->user_ptr[f] < q->user_ptr[f - 1]) ||
+          (f == fu && q->user_ptr[f] != n_uv)) {
+        set_error("ebr_submit: user_ptr must start at 0, not decrease and end at n_user_vals");
+        return EBR_EINVAL;
+      }
+  }
+  for (uint32_t f = 0; f < fu; f++) {
+    const uint32_t r0 = q->user_ptr ? q->user_ptr[f] : f, r1 = q->user_ptr ? q->user_ptr[f + 1] : f + 1;
+    for (uint32_t r = r0; r < r1; r++)
+      if (q->user_vals[r] >= s->cross->vocab_u_host[f]) {
+        set_error("ebr_submit: user field %u value %u outside its vocabulary of %u", f,
+                  q->user_vals[r], s->cross->vocab_u_host[f]);
+        return EBR_EINVAL;
+      }
+  }
   int i = -1;
   uint64_t t = 0;
   {
@@ -501,8 +496,11 @@ extern "C" int ebr_submit(ebr_server *s, const ebr_query *q, uint64_t *ticket) {
   sl.rc = EBR_OK;
   sl.err.clear();
   sl.t_submit = now_s();
+  sl.n_uv = n_uv;
+  sl.has_ptr = q->user_ptr != nullptr;
   memcpy(sl.h_hu, q->h_u, (size_t)s->d * 4);
-  memcpy(sl.h_uv, q->user_vals, (size_t)s->cross->f_u * 4);
+  memcpy(sl.h_uv, q->user_vals, (size_t)n_uv * 4);
+  if (sl.has_ptr) memcpy(sl.h_uv + s->max_user_vals, q->user_ptr, (size_t)(fu + 1) * 4);
   if (sl.has_filter) memcpy(sl.h_filter, q->filter, (size_t)s->words * 8);
   int prev = 0;
   cudaGetDevice(&prev);
@@ -510,8 +508,10 @@ extern "C" int ebr_submit(ebr_server *s, const ebr_query *q, uint64_t *ticket) {
   cudaError_t e = cudaMemcpyAsync(sl.d_hu, sl.h_hu, (size_t)s->d * 4, cudaMemcpyHostToDevice,
                                   s->copy_st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(sl.d_uv, sl.h_uv, (size_t)s->cross->f_u * 4, cudaMemcpyHostToDevice,
-                        s->copy_st);
+    e = cudaMemcpyAsync(sl.d_uv, sl.h_uv, (size_t)n_uv * 4, cudaMemcpyHostToDevice, s->copy_st);
+  if (e == cudaSuccess && sl.has_ptr)
+    e = cudaMemcpyAsync(sl.d_uptr, sl.h_uv + s->max_user_vals, (size_t)(fu + 1) * 4,
+                        cudaMemcpyHostToDevice, s->copy_st);
   if (e == cudaSuccess && sl.has_filter)
     e = cudaMemcpyAsync(sl.d_filter, sl.h_filter, (size_t)s->words * 8, cudaMemcpyHostToDevice,
                         s->copy_st);

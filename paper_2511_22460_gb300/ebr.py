@@ -65,7 +65,7 @@ class QueryC(C.Structure):
 
 class ServerCfg(C.Structure):
     _fields_ = [("hbm_budget", u64), ("max_batch", u32), ("max_slots", u32), ("k_max", u32),
-                ("queue_timeout_ms", u32)]
+                ("queue_timeout_ms", u32), ("max_user_vals", u32)]
 
 
 class ServerStats(C.Structure):
@@ -410,17 +410,20 @@ class Server:
     Requests are host arrays; results come back as host arrays."""
 
     def __init__(self, index: Index, cross: Cross, hbm_budget=0, max_batch=0, max_slots=0,
-                 k_max=0, queue_timeout_ms=0):
+                 k_max=0, queue_timeout_ms=0, max_user_vals=0):
         cfg = ServerCfg(int(hbm_budget), int(max_batch), int(max_slots), int(k_max),
-                        int(queue_timeout_ms))
+                        int(queue_timeout_ms), int(max_user_vals))
         h = vp()
         _check(ebr_server_create(index.h, cross.h, C.byref(cfg), C.byref(h)), "ebr_server_create")
         self.h = h.value
         self._keep = (index, cross)
 
-    def submit(self, h_u, user_vals, k, filter=None):
-        """Ticket of the admitted request, or None when admission is refused."""
-        q = QueryC(ptr(h_u), ptr(user_vals), 0, None, None, ptr(filter), int(k), 0)
+    def submit(self, h_u, user_vals, k, filter=None, user_ptr=None):
+        """Ticket of the admitted request, or None when admission is refused.
+        user_ptr (uint32 [f_u + 1]) makes user_vals a history per field."""
+        n_uv = 0 if user_ptr is None else int(len(user_vals))
+        q = QueryC(ptr(h_u), ptr(user_vals), 0, None, None, ptr(filter), int(k), 0,
+                   ptr(user_ptr), n_uv)
         t = u64()
         rc = ebr_submit(self.h, C.byref(q), C.byref(t))
         if rc == EBR_ENOMEM:

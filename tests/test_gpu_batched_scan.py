@@ -174,3 +174,96 @@ def test_batched_fp8_topk_matches_oracle(n, B, d, k, capsys):
     with capsys.disabled():
         print("\n[recall] batched fp8 d=%d %d ads K=%d: before rescoring %.4f (min %.4f), after 1.0"
               % (d, n, k, float(np.mean(pre)), float(np.min(pre))))
+
+
+def _history_refs(w, hs, post):
+    cr = oracle.Cross.from_workload(w)
+    refs = []
+    for b, (p_b, v_b) in enumerate(hs):
+        ref = oracle.score_query_seq(w, w.h_u[b], p_b, v_b, cr, post)
+        _, cond = oracle.scores_brute_seq(cr, w.h_u[b], w.emb, w.ad_vals, p_b, v_b,
+                                          with_cond=True)
+        refs.append((ref, oracle.tolerance(ref, cond)))
+    return refs
+
+
+@pytest.mark.parametrize("dtype,io", [("bf16", ebr.IO_DEVICE), ("bf16", ebr.IO_HOST),
+                                      ("fp8e4m3", ebr.IO_DEVICE)])
+def test_batched_multi_valued_users(dtype, io):
+    """Users whose fields hold histories (several values, some none; the
+    HitMatch sum over every user value of a cross pair) mixed with
+    single-valued users in one batch: all on the tensor-core scan, none
+    recomputed, each against the FP64 oracle."""
+    from paper_2511_22460_gb300.datagen import user_histories
+    B, n, k = 24, 40_000, 200
+    w = make_workload("serve_bf16_5m", n_ads=n, seed=21, batch=B)
+    post = w.postings(shuffle=True)
+    ix = ebr.build_index(w.n_ads, w.n_keys, *post, w.emb, dtype=dtype)
+    cross = ebr.cross_from_workload(w)
+    hs = user_histories(w, B, max_len=6, seed=5)
+    # every third user keeps its single value per field
+    hs = [(None, w.users[b]) if b % 3 == 0 else hs[b] for b in range(B)]
+    host = io == ebr.IO_HOST
+    conv = (lambda a: np.ascontiguousarray(a)) if host else dev
+    qs = [ebr.Query(h_u=conv(w.h_u[b]), k=k, user_vals=conv(v),
+                    user_ptr=None if p is None else conv(p)) for b, (p, v) in enumerate(hs)]
+    if host:
+        ids = np.empty((B, k), np.uint32)
+        sc = np.empty((B, k), np.float32)
+    else:
+        ids = torch.empty((B, k), dtype=torch.int32, device=DEV)
+        sc = torch.empty((B, k), dtype=torch.float32, device=DEV)
+    before = ix.profile_read()
+    ebr.score_topk(ix, cross, qs, ids, sc, io=io)
+    after = ix.profile_read()
+    assert after.batched - before.batched == B, "the batched path did not run"
+    assert after.recomputed - before.recomputed == 0
+    if not host:
+        ids = ids.cpu().numpy().view(np.uint32)
+        sc = sc.cpu().numpy()
+    refs = _history_refs(w, [(p if p is not None else np.arange(w.vocab_u.size + 1,
+                                                                  dtype=np.uint32), v)
+                             for p, v in hs], post)
+    for b, (p, v) in enumerate(hs):
+        ref, tol = refs[b]
+        assert recall(ids[b], ref, tol, k) == 1.0, "user %d" % b
+        check_topk(ids[b], sc[b], ref, tol, k)
+
+
+@pytest.mark.parametrize("io", [ebr.IO_DEVICE, ebr.IO_HOST])
+def test_batched_multi_valued_bad_offsets(io):
+    """Offsets that do not end at n_user_vals, or decrease, fail the batch
+    with EBR_EDATA (host requests: found on the host; device requests: by
+    the staging kernel), and the index stays usable."""
+    from paper_2511_22460_gb300.datagen import user_histories
+    B, n, k = 4, 20_000, 50
+    w = make_workload("serve_bf16_5m", n_ads=n, seed=22, batch=B)
+    post = w.postings()
+    ix = ebr.build_index(w.n_ads, w.n_keys, *post, w.emb, dtype="bf16")
+    cross = ebr.cross_from_workload(w)
+    hs = user_histories(w, B, max_len=4, seed=6)
+    host = io == ebr.IO_HOST
+    conv = (lambda a: np.ascontiguousarray(a)) if host else dev
+    ids = np.empty((B, k), np.uint32) if host else torch.empty((B, k), dtype=torch.int32,
+                                                               device=DEV)
+    sc = np.empty((B, k), np.float32) if host else torch.empty((B, k), dtype=torch.float32,
+                                                               device=DEV)
+    p2 = hs[2][0]
+    bad_end = p2.copy()
+    bad_end[-1] += 1
+    bad_order = p2.copy()
+    bad_order[1] = p2[-1] + 5
+    for bad in (bad_end, bad_order):
+        qs = [ebr.Query(h_u=conv(w.h_u[b]), k=k, user_vals=conv(hs[b][1]),
+                        user_ptr=conv(bad if b == 2 else hs[b][0])) for b in range(B)]
+        with pytest.raises(ebr.EbrError) as e:
+            ebr.score_topk(ix, cross, qs, ids, sc, io=io)
+        assert e.value.code == ebr.EBR_EDATA
+    qs = [ebr.Query(h_u=conv(w.h_u[b]), k=k, user_vals=conv(hs[b][1]), user_ptr=conv(hs[b][0]))
+          for b in range(B)]
+    ebr.score_topk(ix, cross, qs, ids, sc, io=io)
+    if not host:
+        ids = ids.cpu().numpy().view(np.uint32)
+        sc = sc.cpu().numpy()
+    for b, (ref, tol) in enumerate(_history_refs(w, hs, post)):
+        check_topk(ids[b], sc[b], ref, tol, k)

@@ -574,7 +574,7 @@ def test_multi_valued_user_fields_and_empty_ad_fields(dtype):
     got = ids[0].cpu().numpy().view(np.uint32)
     assert recall(got, *refs[0], k) == 1.0
     check_topk(got, sc[0].cpu().numpy(), *refs[0], k)
-    ebr.score_topk(ix, cross, qs, ids, sc)  # a batch: each request on the single-request scan
+    ebr.score_topk(ix, cross, qs, ids, sc)  # a batch (the batched scan for BF16)
     for b in range(3):
         check_topk(ids[b].cpu().numpy().view(np.uint32), sc[b].cpu().numpy(), *refs[b], k)
     hid = np.empty(k, np.int32)

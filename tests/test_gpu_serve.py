@@ -246,3 +246,59 @@ def test_destroy_while_swap_calls_wait():
             t.join(timeout=30)
         assert not any(t.is_alive() for t in ts)
         assert sorted(out) and all(rc in (ebr.EBR_OK, ebr.EBR_EINVAL) for rc in out), out
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8e4m3"])
+def test_multi_valued_requests_served_alone_and_in_a_mix(dtype):
+    """Requests whose user fields hold histories are admitted as slots and
+    served in the batched scan beside single-valued ones; each result equals
+    the FP64 oracle's and the request served alone."""
+    import oracle
+    from paper_2511_22460_gb300.datagen import user_histories
+    n, B, k = 40_000, 20, 300
+    w, post, ix, cross = _setup(n, B, dtype=dtype, seed=23)
+    f_u = w.vocab_u.size
+    hs = user_histories(w, B, max_len=5, seed=8)
+    hs = [(None, w.users[b]) if b % 4 == 0 else hs[b] for b in range(B)]
+    srv = ebr.Server(ix, cross, max_batch=32, k_max=1000, max_user_vals=5 * f_u)
+    try:
+        def submit(b):
+            p, v = hs[b]
+            return srv.submit(w.h_u[b], np.ascontiguousarray(v), k, user_ptr=p)
+
+        alone = {b: srv.wait(submit(b), k) for b in (1, 4)}
+        tickets = [submit(b) for b in range(B)]
+        assert all(t is not None for t in tickets)
+        mixed = {b: srv.wait(t, k) for b, t in enumerate(tickets)}
+        st = srv.stats()
+        assert st.failed == 0 and st.batches < B + 2, "requests were never batched"
+        prof = ix.profile_read()
+        assert prof.batched > 0 and prof.recomputed == 0
+        cr = oracle.Cross.from_workload(w)
+        for b in range(B):
+            p, v = hs[b]
+            if p is None:
+                p = np.arange(f_u + 1, dtype=np.uint32)
+            ref = oracle.score_query_seq(w, w.h_u[b], p, v, cr, post)
+            _, cond = oracle.scores_brute_seq(cr, w.h_u[b], w.emb, w.ad_vals, p, v,
+                                              with_cond=True)
+            tol = oracle.tolerance(ref, cond)
+            ids, sc = mixed[b]
+            assert recall(ids, ref, tol, k) == 1.0, "request %d" % b
+            check_topk(ids, sc, ref, tol, k)
+            if b in alone:
+                _same_result(alone[b], mixed[b], ref, tol, k)
+        # refused at submit: too many values, bad offsets, a value outside its vocabulary
+        p1, v1 = hs[1]
+        long_p = np.arange(f_u + 1, dtype=np.uint32) * 6
+        long_v = np.zeros(int(long_p[-1]), np.uint32)
+        bad_end = p1.copy()
+        bad_end[-1] += 1
+        bad_val = v1.copy()
+        bad_val[0] = 1 << 30
+        for p, v in ((long_p, long_v), (bad_end, v1), (p1, bad_val)):
+            with pytest.raises(ebr.EbrError) as e:
+                srv.submit(w.h_u[1], np.ascontiguousarray(v), k, user_ptr=p)
+            assert e.value.code == ebr.EBR_EINVAL
+    finally:
+        srv.close()
