@@ -230,26 +230,30 @@ extern "C" int ebr_debug_wait_timeout(uint32_t timeout_us, void *stream) {
 // Batched scan: B users against every ad, one pass over the inventory
 // =====================================================================
 // Per window of 256 ads (one persistent CTA per SM, contiguous windows):
-//   producer warp   -- tensor TMA of the window's BF16 ad rows into a stage
-//                      ring; the users' BF16 vectors are loaded once;
+//   producer warp   -- tensor TMA of the window's BF16/FP8 ad rows into a
+//                      stage ring; the users' vectors are loaded once;
 //   MMA warp        -- tcgen05.mma with the users as the M side and the
-//                      window's ads as N = 256: deep[user][ad] (Eq. 1) lands
-//                      in TMEM with one user per TMEM lane;
+//                      window's ads as N = 256, in two M-tiles: the even
+//                      users and the odd users (the user table is stored in
+//                      that pair order), each replicated down the 128 TMEM
+//                      lanes when the batch has fewer than 256 users;
+//                      deep[user][ad] (Eq. 1) lands in TMEM, FP32;
 //   list warps (2)  -- walk the window's blocks in the window-major view of
 //                      the compressed list and lay out, per run of 32 ads, a
 //                      key table T[r][i] = r-th key of ad i (the window's
 //                      slice of L, transposed; short ads padded with a zero
 //                      row of w^T);
-//   epilogue (8)    -- thread = user (its TMEM lane), runs of 32 ads per
-//                      warp: wide[i] += w^T[T[r][i]][user] for every row r
-//                      (64 independent coalesced 128-byte loads per step,
-//                      accumulators in registers), added to the 32 deep
-//                      scores of one TMEM load, filtered, and each user's
-//                      candidates above its running threshold go to this
-//                      CTA's per-user buffer (top-m kept exactly).
-// Fewer than 128 users are replicated across the 128 TMEM lanes so that all
-// eight epilogue warps have work: with Bq users (32, 64 or 128) per replica,
-// warp w serves users 32(w%4) mod Bq .. +31 on a run of Bq ads.
+//   epilogue (8)    -- thread = user pair (2u, 2u + 1) at TMEM lane L
+//                      (u = L mod Bq/2), runs of 32 ads per warp:
+//                      wide[i] += w^T[T[r][i]][2u .. 2u + 1] for every row r
+//                      (32 independent coalesced 8-byte loads and 32 paired
+//                      FP32 adds per row, accumulators in registers), added
+//                      to both users' deep scores (TMEM columns c and
+//                      256 + c), filtered, and each user's candidates above
+//                      its running threshold go to this CTA's per-user buffer
+//                      (top-m kept exactly).
+// With Bq/2 user pairs per replica (32, 64 or 128), the 256/(Bq/2) warps
+// that hold the same pairs split the window's ads, Bq/2 ads each.
 namespace ebr {
 
 constexpr int kBWin = 256;
@@ -263,6 +267,12 @@ static_assert(kBWin % (kListWarps * 32) == 0, "list threads split the window's a
 constexpr uint32_t kListHdr = 8 + 8 + kBWin;
 constexpr uint32_t kMaxBatchKeysPerAd = 64;  // longest key list the batched tables hold
 
+// Row of user b in the batch's user table: even users first, then odd ones
+// (the two M-tiles of the batched scan), `half` = Bq / 2 rows each.
+__host__ __device__ __forceinline__ uint32_t user_row(uint32_t b, uint32_t half) {
+  return (b & 1u) * half + (b >> 1);
+}
+
 struct CandEntry {
   unsigned long long key;  // approximate score | id
   float wide;              // the ad's wide term for this user (FP32 sum)
@@ -271,7 +281,7 @@ struct CandEntry {
 
 struct BatchArgs {
   CUtensorMap ta;  // ad rows, BF16 or FP8 [N][d], box {tile row, 128}
-  CUtensorMap tu;  // users, same type [Bq][d], box {tile row, min(Bq, 128)}
+  CUtensorMap tu;  // users, same type [Bq][d] in pair order, box {tile row, Bq / 2}
   const uint32_t *wkey[kGroups];
   const uint8_t *wvals[kGroups];
   const uint32_t *win_ptr[kGroups];
@@ -280,11 +290,11 @@ struct BatchArgs {
   const uint64_t *filters;     // [B][words] (rows of users without a filter are unused)
   const uint32_t *has_filter;  // [B]
   uint32_t n_ads, n_win, B, Bq, d, m, cap_u, list_cap, words;
-  uint32_t zero_row;           // n_keys * Bq: offset of the zero row of wT
+  uint32_t zero_row;           // n_keys * Bq / 2: the zero row of wT, in user-pair units
   uint32_t sa, lb, tb;         // A stages, list buffers, TMEM buffers
   uint32_t tile_row, kb_n;     // bytes per K-tile row (128 or 64), K-tiles per row
   const float *ad_scale;       // FP8: [N] row scales of the ad table
-  const float *user_scale;     // FP8: [Bq] row scales of the quantised users
+  const float *user_scale;     // FP8: [Bq] row scales of the quantised users (pair order)
   CandEntry *cand;             // [grid][B][cap_u]
   uint32_t *cand_n;            // [grid][B]
   unsigned long long *cand_thr;  // [grid][B]
@@ -516,7 +526,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t kb_n = a.kb_n, tr = a.tile_row;  // K-tiles per row, bytes per tile row
   const uint32_t tile_elems = tr / (F8 ? 1u : 2u);
-  const uint32_t n_mt = a.Bq > 128 ? 2u : 1u;     // 128-user M-tiles
+  const uint32_t n_mt = 2;                        // M-tiles: even users, odd users
   const uint32_t u_tile = kb_n * 128u * tr;        // one M-tile: kb_n x [128 rows x tr]
   const uint32_t a_stage = kb_n * 256u * tr;       // kb_n x [256 ad rows x tr]
   uint8_t *su = smem;                              // n_mt user tiles
@@ -564,14 +574,15 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
     // ---------------------------------------------------------- producer
     if (lane == 0) {
       const uint64_t pol = l2_evict_first_policy();
-      // users: M-tile rows r hold user r mod Bq (replicas when Bq < 128)
-      const uint32_t box_u = a.Bq < 128 ? a.Bq : 128u;
+      // users (stored in pair order: even users, then odd users): row r of
+      // M-tile mt holds user 2 (r mod Bq/2) + mt (replicas when Bq < 256)
+      const uint32_t box_u = a.Bq / 2;
       mbar_arrive_expect_tx(&sm.u_full, n_mt * u_tile);
       for (uint32_t mt = 0; mt < n_mt; mt++)
         for (uint32_t r0 = 0; r0 < 128; r0 += box_u)
           for (uint32_t kb = 0; kb < kb_n; kb++)
             tma_load_2d(su + mt * u_tile + kb * 128u * tr + r0 * tr, &a.tu,
-                        (int)(kb * tile_elems), (int)(n_mt > 1 ? mt * 128 : 0), &sm.u_full);
+                        (int)(kb * tile_elems), (int)(mt * box_u), &sm.u_full);
       for (uint32_t j = 0; j < my_wins; j++) {
         const uint32_t s = j % a.sa;
         if (j >= a.sa && !mbar_wait_bounded(&sm.a_empty[s], ((j / a.sa) - 1) & 1u, kWaitTimeoutNs)) {
@@ -694,36 +705,51 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
       walk_window(a, w, lt, kListThreads, [&](uint32_t l, uint32_t key) {
         const uint32_t rank = atomicAdd(&fill[l], 1u);
         const uint32_t pos = run_off[l >> 5] + rank * 32u + (l & 31u);
-        if (rank < run_rows[l >> 5] && pos < a.list_cap) tab[pos] = key * a.Bq;
+        if (rank < run_rows[l >> 5] && pos < a.list_cap) tab[pos] = key * (a.Bq / 2);
       });
       mbar_arrive(&sm.l_full[lbuf]);  // release: this thread's list writes
     }
   } else {
     // ---------------------------------------------------------- epilogue
+    // Thread = user pair (2u, 2u + 1): M-tile 0 holds the even users and
+    // M-tile 1 the odd ones, each replicated down the 128 lanes, so lane L
+    // reads both users' deep scores (columns c and 256 + c) and gathers
+    // both users' weights with one 8-byte load of the user-minor w^T.
     const GroupSync gsync{1, kEpiThreads};
     const uint32_t q = warp % 4;                  // TMEM lane quadrant of this warp
     uint32_t *hist = whist + warp * 256;
-    uint32_t mt, user, ad_lo, n_ads_w;
-    if (n_mt > 1) {  // 256 users: warp w serves M-tile w/4, all 256 ads
-      mt = warp / 4;
-      user = mt * 128 + 32 * q + lane;
-      ad_lo = 0;
-      n_ads_w = 256;
-    } else {  // Bq users replicated 128/Bq times; warps split the window's ads
-      const uint32_t rep = 128 / a.Bq;
-      mt = 0;
-      user = (32 * q) % a.Bq + lane;
-      ad_lo = ((warp / 4) * rep + (32 * q) / a.Bq) * a.Bq;
-      n_ads_w = a.Bq;
-    }
-    const uint32_t tl = tmem + ((32u * q) << 16) + mt * 256u;
-    const bool user_ok = user < a.B;
-    // FP8: deep = TMEM x (user scale) x (the ad row's scale)
-    const float u_sc = F8 && user_ok ? a.user_scale[user] : 1.f;
-    const bool filt = user_ok && a.has_filter[user];
-    const uint64_t *frow = a.filters + (uint64_t)(user_ok ? user : 0u) * a.words;
-    const float *wcol = a.wT + user;
-    CandEntry *ubuf = a.cand + ((uint64_t)blockIdx.x * a.B + (user_ok ? user : 0u)) * a.cap_u;
+    const uint32_t U2 = a.Bq / 2;                 // user pairs (32, 64 or 128)
+    const uint32_t pair = (32u * q + lane) % U2;
+    const uint32_t ad_lo = ((warp / 4) * (128 / U2) + q / (U2 / 32)) * U2, n_ads_w = U2;
+    const uint32_t tl = tmem + ((32u * q) << 16);
+    const uint32_t user0 = 2 * pair, user1 = 2 * pair + 1;
+    const bool ok0 = user0 < a.B, ok1 = user1 < a.B;
+    // FP8: deep = TMEM x (user scale) x (the ad row's scale); user rows in pair order
+    const float usc0 = F8 && ok0 ? a.user_scale[pair] : 1.f;
+    const float usc1 = F8 && ok1 ? a.user_scale[U2 + pair] : 1.f;
+    const bool filt0 = ok0 && a.has_filter[user0], filt1 = ok1 && a.has_filter[user1];
+    const uint64_t *frow0 = a.filters + (uint64_t)(ok0 ? user0 : 0u) * a.words;
+    const uint64_t *frow1 = a.filters + (uint64_t)(ok1 ? user1 : 0u) * a.words;
+    const float2 *wcol = reinterpret_cast<const float2 *>(a.wT) + pair;
+    CandEntry *ubuf0 = a.cand + ((uint64_t)blockIdx.x * a.B + (ok0 ? user0 : 0u)) * a.cap_u;
+    CandEntry *ubuf1 = a.cand + ((uint64_t)blockIdx.x * a.B + (ok1 ? user1 : 0u)) * a.cap_u;
+    // one (user, ad) score: filtered, thresholded, appended to the user's buffer
+    auto offer = [&](uint32_t user, bool filt, const uint64_t *frow, CandEntry *ubuf,
+                     unsigned long long thr, float deep, float wide, uint32_t ad) {
+      const unsigned long long key = make_key(deep + wide, ad);
+      if (key < thr) return;
+      if (filt && !((__ldg(frow + (ad >> 6)) >> (ad & 63)) & 1ull)) return;
+      const uint32_t pos = atomicAdd(&sm.cnt_u[user], 1u);
+      if (pos < a.cap_u) {
+        CandEntry ce;
+        ce.key = key;
+        ce.wide = wide;
+        ce.pad = 0;
+        ubuf[pos] = ce;
+      } else {
+        atomicOr(&a.ctrl->flags, DEVERR_OVERFLOW);
+      }
+    };
     for (uint32_t j = 0; j < my_wins; j++) {
       const uint32_t tb = j % a.tb, lbuf = j % a.lb;
       if (tid == 0) {
@@ -744,75 +770,48 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
       const uint32_t *run_off = lists + (size_t)lbuf * list_words;
       const uint32_t *tab = run_off + kListHdr;
       const uint32_t wbase = (w_begin + j) * kBWin;
-      const unsigned long long thr0 = user_ok ? sm.thr_u[user] : ~0ull;
+      const unsigned long long thr0 = ok0 ? sm.thr_u[user0] : ~0ull;
+      const unsigned long long thr1 = ok1 ? sm.thr_u[user1] : ~0ull;
       for (uint32_t c = 0; c < n_ads_w; c += 32) {
         const uint32_t a0 = ad_lo + c;  // first window-local ad of this run
         const uint32_t run = a0 >> 5;
         const uint32_t rows = run_off[8 + run];
         const uint4 *t4 = reinterpret_cast<const uint4 *>(tab + run_off[run]);
-        float acc[32];
+        float2 acc[32];
 #pragma unroll
-        for (int i = 0; i < 32; i++) acc[i] = 0.f;
-        uint32_t r = 0;
-        for (; r + 2 <= rows; r += 2) {  // two rows: 64 independent loads in flight
-          float v0[32], v1[32];
-#pragma unroll
-          for (int i4 = 0; i4 < 8; i4++) {
-            const uint4 k = t4[r * 8 + i4];
-            v0[4 * i4 + 0] = __ldg(wcol + k.x);
-            v0[4 * i4 + 1] = __ldg(wcol + k.y);
-            v0[4 * i4 + 2] = __ldg(wcol + k.z);
-            v0[4 * i4 + 3] = __ldg(wcol + k.w);
-          }
-#pragma unroll
-          for (int i4 = 0; i4 < 8; i4++) {
-            const uint4 k = t4[(r + 1) * 8 + i4];
-            v1[4 * i4 + 0] = __ldg(wcol + k.x);
-            v1[4 * i4 + 1] = __ldg(wcol + k.y);
-            v1[4 * i4 + 2] = __ldg(wcol + k.z);
-            v1[4 * i4 + 3] = __ldg(wcol + k.w);
-          }
-#pragma unroll
-          for (int i = 0; i < 32; i++) acc[i] += v0[i] + v1[i];
-        }
-        if (r < rows) {
+        for (int i = 0; i < 32; i++) acc[i] = make_float2(0.f, 0.f);
+        for (uint32_t r = 0; r < rows; r++) {  // one row: 32 independent 8-byte loads
+          float2 v[32];
 #pragma unroll
           for (int i4 = 0; i4 < 8; i4++) {
             const uint4 k = t4[r * 8 + i4];
-            acc[4 * i4 + 0] += __ldg(wcol + k.x);
-            acc[4 * i4 + 1] += __ldg(wcol + k.y);
-            acc[4 * i4 + 2] += __ldg(wcol + k.z);
-            acc[4 * i4 + 3] += __ldg(wcol + k.w);
+            v[4 * i4 + 0] = __ldg(wcol + k.x);
+            v[4 * i4 + 1] = __ldg(wcol + k.y);
+            v[4 * i4 + 2] = __ldg(wcol + k.z);
+            v[4 * i4 + 3] = __ldg(wcol + k.w);
           }
+#pragma unroll
+          for (int i = 0; i < 32; i++) acc[i] = add_f32x2(acc[i], v[i]);
         }
         // lane i holds the row scale of the run's ad i (FP8)
         const uint32_t ad_l = wbase + a0 + lane;
         const float sa_l = F8 && ad_l < a.n_ads ? __ldg(a.ad_scale + ad_l) : 1.f;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
-          uint32_t dv[16];  // deep scores of 16 ads, one TMEM load
-          tmem_ld16(tl + tb * tcols + a0 + 16 * h, dv);
+          uint32_t d0[16], d1[16];  // deep scores of 16 ads for both users, two TMEM loads
+          tmem_ld16(tl + a0 + 16 * h, d0);
+          tmem_ld16(tl + 256u + a0 + 16 * h, d1);
           tmem_ld_wait();
 #pragma unroll
           for (int ii = 0; ii < 16; ii++) {
             const int i = 16 * h + ii;
-            const float sc = F8 ? __shfl_sync(0xffffffffu, sa_l, i) * u_sc : 1.f;
+            const float sa_i = F8 ? __shfl_sync(0xffffffffu, sa_l, i) : 1.f;
             const uint32_t ad = wbase + a0 + i;
-            if (!user_ok || ad >= a.n_ads) continue;
-            const float deep = F8 ? __uint_as_float(dv[ii]) * sc : __uint_as_float(dv[ii]);
-            const unsigned long long key = make_key(deep + acc[i], ad);
-            if (key < thr0) continue;
-            if (filt && !((__ldg(frow + (ad >> 6)) >> (ad & 63)) & 1ull)) continue;
-            const uint32_t pos = atomicAdd(&sm.cnt_u[user], 1u);
-            if (pos < a.cap_u) {
-              CandEntry ce;
-              ce.key = key;
-              ce.wide = acc[i];
-              ce.pad = 0;
-              ubuf[pos] = ce;
-            } else {
-              atomicOr(&a.ctrl->flags, DEVERR_OVERFLOW);
-            }
+            if (ad >= a.n_ads) continue;
+            const float deep0 = F8 ? __uint_as_float(d0[ii]) * (sa_i * usc0) : __uint_as_float(d0[ii]);
+            const float deep1 = F8 ? __uint_as_float(d1[ii]) * (sa_i * usc1) : __uint_as_float(d1[ii]);
+            if (ok0) offer(user0, filt0, frow0, ubuf0, thr0, deep0, acc[i].x, ad);
+            if (ok1) offer(user1, filt1, frow1, ubuf1, thr1, deep1, acc[i].y, ad);
           }
         }
       }
@@ -887,7 +886,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_batch_merge(
     const CandEntry *__restrict__ cand, const uint32_t *__restrict__ cand_n,
     const unsigned long long *__restrict__ cand_thr, uint32_t grid, uint32_t B, uint32_t cap_u,
     const uint32_t *__restrict__ kscan, const uint32_t *__restrict__ kout, uint32_t kmax,
-    const float *__restrict__ emb, uint32_t d, const float *__restrict__ h_u,
+    const float *__restrict__ emb, uint32_t d, const float *__restrict__ h_u, uint32_t half,
     uint64_t *__restrict__ scratch /* [B][kMergeCap + 8192] */, uint32_t *__restrict__ out_ids,
     float *__restrict__ out_scores, uint32_t *__restrict__ status /* [B] */) {
   extern __shared__ __align__(16) uint64_t s_v[];  // 8192 keys
@@ -901,7 +900,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_batch_merge(
   // 1. gather this user's candidates into scratch (bounded by 8192: with the
   //    per-CTA thresholds far fewer survive; beyond that the request is flagged)
   if (threadIdx.x == 0) s_cnt = 0;
-  for (uint32_t i = threadIdx.x; i < d; i += kMergeThreads) s_h[i] = h_u[(uint64_t)b * d + i];
+  const uint64_t hrow = user_row(b, half);  // the user table is in pair order
+  for (uint32_t i = threadIdx.x; i < d; i += kMergeThreads) s_h[i] = h_u[hrow * d + i];
   __syncthreads();
   // count first, then copy (entries of all CTAs, in CTA order)
   uint32_t total = 0;
@@ -1036,13 +1036,15 @@ struct ReqSrc {
 };
 constexpr uint32_t kStageWords = 8192;  // filter words per block of the gather
 
-// Block (b, y): request b's user vector, field values and field offsets
-// (y == 0) and words [y * kStageWords, +kStageWords) of its filter.  With
+// Block (b, y): request b's user vector (to row user_row(b, half)), field
+// values and field offsets (y == 0) and words [y * kStageWords, +kStageWords)
+// of its filter.  With
 // uptr set, the offsets are written (relative to the request's base, base[b]
 // beside them) after a check that they start at 0, do not decrease and end
 // at n; offsets that fail it are flagged and every field is left empty.
 __global__ void __launch_bounds__(256) k_stage_requests(const ReqSrc *__restrict__ src,
                                                         uint32_t d, uint32_t fu, uint32_t words,
+                                                        uint32_t half,
                                                         float *__restrict__ users,
                                                         uint32_t *__restrict__ vals,
                                                         uint32_t *__restrict__ uptr,
@@ -1053,7 +1055,8 @@ __global__ void __launch_bounds__(256) k_stage_requests(const ReqSrc *__restrict
   const uint32_t b = blockIdx.x;
   const ReqSrc r = src[b];
   if (blockIdx.y == 0) {
-    for (uint32_t t = threadIdx.x; t < d; t += blockDim.x) users[(size_t)b * d + t] = r.h_u[t];
+    const size_t row = (size_t)user_row(b, half);
+    for (uint32_t t = threadIdx.x; t < d; t += blockDim.x) users[row * d + t] = r.h_u[t];
     for (uint32_t t = threadIdx.x; t < r.n; t += blockDim.x) vals[(size_t)r.base + t] = r.vals[t];
     if (uptr) {
       if (threadIdx.x == 0) {
@@ -1103,9 +1106,10 @@ struct BatchPlan {
   size_t smem;
 };
 
-// Users per TMEM replica: the batch rounded up to 32, 64, 128 or 256.
+// Users of the M-tiles: the batch rounded up to 64, 128 or 256 (two tiles of
+// Bq/2 user pairs' halves each).
 static uint32_t users_pow2(uint32_t B) {
-  uint32_t q = 32;
+  uint32_t q = 64;
   while (q < B) q <<= 1;
   return q;
 }
@@ -1117,8 +1121,8 @@ static uint32_t users_pow2(uint32_t B) {
 static bool plan_smem(const ebr_index *ix, uint32_t B, BatchPlan *p) {
   p->Bq = users_pow2(B);
   p->list_cap = kBWin * ix->max_keys_per_ad;  // 8 runs x 32 ads x rows
-  const uint32_t n_mt = p->Bq > 128 ? 2 : 1;
-  p->tb = n_mt == 1 ? 2 : 1;
+  const uint32_t n_mt = 2;  // even and odd users: 512 TMEM columns per window
+  p->tb = 1;
   const uint32_t row_bytes = ix->d * (ix->dtype == EBR_FP8E4M3 ? 1u : 2u);
   p->tile_row = row_bytes >= 128 ? 128u : 64u;
   p->kb_n = row_bytes / p->tile_row;
@@ -1211,7 +1215,7 @@ static bool batch_sizes(const ebr_index *ix, const ebr_cross *cross, uint32_t B,
   z->req = (size_t)B * sizeof(ReqSrc);
   // after the words: the pointer table (device requests) or the packed user
   // vectors and field values (host requests)
-  z->host = host_table_off(B) + std::max(z->req, (size_t)B * d * 4 + z->user_ptr + z->user_vals);
+  z->host = host_table_off(B) + std::max(z->req, Bp * d * 4 + z->user_ptr + z->user_vals);
   return true;
 }
 
@@ -1332,27 +1336,27 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   // request inputs: device-resident requests are gathered by one kernel
   // through a table of their pointers; host requests are packed into the
   // pinned mirror and copied in two transfers (filters one per request)
-  if (Bp > B)
-    EBR_CUDA_TRY(cudaMemsetAsync((float *)w.users_f32.p + (size_t)B * d, 0,
-                                 (size_t)(Bp - B) * d * 4, st));
+  // user vectors in pair order (user_row); rows of absent users stay zero
+  if (Bp > B) EBR_CUDA_TRY(cudaMemsetAsync(w.users_f32.p, 0, (size_t)Bp * d * 4, st));
   bool any_filter = false;
   for (uint32_t b = 0; b < B; b++) any_filter |= q[b].filter != nullptr;
   uint32_t *d_uptr = multi ? (uint32_t *)w.user_ptr.p : nullptr;
   uint32_t *d_base = multi ? d_uptr + (size_t)B * (fu + 1) : nullptr;
   if (io == EBR_IO_HOST) {
-    // [user vectors B x d][offsets B x (f_u + 1)][base B][values], checked here
+    // [user vectors Bq x d, pair order][offsets B x (f_u + 1)][base B][values]
     float *hu = reinterpret_cast<float *>((char *)w.host + host_table_off(B));
-    uint32_t *hp = reinterpret_cast<uint32_t *>(hu + (size_t)B * d);
+    uint32_t *hp = reinterpret_cast<uint32_t *>(hu + (size_t)Bp * d);
     uint32_t *hv = hp + (size_t)B * (fu + 2);
+    if (Bp > B) memset(hu, 0, (size_t)Bp * d * 4);
     for (uint32_t b = 0; b < B; b++) {
-      memcpy(hu + (size_t)b * d, q[b].h_u, (size_t)d * 4);
+      memcpy(hu + (size_t)user_row(b, Bp / 2) * d, q[b].h_u, (size_t)d * 4);
       memcpy(hv + vbase[b], q[b].user_vals, (size_t)nv[b] * 4);
       if (!multi) continue;
       uint32_t *up = hp + (size_t)b * (fu + 1);
       for (uint32_t i = 0; i <= fu; i++) up[i] = q[b].user_ptr ? q[b].user_ptr[i] : i;
       hp[(size_t)B * (fu + 1) + b] = vbase[b];
     }
-    EBR_CUDA_TRY(cudaMemcpyAsync(w.users_f32.p, hu, (size_t)B * d * 4, cudaMemcpyHostToDevice, st));
+    EBR_CUDA_TRY(cudaMemcpyAsync(w.users_f32.p, hu, (size_t)Bp * d * 4, cudaMemcpyHostToDevice, st));
     if (multi)
       EBR_CUDA_TRY(cudaMemcpyAsync(d_uptr, hp, (size_t)B * (fu + 2) * 4, cudaMemcpyHostToDevice, st));
     EBR_CUDA_TRY(cudaMemcpyAsync(w.user_vals.p, hv, n_vals * 4, cudaMemcpyHostToDevice, st));
@@ -1366,7 +1370,7 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
     EBR_CUDA_TRY(cudaMemcpyAsync(w.req.p, tab, (size_t)B * sizeof(ReqSrc), cudaMemcpyHostToDevice,
                                  st));
     const uint32_t ys = any_filter ? (words + kStageWords - 1) / kStageWords : 1u;
-    k_stage_requests<<<dim3(B, ys), 256, 0, st>>>((const ReqSrc *)w.req.p, d, fu, words,
+    k_stage_requests<<<dim3(B, ys), 256, 0, st>>>((const ReqSrc *)w.req.p, d, fu, words, Bp / 2,
                                                   (float *)w.users_f32.p,
                                                   (uint32_t *)w.user_vals.p, d_uptr, d_base,
                                                   (uint64_t *)w.filters.p, &ctrl->flags);
@@ -1394,7 +1398,7 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   BatchArgs a;
   memset(&a, 0, sizeof(a));
   memcpy(&a.ta, w.tmap_bytes, sizeof(CUtensorMap));
-  EBR_TRY(make_tmap_2d(&a.tu, w.users_bf16.p, Bp, d, eb, std::min<uint32_t>(Bp, 128)));
+  EBR_TRY(make_tmap_2d(&a.tu, w.users_bf16.p, Bp, d, eb, Bp / 2));
   a.tile_row = pl.tile_row;
   a.kb_n = pl.kb_n;
   a.ad_scale = f8 ? (const float *)ix->emb_scale.p : nullptr;
@@ -1416,7 +1420,7 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   a.m = pl.m;
   a.cap_u = pl.cap_u;
   a.list_cap = pl.list_cap;
-  a.zero_row = ix->n_keys * Bp;
+  a.zero_row = ix->n_keys * (Bp / 2);  // in 8-byte pair units
   a.words = words;
   a.sa = pl.sa;
   a.lb = pl.lb;
@@ -1437,8 +1441,8 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   k_batch_merge<<<B, kMergeThreads, 8192 * 8, st>>>(
       (const CandEntry *)w.cand.p, (const uint32_t *)w.cand_n.p,
       (const unsigned long long *)w.cand_thr.p, (uint32_t)grid, B, pl.cap_u, kk, kk + B, kmax,
-      (const float *)ix->emb_f32.p, d, (const float *)w.users_f32.p, (uint64_t *)w.scratch.p,
-      d_ids, d_scores, status);
+      (const float *)ix->emb_f32.p, d, (const float *)w.users_f32.p, Bp / 2,
+      (uint64_t *)w.scratch.p, d_ids, d_scores, status);
   EBR_CUDA_TRY(cudaGetLastError());
   if (prof) {
     EBR_CUDA_TRY(cudaEventRecord(ev[3], st));
@@ -1468,7 +1472,7 @@ int batch_finish(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   for (uint32_t b = 0; b < B; b++) {
     if (!h_status[b]) continue;
     ebr_query dq = q[b];
-    dq.h_u = (const float *)w.users_f32.p + (size_t)b * d;
+    dq.h_u = (const float *)w.users_f32.p + (size_t)user_row(b, users_pow2(B) / 2) * d;
     dq.user_vals = (const uint32_t *)w.user_vals.p + vbase[b];
     // the checked offsets staged for the batch (device memory)
     dq.user_ptr = q[b].user_ptr ? (const uint32_t *)w.user_ptr.p + (size_t)b * (fu + 1) : nullptr;

@@ -148,6 +148,18 @@ __device__ __forceinline__ uint32_t warp_append(bool pred, uint32_t *counter) {
 struct CtaSync {
   __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
+// Two FP32 adds in one instruction (round to nearest even in each lane, as
+// two scalar adds).
+__device__ __forceinline__ float2 add_f32x2(float2 a, float2 b) {
+  uint64_t ra, rb, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
+}
+
 struct GroupSync {  // named barrier over the first `n` threads of the CTA
   int id, n;
   __device__ __forceinline__ void operator()() const { named_sync(id, n); }
