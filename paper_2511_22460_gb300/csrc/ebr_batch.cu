@@ -289,7 +289,8 @@ struct BatchArgs {
   const float *wT;             // [n_keys + 1][Bq] expanded weights, user-minor; last row 0
   const uint64_t *filters;     // [B][words] (rows of users without a filter are unused)
   const uint32_t *has_filter;  // [B]
-  uint32_t n_ads, n_win, B, Bq, d, m, cap_u, list_cap, words;
+  uint32_t n_ads, n_win, B, Bq, d, m, cap_u, list_cap, words;  // B: users (buffer stride)
+  const uint32_t *B_dev;       // non-null: the active users (<= B) are read here at launch
   uint32_t zero_row;           // n_keys * Bq / 2: the zero row of wT, in user-pair units
   uint32_t sa, lb, tb;         // A stages, list buffers, TMEM buffers
   uint32_t tile_row, kb_n;     // bytes per K-tile row (128 or 64), K-tiles per row
@@ -428,7 +429,7 @@ __device__ uint32_t warp_compact(CandEntry *buf, uint32_t n, uint64_t T) {
 // read once into registers: the eight digit passes then touch only the
 // shared-memory histogram, and the survivors are written back in one sweep.
 // Returns how many were kept; *T_out = the selected cut.
-constexpr int kSelNpl = 18;  // entries per lane of the register form (576 per buffer)
+constexpr int kSelNpl = 28;  // entries per lane of the register form (896 per buffer)
 template <int NPL>
 __device__ uint32_t warp_trim_regs(CandEntry *buf, uint32_t n, uint32_t need, uint32_t *hist,
                                    uint64_t *T_out) {
@@ -540,6 +541,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
   const uint32_t my_wins = w_end - w_begin;
   const uint32_t tcols = 256u * n_mt;  // TMEM columns per window
   const uint32_t ncols = 512;
+  // active users: all B, or the count a device-side loop wrote for this wave
+  // (the same for every thread; none: nothing to do, nothing allocated)
+  const uint32_t nB = a.B_dev ? min(*a.B_dev, a.B) : a.B;
+  if (nB == 0) return;
 
   for (uint32_t b = tid; b < a.B; b += kBatchThreads) {
     sm.cnt_u[b] = 0;
@@ -723,7 +728,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
     const uint32_t ad_lo = ((warp / 4) * (128 / U2) + q / (U2 / 32)) * U2, n_ads_w = U2;
     const uint32_t tl = tmem + ((32u * q) << 16);
     const uint32_t user0 = 2 * pair, user1 = 2 * pair + 1;
-    const bool ok0 = user0 < a.B, ok1 = user1 < a.B;
+    const bool ok0 = user0 < nB, ok1 = user1 < nB;
     // FP8: deep = TMEM x (user scale) x (the ad row's scale); user rows in pair order
     const float usc0 = F8 && ok0 ? a.user_scale[pair] : 1.f;
     const float usc1 = F8 && ok1 ? a.user_scale[U2 + pair] : 1.f;
@@ -822,7 +827,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
         mbar_arrive(&sm.l_empty[lbuf]);
       }
       // keep each user's buffer below capacity: exact top-m by radix select
-      for (uint32_t b = warp; b < a.B; b += kEpiWarps) {
+      for (uint32_t b = warp; b < nB; b += kEpiWarps) {
         const uint32_t n = sm.cnt_u[b];
         if (n + kBWin <= a.cap_u) continue;
         CandEntry *buf = a.cand + ((uint64_t)blockIdx.x * a.B + b) * a.cap_u;
@@ -840,7 +845,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_window(const __grid_
     gsync();
     // final trim to at most m candidates per user (the merge reads grid * m)
     if (!sm.stop_epi) {
-      for (uint32_t b = warp; b < a.B; b += kEpiWarps) {
+      for (uint32_t b = warp; b < nB; b += kEpiWarps) {
         const uint32_t n = min(sm.cnt_u[b], a.cap_u);
         if (n <= a.m) continue;
         CandEntry *buf = a.cand + ((uint64_t)blockIdx.x * a.B + b) * a.cap_u;
@@ -888,12 +893,22 @@ __global__ void __launch_bounds__(kMergeThreads) k_batch_merge(
     const uint32_t *__restrict__ kscan, const uint32_t *__restrict__ kout, uint32_t kmax,
     const float *__restrict__ emb, uint32_t d, const float *__restrict__ h_u, uint32_t half,
     uint64_t *__restrict__ scratch /* [B][kMergeCap + 8192] */, uint32_t *__restrict__ out_ids,
-    float *__restrict__ out_scores, uint32_t *__restrict__ status /* [B] */) {
+    float *__restrict__ out_scores, uint32_t *__restrict__ status /* [B] */,
+    const uint32_t *__restrict__ B_dev, const uint32_t *__restrict__ slot_dev,
+    uint64_t out_slot_stride, uint32_t status_slot_stride) {
   extern __shared__ __align__(16) uint64_t s_v[];  // 8192 keys
   __shared__ uint32_t s_hist[256], s_misc[8], s_cnt;
   __shared__ uint32_t s_base[1024];
   __shared__ float s_h[128];
   const uint32_t b = blockIdx.x;
+  // a device-side loop: only the wave's active users, results into its ring slot
+  if (B_dev && b >= *B_dev) return;
+  if (slot_dev) {
+    const uint32_t slot = *slot_dev;
+    out_ids += slot * out_slot_stride;
+    out_scores += slot * out_slot_stride;
+    status += (uint64_t)slot * status_slot_stride;
+  }
   const uint32_t ks = kscan[b], ko = kout[b];
   uint64_t *keys = scratch + (uint64_t)b * (kMergeCap + 8192);  // gathered approximate keys
   uint32_t inexact = 0;
@@ -1038,7 +1053,8 @@ constexpr uint32_t kStageWords = 8192;  // filter words per block of the gather
 
 // Block (b, y): request b's user vector (to row user_row(b, half)), field
 // values and field offsets (y == 0) and words [y * kStageWords, +kStageWords)
-// of its filter.  With
+// of its filter.  With B_dev (a device-side loop launching Bq blocks), blocks
+// past the wave's users zero their user row and stop.  With
 // uptr set, the offsets are written (relative to the request's base, base[b]
 // beside them) after a check that they start at 0, do not decrease and end
 // at n; offsets that fail it are flagged and every field is left empty.
@@ -1050,9 +1066,16 @@ __global__ void __launch_bounds__(256) k_stage_requests(const ReqSrc *__restrict
                                                         uint32_t *__restrict__ uptr,
                                                         uint32_t *__restrict__ base,
                                                         uint64_t *__restrict__ filters,
-                                                        uint32_t *__restrict__ flags) {
+                                                        uint32_t *__restrict__ flags,
+                                                        const uint32_t *__restrict__ B_dev) {
   __shared__ uint32_t s_ok;
   const uint32_t b = blockIdx.x;
+  if (B_dev && b >= *B_dev) {  // a device-side loop's wave has fewer users: zero the row
+    if (blockIdx.y == 0)
+      for (uint32_t t = threadIdx.x; t < d; t += blockDim.x)
+        users[(size_t)user_row(b, half) * d + t] = 0.f;
+    return;
+  }
   const ReqSrc r = src[b];
   if (blockIdx.y == 0) {
     const size_t row = (size_t)user_row(b, half);
@@ -1169,7 +1192,7 @@ static bool plan_batch(const ebr_index *ix, uint32_t B, uint32_t kscan_max, int 
   if (!plan_smem(ix, B, p)) return false;
   const uint32_t per_cta = (kscan_max + grid - 1) / grid;
   p->m = std::max<uint32_t>(64, (2 * per_cta + 32 + 31) / 32 * 32);
-  p->cap_u = 2 * p->m + kBWin;
+  p->cap_u = 4 * p->m + kBWin;  // a trim every 3m insertions at least
   return (uint64_t)grid * p->m <= kMergeCap;
 }
 
@@ -1373,7 +1396,7 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
     k_stage_requests<<<dim3(B, ys), 256, 0, st>>>((const ReqSrc *)w.req.p, d, fu, words, Bp / 2,
                                                   (float *)w.users_f32.p,
                                                   (uint32_t *)w.user_vals.p, d_uptr, d_base,
-                                                  (uint64_t *)w.filters.p, &ctrl->flags);
+                                                  (uint64_t *)w.filters.p, &ctrl->flags, nullptr);
     EBR_CUDA_TRY(cudaGetLastError());
     ix->launches += 1;
   }
@@ -1442,7 +1465,7 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
       (const CandEntry *)w.cand.p, (const uint32_t *)w.cand_n.p,
       (const unsigned long long *)w.cand_thr.p, (uint32_t)grid, B, pl.cap_u, kk, kk + B, kmax,
       (const float *)ix->emb_f32.p, d, (const float *)w.users_f32.p, Bp / 2,
-      (uint64_t *)w.scratch.p, d_ids, d_scores, status);
+      (uint64_t *)w.scratch.p, d_ids, d_scores, status, nullptr, nullptr, 0, 0);
   EBR_CUDA_TRY(cudaGetLastError());
   if (prof) {
     EBR_CUDA_TRY(cudaEventRecord(ev[3], st));

@@ -211,9 +211,10 @@ int launch_quantize_rows_fp8(const float *x, uint64_t n, uint32_t d, uint8_t *q,
 // Query expansion for a batch straight into user-minor layout wT[key][Bp].
 // uptr/base null: users[b * f_u + i]; else user b's field i holds
 // users[base[b] + uptr[b][i] .. base[b] + uptr[b][i + 1]) (checked offsets).
+// batch_dev (optional): the users of this wave, read on the device (<= batch).
 int expand_transposed(const ebr_cross *c, const uint32_t *users, const uint32_t *uptr,
                       const uint32_t *base, uint32_t batch, uint32_t Bp, float *wT,
-                      uint32_t *flags, cudaStream_t st);
+                      uint32_t *flags, cudaStream_t st, const uint32_t *batch_dev = nullptr);
 // Batched tensor-core path; returns EBR_EINVAL (nothing launched) when the
 // batch does not qualify, so the caller can fall back to per-request scans.
 bool batch_qualifies(const ebr_index *ix, const ebr_cross *cross, const ebr_query *q,

@@ -1082,8 +1082,12 @@ template <bool MULTI>
 __global__ void k_expand_T(CrossView cv, const uint32_t *__restrict__ users,
                            const uint32_t *__restrict__ uptr, const uint32_t *__restrict__ base,
                            uint32_t batch, uint32_t Bp, float *__restrict__ wT,
-                           uint32_t *__restrict__ flags) {
+                           uint32_t *__restrict__ flags, const uint32_t *__restrict__ batch_dev) {
   extern __shared__ uint32_t s_off2[];
+  if (batch_dev) {  // a device-side loop: this wave's users (none: nothing to expand)
+    batch = min(*batch_dev, batch);
+    if (batch == 0) return;
+  }
   for (uint32_t j = threadIdx.x; j <= cv.f_a; j += blockDim.x) s_off2[j] = cv.key_off[j];
   __syncthreads();
   const uint64_t total = (uint64_t)cv.n_keys * Bp;
@@ -1128,17 +1132,18 @@ __global__ void k_expand_T(CrossView cv, const uint32_t *__restrict__ users,
 
 int expand_transposed(const ebr_cross *c, const uint32_t *users, const uint32_t *uptr,
                       const uint32_t *base, uint32_t batch, uint32_t Bp, float *wT,
-                      uint32_t *flags, cudaStream_t st) {
+                      uint32_t *flags, cudaStream_t st, const uint32_t *batch_dev) {
   CrossView cv = cross_view(c);
   const uint64_t total = (uint64_t)cv.n_keys * Bp;
   uint64_t blocks = (total + 255) / 256;
   if (blocks > 65535) blocks = 65535;
   const size_t smem = (c->f_a + 1) * 4;
   if (uptr)
-    k_expand_T<true><<<(int)blocks, 256, smem, st>>>(cv, users, uptr, base, batch, Bp, wT, flags);
+    k_expand_T<true><<<(int)blocks, 256, smem, st>>>(cv, users, uptr, base, batch, Bp, wT, flags,
+                                                     batch_dev);
   else
     k_expand_T<false><<<(int)blocks, 256, smem, st>>>(cv, users, nullptr, nullptr, batch, Bp, wT,
-                                                      flags);
+                                                      flags, batch_dev);
   EBR_CUDA_TRY(cudaGetLastError());
   return EBR_OK;
 }
