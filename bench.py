@@ -490,7 +490,8 @@ def run_serving(args, device=0):
     ks = [int(x) for x in w.ks]
     reqs = [(np.ascontiguousarray(w.h_u[b]), np.ascontiguousarray(w.users[b]), ks[b],
              np.ascontiguousarray(w.filters[b])) for b in range(pool)]
-    srv = ebr.Server(ix, cross, max_batch=args.serve_batch, max_slots=4096, k_max=1000)
+    srv = ebr.Server(ix, cross, max_batch=args.serve_batch, max_slots=4096, k_max=1000,
+                     host_driven=args.serve_host_driven)
 
     def drive(rate, duration, keep=None):
         # one thread: submit every request whose arrival time has passed, then
@@ -582,6 +583,9 @@ def run_serving(args, device=0):
             "cross_pairs": int(len(w.pairs)), "k_choices": [100, 500, 1000],
             "filter_fraction": "U[0.01, 1] per request", "request_pool": pool,
             "max_batch": srv_stats.max_batch, "rates": rows,
+            "mode": ("host-driven pipelines" if args.serve_host_driven else
+                     "device-resident loop (one graph launch; WHILE node running waves)"),
+            "loop_launches": int(srv_stats.loop_launches),
             "max_req_per_s": best["req_per_s"],
             "recall": {"checked": len(rec), "min": float(min(rec)) if rec else None,
                        "definition": "|S_gpu & S_oracle| / K against the FP64 oracle, ids "
@@ -728,6 +732,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-host-driven", action="store_true",
+                    help="serve with the host-driven pipelines instead of the device-resident loop")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched BF16, FP8 single and FP8 batched lines")
     ap.add_argument("--extra-steps", type=int, default=10,

@@ -377,11 +377,17 @@ int ebr_profile_read(ebr_index *ix, ebr_profile *out);
  * concurrent users; the paper itself gives no serving design).
  *
  * ebr_submit copies a host request into a device-resident slot (the copy
- * runs on the server's copy stream) and queues it; a worker thread launches
- * whatever is queued, up to max_batch users, as one batched scan as soon as
- * one of its two pipelines is free, so a batch is being staged and launched
- * while the previous one is still on the GPU.  ebr_poll returns the result
- * once it is visible on the host.
+ * runs on the server's copy stream) and queues it.  By default (an index the
+ * batched scan takes, host_driven = 0) the waves run in a device-resident
+ * loop: one graph launch whose WHILE node, on the device, waits with a
+ * bounded poll for the next wave a worker thread posted (up to max_batch
+ * queued users, up to four waves ahead), stages it from its slots, runs the
+ * batched scan and merge and publishes the results; the loop leaves after
+ * about 0.2 s without work and is relaunched on demand.  With host_driven =
+ * 1 (and for FP32 indexes) the worker launches whatever is queued as one
+ * batched scan as soon as one of two pipelines is free, so a batch is being
+ * staged and launched while the previous one is still on the GPU.  ebr_poll
+ * returns the result once it is visible on the host.
  *
  * Admission is by device memory: every slot holds a request's inputs (user
  * vector, user field values, targeting bitmap) in HBM, and the slots plus the
@@ -399,6 +405,8 @@ typedef struct {
   uint32_t queue_timeout_ms;  /* a request still queued after this long fails with EBR_ETIMEDOUT (0: never) */
   uint32_t max_user_vals;     /* user field values one request may carry, multi-valued (user_ptr)
                                  requests included; sizes every slot (0: 8 * f_u) */
+  uint32_t host_driven;       /* 1: the worker thread launches every batch on two pipelines;
+                                 0: the device-resident loop (indexes the batched scan takes) */
 } ebr_server_cfg;
 
 typedef struct {
@@ -409,6 +417,7 @@ typedef struct {
   uint64_t slot_bytes;              /* device bytes of one request slot */
   double launch_ms, finish_ms;      /* worker host time staging+launching / waiting+publishing */
   uint64_t index_swaps;             /* indexes swapped in by ebr_server_swap_index */
+  uint64_t loop_launches;           /* launches of the device-resident loop (it leaves when idle) */
 } ebr_server_stats;
 
 /*

@@ -1292,6 +1292,57 @@ static int stage(void *dst, const void *src, size_t bytes, int io, cudaStream_t 
   return EBR_OK;
 }
 
+// The window kernel's arguments for a batch of B users (B: the candidate
+// buffers' user stride; B_dev: the active users, read on the device, or null).
+static int fill_batch_args(ebr_index *ix, uint32_t B, const BatchPlan &pl, BatchWs &w,
+                           const uint32_t *has_filter, Ctrl *ctrl, const uint32_t *B_dev,
+                           BatchArgs *out) {
+  const bool f8 = ix->dtype == EBR_FP8E4M3;
+  const uint32_t eb = f8 ? 1u : 2u, d = ix->d, Bp = pl.Bq;
+  if (!w.tmap_ready || w.tmap_for != ix->emb_q.p) {
+    EBR_TRY(make_tmap_2d(reinterpret_cast<CUtensorMap *>(w.tmap_bytes), ix->emb_q.p, ix->n_ads, d,
+                         eb, 128));
+    w.tmap_ready = true;
+    w.tmap_for = ix->emb_q.p;
+  }
+  BatchArgs &a = *out;
+  memset(&a, 0, sizeof(a));
+  memcpy(&a.ta, w.tmap_bytes, sizeof(CUtensorMap));
+  EBR_TRY(make_tmap_2d(&a.tu, w.users_bf16.p, Bp, d, eb, Bp / 2));
+  a.tile_row = pl.tile_row;
+  a.kb_n = pl.kb_n;
+  a.ad_scale = f8 ? (const float *)ix->emb_scale.p : nullptr;
+  a.user_scale = f8 ? (const float *)w.users_scale.p : nullptr;
+  for (int g = 0; g < kGroups; g++) {
+    a.wkey[g] = ix->wkey[g];
+    a.wvals[g] = ix->wvals[g];
+    a.win_ptr[g] = ix->win_ptr[g];
+  }
+  a.ad_nkeys = (const uint16_t *)ix->ad_nkeys.p;
+  a.wT = (const float *)w.wT.p;
+  a.filters = (const uint64_t *)w.filters.p;
+  a.has_filter = has_filter;
+  a.n_ads = ix->n_ads;
+  a.n_win = ix->n_win;
+  a.B = B;
+  a.B_dev = B_dev;
+  a.Bq = Bp;
+  a.d = d;
+  a.m = pl.m;
+  a.cap_u = pl.cap_u;
+  a.list_cap = pl.list_cap;
+  a.zero_row = ix->n_keys * (Bp / 2);  // in 8-byte pair units
+  a.words = (ix->n_ads + 63) / 64;
+  a.sa = pl.sa;
+  a.lb = pl.lb;
+  a.tb = pl.tb;
+  a.cand = (CandEntry *)w.cand.p;
+  a.cand_n = (uint32_t *)w.cand_n.p;
+  a.cand_thr = (unsigned long long *)w.cand_thr.p;
+  a.ctrl = ctrl;
+  return EBR_OK;
+}
+
 // Stages the batch's requests into w, launches expansion, the window scan and
 // the merge on st, and queues the copies of the per-user status and the
 // control block to w's pinned mirror.  Nothing here waits for the device.
@@ -1410,48 +1461,8 @@ int batch_launch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint
   EBR_TRY(expand_transposed(cross, (const uint32_t *)w.user_vals.p, d_uptr, d_base, B, Bp,
                             (float *)w.wT.p, &ctrl->flags, st));
   EBR_CUDA_TRY(cudaMemsetAsync((float *)w.wT.p + (size_t)ix->n_keys * Bp, 0, (size_t)Bp * 4, st));
-  // tensor maps
-  const uint32_t eb = f8 ? 1u : 2u;
-  if (!w.tmap_ready || w.tmap_for != ix->emb_q.p) {
-    EBR_TRY(make_tmap_2d(reinterpret_cast<CUtensorMap *>(w.tmap_bytes), ix->emb_q.p, ix->n_ads, d,
-                         eb, 128));
-    w.tmap_ready = true;
-    w.tmap_for = ix->emb_q.p;
-  }
   BatchArgs a;
-  memset(&a, 0, sizeof(a));
-  memcpy(&a.ta, w.tmap_bytes, sizeof(CUtensorMap));
-  EBR_TRY(make_tmap_2d(&a.tu, w.users_bf16.p, Bp, d, eb, Bp / 2));
-  a.tile_row = pl.tile_row;
-  a.kb_n = pl.kb_n;
-  a.ad_scale = f8 ? (const float *)ix->emb_scale.p : nullptr;
-  a.user_scale = f8 ? (const float *)w.users_scale.p : nullptr;
-  for (int g = 0; g < kGroups; g++) {
-    a.wkey[g] = ix->wkey[g];
-    a.wvals[g] = ix->wvals[g];
-    a.win_ptr[g] = ix->win_ptr[g];
-  }
-  a.ad_nkeys = (const uint16_t *)ix->ad_nkeys.p;
-  a.wT = (const float *)w.wT.p;
-  a.filters = (const uint64_t *)w.filters.p;
-  a.has_filter = has_filter;
-  a.n_ads = ix->n_ads;
-  a.n_win = ix->n_win;
-  a.B = B;
-  a.Bq = Bp;
-  a.d = d;
-  a.m = pl.m;
-  a.cap_u = pl.cap_u;
-  a.list_cap = pl.list_cap;
-  a.zero_row = ix->n_keys * (Bp / 2);  // in 8-byte pair units
-  a.words = words;
-  a.sa = pl.sa;
-  a.lb = pl.lb;
-  a.tb = pl.tb;
-  a.cand = (CandEntry *)w.cand.p;
-  a.cand_n = (uint32_t *)w.cand_n.p;
-  a.cand_thr = (unsigned long long *)w.cand_thr.p;
-  a.ctrl = ctrl;
+  EBR_TRY(fill_batch_args(ix, B, pl, w, has_filter, ctrl, nullptr, &a));
   auto kern = f8 ? k_batch_window<true> : k_batch_window<false>;
   EBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)pl.smem));
@@ -1540,6 +1551,304 @@ int query_batch(ebr_index *ix, const ebr_cross *cross, const ebr_query *q, uint3
     EBR_CUDA_TRY(
         cudaMemcpyAsync(out_scores, d_scores, (size_t)B * kmax * 4, cudaMemcpyDeviceToHost, st));
     EBR_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  return EBR_OK;
+}
+
+// =====================================================================
+// Device-resident serving loop
+// =====================================================================
+// Wave descriptor (one ring slot, written by the host, copied to `cur` by
+// the fetch kernel): [B, pad x3][kscan Bmax][kout Bmax][has_filter Bmax]
+// [ReqSrc Bmax, 16-byte aligned].
+static size_t desc_src_off(uint32_t Bmax) { return (16 + (size_t)12 * Bmax + 15) / 16 * 16; }
+static size_t desc_bytes_for(uint32_t Bmax) {
+  return (desc_src_off(Bmax) + (size_t)Bmax * sizeof(ReqSrc) + 15) / 16 * 16;
+}
+
+struct LoopArgs {
+  LoopShared *sh;              // mapped host words
+  const uint8_t *desc;         // mapped [R][desc_bytes]
+  uint32_t *flags_out;         // mapped [R]
+  uint32_t *status_out;        // mapped [R][Bmax]
+  uint8_t *cur;                // device copy of the current descriptor
+  uint32_t *slot;
+  unsigned long long *seq, *idle_ns;
+  Ctrl *ctrl;
+  uint32_t *status;            // [R][Bmax]
+  uint32_t R, Bmax, desc_bytes;
+  unsigned long long poll_ns, idle_exit_ns;
+  cudaGraphConditionalHandle handle;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const volatile unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys(volatile unsigned long long *p,
+                                               unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// First node of the loop body.  Thread 0 waits, for at most poll_ns, for a
+// wave the host posted whose result slot the host has freed, or for stop.
+// A wave: its descriptor is copied into `cur` and its control block and
+// status zeroed.  No wave: cur.B = 0 (every later node of this iteration
+// returns at once), and after idle_exit_ns without a wave, or on stop, the
+// loop's condition is cleared so that this iteration is the last.
+__global__ void __launch_bounds__(256) k_loop_fetch(LoopArgs a) {
+  __shared__ uint32_t s_state, s_slot;
+  if (threadIdx.x == 0) {
+    const unsigned long long seq = *a.seq;
+    const uint64_t t0 = global_timer_ns();
+    uint32_t st = 0;  // 0: no wave, 1: a wave, 2: leave the loop
+    for (;;) {
+      if (a.sh->stop) {
+        st = 2;
+        break;
+      }
+      const unsigned long long posted = ld_acquire_sys(&a.sh->posted);
+      if (posted > seq && seq < a.sh->freed + a.R) {
+        st = 1;
+        break;
+      }
+      if (global_timer_ns() - t0 >= a.poll_ns) break;
+      __nanosleep(1000);
+    }
+    if (st == 0) {
+      *a.idle_ns += global_timer_ns() - t0;
+      if (*a.idle_ns >= a.idle_exit_ns) st = 2;
+    } else if (st == 1) {
+      *a.idle_ns = 0;
+    }
+    if (st == 2) cudaGraphSetConditional(a.handle, 0u);
+    s_state = st;
+    s_slot = (uint32_t)(seq % a.R);
+    *a.slot = s_slot;
+  }
+  __syncthreads();
+  if (s_state != 1) {
+    if (threadIdx.x == 0) *reinterpret_cast<uint32_t *>(a.cur) = 0u;
+    return;
+  }
+  const volatile uint32_t *src =
+      reinterpret_cast<const volatile uint32_t *>(a.desc + (size_t)s_slot * a.desc_bytes);
+  uint32_t *dst = reinterpret_cast<uint32_t *>(a.cur);
+  for (uint32_t i = threadIdx.x; i < a.desc_bytes / 4; i += blockDim.x) dst[i] = src[i];
+  for (uint32_t i = threadIdx.x; i < sizeof(Ctrl) / 4; i += blockDim.x)
+    reinterpret_cast<uint32_t *>(a.ctrl)[i] = 0u;
+  for (uint32_t i = threadIdx.x; i < a.Bmax; i += blockDim.x) a.status[s_slot * a.Bmax + i] = 0u;
+}
+
+// Last node of the loop body: a wave's flags and per-user status go to the
+// mapped result words, then (system-scope release) done = waves finished.
+__global__ void k_loop_publish(LoopArgs a) {
+  const uint32_t B = *reinterpret_cast<const uint32_t *>(a.cur);
+  if (B == 0) return;
+  const uint32_t slot = *a.slot;
+  for (uint32_t b = threadIdx.x; b < B; b += blockDim.x)
+    a.status_out[slot * a.Bmax + b] = a.status[slot * a.Bmax + b];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.flags_out[slot] = a.ctrl->flags;
+    __threadfence_system();
+    const unsigned long long seq = *a.seq + 1;
+    *a.seq = seq;
+    st_release_sys(&a.sh->done, seq);
+  }
+}
+
+static void loop_dev_sizes(uint32_t R, uint32_t Bmax, uint32_t kmax, size_t *cur_b, size_t *st_b,
+                           size_t *out_b, size_t *ctl_b) {
+  *cur_b = (desc_bytes_for(Bmax) + 255) / 256 * 256;
+  *st_b = ((size_t)R * Bmax * 4 + 255) / 256 * 256;
+  *out_b = ((size_t)R * Bmax * kmax * 4 + 255) / 256 * 256;
+  *ctl_b = (256 + sizeof(Ctrl) + 255) / 256 * 256;
+}
+
+size_t loop_dev_bytes(uint32_t Bmax, uint32_t kmax) {
+  size_t cur_b, st_b, out_b, ctl_b;
+  loop_dev_sizes(LoopBufs{}.R, Bmax, kmax, &cur_b, &st_b, &out_b, &ctl_b);
+  return cur_b + st_b + 2 * out_b + ctl_b;
+}
+
+int loop_alloc(LoopBufs &L, uint32_t Bmax, uint32_t kmax) {
+  L.Bmax = Bmax;
+  L.kmax = kmax;
+  L.desc_bytes = (uint32_t)desc_bytes_for(Bmax);
+  const size_t sh_b = 256, desc_b = (size_t)L.R * L.desc_bytes, fl_b = (size_t)L.R * 4;
+  const size_t host_b = sh_b + desc_b + fl_b + (size_t)L.R * Bmax * 4;
+  if (cudaHostAlloc(&L.host, host_b, cudaHostAllocMapped) != cudaSuccess) {
+    cudaGetLastError();
+    L.host = nullptr;
+    set_error("serving loop: mapped host allocation of %zu bytes failed", host_b);
+    return EBR_ENOMEM;
+  }
+  memset(L.host, 0, host_b);
+  void *dp = nullptr;
+  EBR_CUDA_TRY(cudaHostGetDevicePointer(&dp, L.host, 0));
+  if (dp != L.host) {  // every pointer below is used on both sides
+    set_error("serving loop: mapped host memory has a different device address");
+    return EBR_EINVAL;
+  }
+  uint8_t *h = (uint8_t *)L.host;
+  L.sh = (LoopShared *)h;
+  L.desc = h + sh_b;
+  L.flags_out = (uint32_t *)(h + sh_b + desc_b);
+  L.status_out = (uint32_t *)(h + sh_b + desc_b + fl_b);
+  size_t cur_b, st_b, out_b, ctl_b;
+  loop_dev_sizes(L.R, Bmax, kmax, &cur_b, &st_b, &out_b, &ctl_b);
+  EBR_TRY(dev_alloc(L.dev, cur_b + st_b + 2 * out_b + ctl_b));
+  uint8_t *d = (uint8_t *)L.dev.p;
+  L.cur = d;
+  L.status = (uint32_t *)(d + cur_b);
+  L.out_ids = (uint32_t *)(d + cur_b + st_b);
+  L.out_scores = (float *)(d + cur_b + st_b + out_b);
+  uint8_t *c = d + cur_b + st_b + 2 * out_b;
+  L.slot = (uint32_t *)c;
+  L.seq = (unsigned long long *)(c + 8);
+  L.idle_ns = (unsigned long long *)(c + 16);
+  L.ctrl = (Ctrl *)(c + 256);
+  EBR_CUDA_TRY(cudaMemset(L.dev.p, 0, L.dev.bytes));
+  return EBR_OK;
+}
+
+void loop_free(LoopBufs &L) {
+  if (L.exec) cudaGraphExecDestroy(L.exec);
+  L.exec = nullptr;
+  dev_free(L.dev);
+  if (L.host) cudaFreeHost(L.host);
+  L.host = nullptr;
+}
+
+int loop_fill(LoopBufs &L, uint64_t wave, const ebr_index *ix, const ebr_cross *cross,
+              const ebr_query *q, uint32_t B) {
+  if (B == 0 || B > L.Bmax) {
+    set_error("serving loop: a wave of %u users (at most %u)", B, L.Bmax);
+    return EBR_EINVAL;
+  }
+  uint8_t *p = L.desc + (size_t)(wave % L.R) * L.desc_bytes;
+  uint32_t *w32 = (uint32_t *)p;
+  w32[0] = B;
+  uint32_t *ks = (uint32_t *)(p + 16), *ko = ks + L.Bmax, *hf = ko + L.Bmax;
+  ReqSrc *src = (ReqSrc *)(p + desc_src_off(L.Bmax));
+  uint32_t base = 0;
+  for (uint32_t b = 0; b < B; b++) {
+    ks[b] = std::min<uint32_t>(q[b].k * ix->rescore_mult, ix->n_ads);
+    ko[b] = q[b].k;
+    hf[b] = q[b].filter ? 1u : 0u;
+    const uint32_t n = q[b].user_ptr ? q[b].n_user_vals : cross->f_u;
+    src[b] = ReqSrc{q[b].h_u, q[b].user_vals, q[b].filter, q[b].user_ptr, n, base};
+    base += n;
+  }
+  return EBR_OK;
+}
+
+// Captures the loop body for index ix into a WHILE node and instantiates
+// it.  The batch plan is fixed for Bmax users and K up to L.kmax.
+int loop_build(ebr_index *ix, const ebr_cross *cross, uint32_t max_user_vals, BatchWs &w,
+               LoopBufs &L, cudaStream_t st) {
+  if (L.exec) {
+    cudaGraphExecDestroy(L.exec);
+    L.exec = nullptr;
+  }
+  const uint32_t Bmax = L.Bmax, d = ix->d, fu = cross->f_u, words = (ix->n_ads + 63) / 64;
+  const uint32_t kscan_max = std::min<uint32_t>(L.kmax * ix->rescore_mult, ix->n_ads);
+  EBR_TRY(batch_ws_reserve(ix, cross, Bmax, kscan_max, (uint64_t)Bmax * max_user_vals, w));
+  BatchSizes z;
+  batch_sizes(ix, cross, Bmax, kscan_max, (uint64_t)Bmax * max_user_vals, &z);
+  const BatchPlan pl = z.pl;
+  const uint32_t Bp = pl.Bq;
+  const bool f8 = ix->dtype == EBR_FP8E4M3;
+  uint8_t *cur = L.cur;
+  const uint32_t *B_dev = (const uint32_t *)cur;
+  const uint32_t *ks = (const uint32_t *)(cur + 16), *ko = ks + Bmax, *hf = ko + Bmax;
+  const ReqSrc *srcs = (const ReqSrc *)(cur + desc_src_off(Bmax));
+  uint32_t *d_uptr = (uint32_t *)w.user_ptr.p;
+  uint32_t *d_base = d_uptr + (size_t)Bmax * (fu + 1);
+  BatchArgs ba;
+  EBR_TRY(fill_batch_args(ix, Bmax, pl, w, hf, L.ctrl, B_dev, &ba));
+  auto kern = f8 ? k_batch_window<true> : k_batch_window<false>;
+  EBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)pl.smem));
+  EBR_CUDA_TRY(cudaFuncSetAttribute(k_batch_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    8192 * 8));
+  cudaGraph_t g = nullptr;
+  EBR_CUDA_TRY(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    set_error("serving loop: conditional graph node: %s", cudaGetErrorString(e));
+    return EBR_ECUDA;
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  LoopArgs la;
+  la.sh = L.sh;
+  la.desc = L.desc;
+  la.flags_out = L.flags_out;
+  la.status_out = L.status_out;
+  la.cur = cur;
+  la.slot = L.slot;
+  la.seq = L.seq;
+  la.idle_ns = L.idle_ns;
+  la.ctrl = L.ctrl;
+  la.status = L.status;
+  la.R = L.R;
+  la.Bmax = Bmax;
+  la.desc_bytes = L.desc_bytes;
+  la.poll_ns = L.poll_ns;
+  la.idle_exit_ns = L.idle_exit_ns;
+  la.handle = h;
+  e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  int rc = EBR_OK;
+  if (e == cudaSuccess) {
+    const uint32_t ys = (words + kStageWords - 1) / kStageWords;
+    k_loop_fetch<<<1, 256, 0, st>>>(la);
+    k_stage_requests<<<dim3(Bp, ys), 256, 0, st>>>(srcs, d, fu, words, Bp / 2,
+                                                   (float *)w.users_f32.p,
+                                                   (uint32_t *)w.user_vals.p, d_uptr, d_base,
+                                                   (uint64_t *)w.filters.p, &L.ctrl->flags, B_dev);
+    if (f8)
+      rc = launch_quantize_rows_fp8((const float *)w.users_f32.p, Bp, d,
+                                    (uint8_t *)w.users_bf16.p, (float *)w.users_scale.p, st);
+    else
+      rc = launch_quantize((const float *)w.users_f32.p, (uint64_t)Bp * d, EBR_BF16,
+                           w.users_bf16.p, st);
+    if (rc == EBR_OK)
+      rc = expand_transposed(cross, (const uint32_t *)w.user_vals.p, d_uptr, d_base, Bmax, Bp,
+                             (float *)w.wT.p, &L.ctrl->flags, st, B_dev);
+    if (rc == EBR_OK) {
+      cudaMemsetAsync((float *)w.wT.p + (size_t)ix->n_keys * Bp, 0, (size_t)Bp * 4, st);
+      kern<<<z.grid, kBatchThreads, pl.smem, st>>>(ba);
+      k_batch_merge<<<Bmax, kMergeThreads, 8192 * 8, st>>>(
+          (const CandEntry *)w.cand.p, (const uint32_t *)w.cand_n.p,
+          (const unsigned long long *)w.cand_thr.p, (uint32_t)z.grid, Bmax, pl.cap_u, ks, ko,
+          L.kmax, (const float *)ix->emb_f32.p, d, (const float *)w.users_f32.p, Bp / 2,
+          (uint64_t *)w.scratch.p, L.out_ids, L.out_scores, L.status, B_dev, L.slot,
+          (uint64_t)Bmax * L.kmax, Bmax);
+      k_loop_publish<<<1, 256, 0, st>>>(la);
+    }
+    cudaGraph_t cap = nullptr;
+    e = cudaStreamEndCapture(st, &cap);
+  }
+  if (e == cudaSuccess && rc == EBR_OK) e = cudaGraphInstantiate(&L.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (rc != EBR_OK) return rc;
+  if (e != cudaSuccess) {
+    L.exec = nullptr;
+    set_error("serving loop: graph capture: %s", cudaGetErrorString(e));
+    return EBR_ECUDA;
   }
   return EBR_OK;
 }

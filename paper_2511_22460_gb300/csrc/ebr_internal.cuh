@@ -110,6 +110,48 @@ void batch_ws_free(BatchWs &w);
 inline size_t small_status_off(uint32_t B) { return ((size_t)3 * B * 4 + 127) / 128 * 128; }
 inline size_t small_bytes(uint32_t B) { return small_status_off(B) + (size_t)B * 4; }
 
+// ------------------------------------------- device-resident serving loop
+// One graph launch that runs waves of the batched scan back to back: a
+// conditional WHILE node whose body fetches the next posted wave (a bounded
+// wait on host-written words), stages it, scans it, merges it into a ring
+// slot of results and publishes it; the loop leaves when told to stop or
+// after idle_exit_ns without work (the host relaunches it on demand).
+struct LoopShared {                     // pinned host memory mapped into the device
+  volatile unsigned long long posted;   // host: waves posted
+  volatile unsigned long long freed;    // host: waves whose results the host has taken
+  volatile unsigned long long done;     // device: waves finished
+  volatile uint32_t stop;               // host: leave the loop at the next poll
+  uint32_t pad[9];
+};
+struct LoopBufs {
+  uint32_t R = 4, Bmax = 0, kmax = 0, desc_bytes = 0;
+  void *host = nullptr;           // pinned, mapped: LoopShared, descriptors [R], flags [R], status [R][Bmax]
+  LoopShared *sh = nullptr;
+  uint8_t *desc = nullptr;        // [R][desc_bytes] wave descriptors (host-written)
+  uint32_t *flags_out = nullptr;  // [R] device error flags of each wave (device-written)
+  uint32_t *status_out = nullptr; // [R][Bmax] per-user "not proven exact" (device-written)
+  DevBuf dev;                     // the device-side state below, one allocation
+  uint8_t *cur = nullptr;         // the current wave's descriptor (device copy)
+  uint32_t *slot = nullptr;       // its ring slot
+  unsigned long long *seq = nullptr, *idle_ns = nullptr;
+  uint32_t *status = nullptr;     // [R][Bmax] written by the merge
+  uint32_t *out_ids = nullptr;    // [R][Bmax][kmax]
+  float *out_scores = nullptr;    // [R][Bmax][kmax]
+  Ctrl *ctrl = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t poll_ns = 2000000ull, idle_exit_ns = 200000000ull;
+};
+int loop_alloc(LoopBufs &L, uint32_t Bmax, uint32_t kmax);
+size_t loop_dev_bytes(uint32_t Bmax, uint32_t kmax);  // the device memory loop_alloc takes
+void loop_free(LoopBufs &L);
+// (Re)builds L's graph for index ix; w is the loop's batch workspace.
+int loop_build(ebr_index *ix, const ebr_cross *cross, uint32_t max_user_vals, BatchWs &w,
+               LoopBufs &L, cudaStream_t st);
+// Writes wave `wave`'s descriptor (ring slot wave % R) from B requests
+// whose arrays are device pointers (user_ptr optional).
+int loop_fill(LoopBufs &L, uint64_t wave, const ebr_index *ix, const ebr_cross *cross,
+              const ebr_query *q, uint32_t B);
+
 }  // namespace ebr
 
 struct ebr_index {

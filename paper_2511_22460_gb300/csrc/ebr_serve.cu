@@ -1,16 +1,25 @@
 // Continuous-batching request loop (ebr_server_*, ebr_submit, ebr_poll).
 //
 // Requests arrive on any host thread and are copied into device-resident
-// slots on a copy stream.  One worker thread owns the GPU side: it keeps two
-// pipelines (workspace + stream each) and, whenever one is free and requests
-// are queued, launches all of them (up to max_batch) as one batched scan;
-// otherwise it finishes the oldest pipeline in flight and publishes its
-// results.  Requests that arrive while a batch is on the GPU therefore join
-// the next batch, which is staged and launched before the running one is
-// finished.  Admission is by device memory: the slots and both workspaces are
-// allocated up front from the HBM budget, and a submit finding no free slot
-// is refused.
+// slots on a copy stream.  Two ways of running them:
+//  - the device-resident loop (default for indexes the batched scan takes):
+//    one graph launch whose conditional WHILE node runs waves back to back
+//    on the device.  Each iteration waits (bounded, on host-written words in
+//    mapped memory) for the next wave the worker thread posted, stages the
+//    wave's requests from their slots, runs the batched scan and merge into
+//    a ring slot of results and publishes it.  The worker thread only posts
+//    waves (up to max_batch queued requests each, up to four waves ahead)
+//    and takes finished ones back; the loop leaves after a while without
+//    work and is relaunched on demand;
+//  - host-driven pipelines: the worker thread keeps two pipelines (workspace
+//    + stream each) and launches all queued requests (up to max_batch) as
+//    one batched scan whenever one is free, finishing the oldest otherwise.
+// Either way, requests that arrive while others are on the GPU join the
+// next wave.  Admission is by device memory: the slots and the workspaces
+// are allocated up front from the HBM budget, and a submit finding no free
+// slot is refused.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -109,6 +118,18 @@ struct ebr_server {
   std::vector<float> lat;  // ring of latencies (ms)
   uint64_t lat_n = 0;
   std::deque<uint64_t> finished;  // tickets not yet reported by ebr_server_completed
+  // device-resident loop (loop_mode): one graph launch runs the waves
+  bool loop_mode = false;
+  LoopBufs loop;
+  BatchWs loop_ws;
+  cudaStream_t loop_st = nullptr, res_st = nullptr;
+  cudaEvent_t loop_end = nullptr;
+  bool loop_running = false;
+  uint64_t loop_posted = 0, loop_done = 0;   // waves posted / taken back (worker thread only)
+  std::vector<std::vector<int>> wave_slots;  // [R] slots of each wave in flight
+  std::vector<std::vector<ebr_query>> wave_qs;
+  uint32_t *h_wave_ids = nullptr;            // pinned [Bmax][k_max]
+  float *h_wave_scores = nullptr;
 };
 
 namespace ebr {
@@ -200,6 +221,25 @@ int pipe_finish(ebr_server *s, int p) {
   return EBR_OK;
 }
 
+void shed_timed_out(ebr_server *s) {  // under s->mu
+  if (!s->timeout_ms || s->queue.empty()) return;
+  const double t = now_s();
+  std::deque<int> keep;
+  for (int i : s->queue) {
+    Slot &sl = s->slots[i];
+    if ((t - sl.t_submit) * 1e3 > s->timeout_ms) {
+      sl.state = kFailed;
+      sl.rc = EBR_ETIMEDOUT;
+      sl.err = "ebr_server: request waited longer than queue_timeout_ms";
+      s->st.failed += 1;
+      s->finished.push_back(sl.ticket);
+    } else {
+      keep.push_back(i);
+    }
+  }
+  s->queue.swap(keep);
+}
+
 void worker_main(ebr_server *s) {
   cudaSetDevice(s->device);
   std::deque<int> inflight;  // pipes in launch order
@@ -209,23 +249,7 @@ void worker_main(ebr_server *s) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
       if (s->stop) break;
-      if (s->timeout_ms && !s->queue.empty()) {  // shed requests that waited too long
-        const double t = now_s();
-        std::deque<int> keep;
-        for (int i : s->queue) {
-          Slot &sl = s->slots[i];
-          if ((t - sl.t_submit) * 1e3 > s->timeout_ms) {
-            sl.state = kFailed;
-            sl.rc = EBR_ETIMEDOUT;
-            sl.err = "ebr_server: request waited longer than queue_timeout_ms";
-            s->st.failed += 1;
-            s->finished.push_back(sl.ticket);
-          } else {
-            keep.push_back(i);
-          }
-        }
-        s->queue.swap(keep);
-      }
+      shed_timed_out(s);
       if (s->swap_req && inflight.empty()) {  // no batch uses the old index any more
         s->ix = s->next_ix;
         s->next_ix = nullptr;
@@ -280,6 +304,219 @@ void worker_main(ebr_server *s) {
   }
 }
 
+// ------------------------------------------------- device-resident loop
+// The worker posts waves (up to max_batch queued requests each) into the
+// loop's descriptor ring and takes finished waves back; the device runs them
+// back to back inside one graph launch, relaunched only after the loop left
+// on its own for want of work.
+
+// (Re)launches the loop graph unless it is running.
+int loop_ensure_running(ebr_server *s) {
+  if (s->loop_running) {
+    const cudaError_t q = cudaEventQuery(s->loop_end);
+    if (q == cudaErrorNotReady) return EBR_OK;
+    s->loop_running = false;
+    if (q != cudaSuccess) {
+      set_error("ebr_server (device loop): %s", cudaGetErrorString(q));
+      return EBR_ECUDA;
+    }
+  }
+  EBR_CUDA_TRY(cudaMemsetAsync(s->loop.idle_ns, 0, sizeof(unsigned long long), s->loop_st));
+  EBR_CUDA_TRY(cudaGraphLaunch(s->loop.exec, s->loop_st));
+  EBR_CUDA_TRY(cudaEventRecord(s->loop_end, s->loop_st));
+  s->loop_running = true;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->st.loop_launches += 1;
+  return EBR_OK;
+}
+
+// Asks the running loop to leave and waits for it (its polls are bounded,
+// so it leaves within one wave plus one poll period).
+void loop_stop(ebr_server *s) {
+  if (!s->loop_running) return;
+  s->loop.sh->stop = 1u;
+  cudaStreamSynchronize(s->loop_st);
+  s->loop.sh->stop = 0u;
+  s->loop_running = false;
+}
+
+int loop_post(ebr_server *s, const std::vector<int> &take) {
+  LoopBufs &L = s->loop;
+  const uint32_t r = (uint32_t)(s->loop_posted % L.R);
+  std::vector<ebr_query> &qs = s->wave_qs[r];
+  qs.assign(take.size(), ebr_query{});
+  for (size_t i = 0; i < take.size(); i++) {
+    Slot &sl = s->slots[take[i]];
+    EBR_CUDA_TRY(cudaEventSynchronize(sl.copied));  // the slot's inputs are on the device
+    ebr_query &q = qs[i];
+    q.h_u = sl.d_hu;
+    q.user_vals = sl.d_uv;
+    q.user_ptr = sl.has_ptr ? sl.d_uptr : nullptr;
+    q.n_user_vals = sl.has_ptr ? sl.n_uv : 0;
+    q.filter = sl.has_filter ? sl.d_filter : nullptr;
+    q.k = sl.k;
+  }
+  EBR_TRY(loop_fill(L, s->loop_posted, s->ix, s->cross, qs.data(), (uint32_t)take.size()));
+  s->wave_slots[r] = take;
+  std::atomic_thread_fence(std::memory_order_release);  // the descriptor before the count
+  s->loop_posted += 1;
+  L.sh->posted = s->loop_posted;
+  return loop_ensure_running(s);
+}
+
+// A finished wave: error flags, the users whose exactness the merge could
+// not prove recomputed on the single-request scan, results to the slots.
+int loop_finish(ebr_server *s, uint32_t r) {
+  LoopBufs &L = s->loop;
+  const std::vector<int> &take = s->wave_slots[r];
+  const uint32_t B = (uint32_t)take.size();
+  std::atomic_thread_fence(std::memory_order_acquire);  // the count before the results
+  const uint32_t flags = L.flags_out[r];
+  EBR_TRY(check_device_flags(flags, "ebr_server (device loop)"));
+  uint32_t *d_ids = L.out_ids + (size_t)r * L.Bmax * L.kmax;
+  float *d_scores = L.out_scores + (size_t)r * L.Bmax * L.kmax;
+  for (uint32_t b = 0; b < B; b++) {
+    if (!L.status_out[(size_t)r * L.Bmax + b]) continue;
+    EBR_TRY(ws_prepare_one(s->ix, s->ix->n_keys, 8192));
+    EBR_TRY(query_one(s->ix, s->cross, s->wave_qs[r][b], d_ids + (size_t)b * L.kmax,
+                      d_scores + (size_t)b * L.kmax, L.kmax, s->res_st));
+    Ctrl hc;
+    EBR_CUDA_TRY(cudaMemcpyAsync(&hc, s->ix->ws.ctrl.p, sizeof(Ctrl), cudaMemcpyDeviceToHost,
+                                 s->res_st));
+    EBR_CUDA_TRY(cudaStreamSynchronize(s->res_st));
+    EBR_TRY(check_device_flags(hc.flags, "ebr_server (single-request recompute)"));
+    s->ix->fallbacks += 1;
+  }
+  EBR_CUDA_TRY(cudaMemcpyAsync(s->h_wave_ids, d_ids, (size_t)B * L.kmax * 4,
+                               cudaMemcpyDeviceToHost, s->res_st));
+  EBR_CUDA_TRY(cudaMemcpyAsync(s->h_wave_scores, d_scores, (size_t)B * L.kmax * 4,
+                               cudaMemcpyDeviceToHost, s->res_st));
+  EBR_CUDA_TRY(cudaStreamSynchronize(s->res_st));
+  s->ix->batched += B;
+  s->ix->launches += 8;  // fetch, staging, quantiser, expansion, window scan, merge, publish (+ memset)
+  const double t = now_s();
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (uint32_t b = 0; b < B; b++) {
+    Slot &sl = s->slots[take[b]];
+    memcpy(sl.h_ids, s->h_wave_ids + (size_t)b * L.kmax, sl.k * 4);
+    memcpy(sl.h_scores, s->h_wave_scores + (size_t)b * L.kmax, sl.k * 4);
+    sl.state = kDone;
+    s->finished.push_back(sl.ticket);
+    const float ms = (float)((t - sl.t_submit) * 1e3);
+    s->lat[s->lat_n % s->lat.size()] = ms;
+    s->lat_n += 1;
+    s->st.completed += 1;
+  }
+  s->st.batches += 1;
+  s->st.batched_requests += B;
+  return EBR_OK;
+}
+
+// Gives up on the waves in flight (the loop made no progress for
+// kStallSeconds): stops the loop, fails their requests and moves the
+// device's wave counter past them so that a relaunch does not run them.
+constexpr double kStallSeconds = 10.0;
+void loop_abandon(ebr_server *s, int rc, const char *why) {
+  LoopBufs &L = s->loop;
+  loop_stop(s);
+  for (uint64_t w = s->loop_done; w < s->loop_posted; w++) {
+    fail_slots(s, s->wave_slots[w % L.R], rc, why);
+    s->wave_slots[w % L.R].clear();
+  }
+  const unsigned long long posted = s->loop_posted;
+  cudaMemcpyAsync(L.seq, &posted, sizeof(posted), cudaMemcpyHostToDevice, s->loop_st);
+  cudaStreamSynchronize(s->loop_st);
+  s->loop_done = s->loop_posted;
+  L.sh->done = posted;
+  L.sh->freed = posted;
+}
+
+void worker_loop_main(ebr_server *s) {
+  cudaSetDevice(s->device);
+  LoopBufs &L = s->loop;
+  double progress = now_s();  // last wave posted or taken back
+  for (;;) {
+    // waves the device finished
+    const uint64_t done = L.sh->done;
+    if (s->loop_done < done) progress = now_s();
+    while (s->loop_done < done) {
+      const uint32_t r = (uint32_t)(s->loop_done % L.R);
+      const double tf0 = now_s();
+      const int rc = loop_finish(s, r);
+      if (rc != EBR_OK) fail_slots(s, s->wave_slots[r], rc, ebr_last_error());
+      s->wave_slots[r].clear();
+      s->loop_done += 1;
+      std::atomic_thread_fence(std::memory_order_release);
+      L.sh->freed = s->loop_done;  // the wave's result slot may be reused
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->st.finish_ms += (now_s() - tf0) * 1e3;
+    }
+    const bool inflight = s->loop_posted > s->loop_done;
+    std::vector<int> take;
+    bool swap_now = false;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->stop && !inflight) break;
+      shed_timed_out(s);
+      if (s->swap_req && !inflight) {
+        swap_now = true;
+      } else if (!s->swap_req && !s->stop && !s->queue.empty() &&
+                 s->loop_posted - s->loop_done < L.R) {
+        while (!s->queue.empty() && take.size() < s->max_batch) {
+          const int i = s->queue.front();
+          s->queue.pop_front();
+          s->slots[i].state = kRunning;
+          take.push_back(i);
+        }
+      } else if (!inflight) {
+        s->cv.wait_for(lk, std::chrono::milliseconds(2));
+        continue;
+      }
+    }
+    if (swap_now) {  // no wave uses the old index: leave the loop, rebuild it for the new one
+      loop_stop(s);
+      ebr_index *nx = nullptr;
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        nx = s->next_ix;
+      }
+      const int rc = loop_build(nx, s->cross, s->max_user_vals, s->loop_ws, L, s->loop_st);
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (rc == EBR_OK) {
+        s->ix = nx;
+        s->st.index_swaps += 1;
+      } else {  // keep serving the old index: rebuild its graph
+        loop_build(s->ix, s->cross, s->max_user_vals, s->loop_ws, L, s->loop_st);
+      }
+      s->next_ix = nullptr;
+      s->swap_req = false;
+      s->swap_cv.notify_all();
+      continue;
+    }
+    if (!take.empty()) {
+      const double tl0 = now_s();
+      progress = tl0;
+      const int rc = loop_post(s, take);
+      if (rc != EBR_OK) fail_slots(s, take, rc, ebr_last_error());
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->st.launch_ms += (now_s() - tl0) * 1e3;
+      continue;
+    }
+    // waves on the device: keep the loop running and look again shortly
+    if (loop_ensure_running(s) != EBR_OK) {  // the loop failed: its waves fail
+      loop_abandon(s, EBR_ECUDA, ebr_last_error());
+      continue;
+    }
+    if (now_s() - progress > kStallSeconds) {
+      loop_abandon(s, EBR_ETIMEDOUT, "ebr_server: the device loop made no progress");
+      progress = now_s();
+      continue;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  loop_stop(s);
+}
+
 void server_free(ebr_server *s) {
   for (Pipe &P : s->pipes) {
     batch_ws_free(P.ws);
@@ -288,6 +525,13 @@ void server_free(ebr_server *s) {
     if (P.h_scores) cudaFreeHost(P.h_scores);
     if (P.st) cudaStreamDestroy(P.st);
   }
+  loop_free(s->loop);
+  batch_ws_free(s->loop_ws);
+  if (s->h_wave_ids) cudaFreeHost(s->h_wave_ids);
+  if (s->h_wave_scores) cudaFreeHost(s->h_wave_scores);
+  if (s->loop_end) cudaEventDestroy(s->loop_end);
+  if (s->loop_st) cudaStreamDestroy(s->loop_st);
+  if (s->res_st) cudaStreamDestroy(s->res_st);
   for (Slot &sl : s->slots)
     if (sl.copied) cudaEventDestroy(sl.copied);
   dev_free(s->slot_mem);
@@ -358,18 +602,22 @@ extern "C" int ebr_server_create(ebr_index *ix, const ebr_cross *cross, const eb
     cudaMemGetInfo(&fr, &tot);
     budget = fr / 2;
   }
-  s->max_user_vals = c.max_user_vals ? c.max_user_vals : 8 * cross->f_u;
+  s->max_user_vals = std::max(c.max_user_vals ? c.max_user_vals : 8 * cross->f_u, cross->f_u);
   const size_t uv_bytes = round256((size_t)(s->max_user_vals + cross->f_u + 1) * 4);
   s->slot_bytes = round256((size_t)s->words * 8) + round256((size_t)ix->d * 4) + uv_bytes;
   const uint32_t kscan = std::min<uint32_t>(c.k_max * ix->rescore_mult, ix->n_ads);
   s->batched_ok = c.max_batch >= 2 && batch_index_ok(ix, cross, std::min<uint32_t>(c.max_batch, 256)) &&
                   (uint64_t)c.k_max * ix->rescore_mult <= 8192;
+  s->loop_mode = s->batched_ok && !c.host_driven;
   uint32_t mb = c.max_batch;
+  // workspaces: the device loop's (one batch workspace and its result ring),
+  // or two host-driven pipelines
   auto pipes_bytes = [&](uint32_t B) {
     const size_t ws = s->batched_ok ? batch_ws_bytes(ix, cross, std::max<uint32_t>(B, 2), kscan,
                                                      (uint64_t)std::max<uint32_t>(B, 2) *
                                                          s->max_user_vals)
                                     : 0;
+    if (s->loop_mode) return ws + loop_dev_bytes(B, c.k_max);
     return 2 * (ws + 2 * round256((size_t)B * c.k_max * 4));
   };
   while (mb > 1 && pipes_bytes(mb) + (uint64_t)mb * s->slot_bytes > budget) mb >>= 1;
@@ -428,14 +676,36 @@ extern "C" int ebr_server_create(ebr_index *ix, const ebr_cross *cross, const eb
       s->free_slots.push_back((int)(s->max_slots - 1 - i));
     }
   }
-  for (int p = 0; p < 2 && rc == EBR_OK; p++) rc = pipe_reserve(s, s->pipes[p]);
+  if (!s->loop_mode) {
+    for (int p = 0; p < 2 && rc == EBR_OK; p++) rc = pipe_reserve(s, s->pipes[p]);
+  } else if (rc == EBR_OK) {
+    rc = loop_alloc(s->loop, mb, c.k_max);
+    s->wave_slots.resize(s->loop.R);
+    s->wave_qs.resize(s->loop.R);
+    if (rc == EBR_OK &&
+        (cudaStreamCreateWithFlags(&s->loop_st, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaStreamCreateWithFlags(&s->res_st, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&s->loop_end, cudaEventDisableTiming) != cudaSuccess)) {
+      set_error("ebr_server_create: stream creation failed");
+      rc = EBR_ECUDA;
+    }
+    if (rc == EBR_OK &&
+        (cudaMallocHost((void **)&s->h_wave_ids, (size_t)mb * c.k_max * 4) != cudaSuccess ||
+         cudaMallocHost((void **)&s->h_wave_scores, (size_t)mb * c.k_max * 4) != cudaSuccess)) {
+      cudaGetLastError();
+      set_error("ebr_server_create: pinned host allocation failed");
+      rc = EBR_ENOMEM;
+    }
+    if (rc == EBR_OK) rc = ws_prepare_one(ix, ix->n_keys, 8192);  // recomputes allocate nothing
+    if (rc == EBR_OK) rc = loop_build(ix, cross, s->max_user_vals, s->loop_ws, s->loop, s->loop_st);
+  }
   if (rc != EBR_OK) {
     server_free(s);
     cudaSetDevice(prev);
     return rc;
   }
   s->device_bytes = (uint64_t)s->max_slots * s->slot_bytes + pipes_bytes(mb);
-  s->worker = std::thread(worker_main, s);
+  s->worker = std::thread(s->loop_mode ? worker_loop_main : worker_main, s);
   cudaSetDevice(prev);
   *out = s;
   return EBR_OK;

@@ -65,7 +65,7 @@ class QueryC(C.Structure):
 
 class ServerCfg(C.Structure):
     _fields_ = [("hbm_budget", u64), ("max_batch", u32), ("max_slots", u32), ("k_max", u32),
-                ("queue_timeout_ms", u32), ("max_user_vals", u32)]
+                ("queue_timeout_ms", u32), ("max_user_vals", u32), ("host_driven", u32)]
 
 
 class ServerStats(C.Structure):
@@ -74,7 +74,7 @@ class ServerStats(C.Structure):
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
                 ("max_batch", u32), ("max_slots", u32), ("device_bytes", u64),
                 ("slot_bytes", u64), ("launch_ms", C.c_double), ("finish_ms", C.c_double),
-                ("index_swaps", u64)]
+                ("index_swaps", u64), ("loop_launches", u64)]
 
 
 class Profile(C.Structure):
@@ -410,9 +410,9 @@ class Server:
     Requests are host arrays; results come back as host arrays."""
 
     def __init__(self, index: Index, cross: Cross, hbm_budget=0, max_batch=0, max_slots=0,
-                 k_max=0, queue_timeout_ms=0, max_user_vals=0):
+                 k_max=0, queue_timeout_ms=0, max_user_vals=0, host_driven=False):
         cfg = ServerCfg(int(hbm_budget), int(max_batch), int(max_slots), int(k_max),
-                        int(queue_timeout_ms), int(max_user_vals))
+                        int(queue_timeout_ms), int(max_user_vals), int(bool(host_driven)))
         h = vp()
         _check(ebr_server_create(index.h, cross.h, C.byref(cfg), C.byref(h)), "ebr_server_create")
         self.h = h.value

@@ -42,14 +42,16 @@ def _same_result(a, b, ref, tol, k, mask=None):
         assert abs(float(pa[int(i)]) - float(pb[int(i)])) <= 2 * tol[i]
 
 
-def test_alone_and_in_a_mix_give_the_same_result():
+@pytest.mark.parametrize("host_driven", [False, True])
+def test_alone_and_in_a_mix_give_the_same_result(host_driven):
+    """Default: the device-resident loop; host_driven: two pipelines."""
     n, B = 60_000, 40
     w, post, ix, cross = _setup(n, B)
     rng = np.random.default_rng(3)
     ks = [int(x) for x in rng.choice([100, 500, 1000], size=B)]
     fl = make_filters(rng, n, B, (0.01, 1.0))
     filt = [fl[b] if b % 2 else None for b in range(B)]
-    srv = ebr.Server(ix, cross, max_batch=64, k_max=1000)
+    srv = ebr.Server(ix, cross, max_batch=64, k_max=1000, host_driven=host_driven)
     try:
         probe = [0, 7, 13, 30]
         alone = {}
@@ -63,6 +65,7 @@ def test_alone_and_in_a_mix_give_the_same_result():
         st = srv.stats()
         assert st.completed == B + len(probe) and st.failed == 0
         assert st.batches < B + len(probe), "requests were never batched"
+        assert (st.loop_launches > 0) == (not host_driven)
         prof = ix.profile_read()
         assert prof.batched > 0 and prof.recomputed == 0, "batched users were recomputed"
         for b in probe + [1, 2, 5, 39]:
@@ -300,5 +303,29 @@ def test_multi_valued_requests_served_alone_and_in_a_mix(dtype):
             with pytest.raises(ebr.EbrError) as e:
                 srv.submit(w.h_u[1], np.ascontiguousarray(v), k, user_ptr=p)
             assert e.value.code == ebr.EBR_EINVAL
+    finally:
+        srv.close()
+
+
+def test_device_loop_leaves_when_idle_and_is_relaunched():
+    """The device-resident loop leaves after a while without work (its polls
+    are bounded) and the next request relaunches it; results stay exact."""
+    import time
+    n, k = 30_000, 100
+    w, post, ix, cross = _setup(n, 6)
+    srv = ebr.Server(ix, cross, max_batch=16, k_max=100)
+    try:
+        t = srv.submit(w.h_u[0], w.users[0], k)
+        r0 = srv.wait(t, k)
+        time.sleep(0.6)  # longer than the loop's idle exit
+        tickets = [srv.submit(w.h_u[b], w.users[b], k) for b in range(1, 6)]
+        res = [srv.wait(t, k) for t in tickets]
+        st = srv.stats()
+        assert st.failed == 0 and st.completed == 6
+        assert st.loop_launches >= 2, "the loop was not relaunched after leaving"
+        for b, (ids, sc) in enumerate([r0] + res):
+            ref, tol = ref_scores(w, b, post)
+            assert recall(ids, ref, tol, k) == 1.0
+            check_topk(ids, sc, ref, tol, k)
     finally:
         srv.close()
