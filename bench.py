@@ -469,6 +469,10 @@ def run_gpu_batched(args, w, rank, world, local_rank, steps=None, cpu_users=None
     return out
 
 
+MODE_NAMES = {False: "device-resident loop (one graph launch; a WHILE node running waves)",
+              True: "host-driven pipelines (a host launch per batch, two in flight)"}
+
+
 def run_serving(args, device=0):
     """Serving form (the 5,000,000-ad BF16 d=64 serving workload): open-loop
     Poisson arrivals through ebr_submit/ebr_poll at each offered rate, each
@@ -490,10 +494,7 @@ def run_serving(args, device=0):
     ks = [int(x) for x in w.ks]
     reqs = [(np.ascontiguousarray(w.h_u[b]), np.ascontiguousarray(w.users[b]), ks[b],
              np.ascontiguousarray(w.filters[b])) for b in range(pool)]
-    srv = ebr.Server(ix, cross, max_batch=args.serve_batch, max_slots=4096, k_max=1000,
-                     host_driven=args.serve_host_driven)
-
-    def drive(rate, duration, keep=None):
+    def drive(srv, rate, duration, keep=None):
         # one thread: submit every request whose arrival time has passed, then
         # retire whatever the server reports finished (no lock, no GIL contention);
         # `keep` collects (user, K, ids) of the first results of distinct users
@@ -534,20 +535,37 @@ def run_serving(args, device=0):
         span = max(last, t0 + duration) - t0
         return len(arr), n_done, rejected + failed, span
 
-    drive(2000.0, 0.3)  # warm-up
-    rows, checks = [], []
-    for rate in args.serve_rates:
-        srv.reset_stats()
-        keep = []
-        offered, n_done, rejected, span = drive(rate, args.serve_seconds, keep)
-        st = srv.stats()
-        rows.append({"offered_req_s": rate, "submitted": offered, "completed": n_done,
-                     "rejected": rejected, "req_per_s": n_done / span,
-                     "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
-                     "mean_batch": st.batched_requests / max(st.batches, 1)})
-        checks.append(keep)
-    srv_stats = srv.stats()
-    srv.close()
+    def serve(host_driven, rates, seconds, checks=None):
+        srv = ebr.Server(ix, cross, max_batch=args.serve_batch, max_slots=4096, k_max=1000,
+                         host_driven=host_driven)
+        drive(srv, 2000.0, 0.3)  # warm-up
+        rows = []
+        launches = srv.stats().loop_launches
+        for rate in rates:
+            srv.reset_stats()
+            keep = [] if checks is not None else None
+            offered, n_done, rejected, span = drive(srv, rate, seconds, keep)
+            st = srv.stats()
+            launches += st.loop_launches
+            rows.append({"offered_req_s": rate, "submitted": offered, "completed": n_done,
+                         "rejected": rejected, "req_per_s": n_done / span,
+                         "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
+                         "mean_batch": st.batched_requests / max(st.batches, 1)})
+            if checks is not None:
+                checks.append(keep)
+        mb = srv.stats().max_batch
+        srv.close()
+        return rows, launches, mb
+
+    checks = []
+    rows, loop_launches, max_batch = serve(args.serve_host_driven, args.serve_rates,
+                                           args.serve_seconds, checks)
+    other = None
+    if not args.no_serve_compare:  # the other form, fewer rates, for comparison
+        orows, olaunch, _ = serve(not args.serve_host_driven, (2000.0, 10000.0, 20000.0),
+                                  max(2.0, args.serve_seconds / 2))
+        other = {"mode": MODE_NAMES[not args.serve_host_driven], "loop_launches": int(olaunch),
+                 "rates": orows, "max_req_per_s": max(r["req_per_s"] for r in orows)}
     # the plain per-request FP32 path on the same inventory, host buffers
     del ix
     ix32 = ebr.build_index(w.n_ads, w.n_keys, pk, pa, w.emb, dtype="f32", device=device)
@@ -582,10 +600,9 @@ def run_serving(args, device=0):
             "emb_dtype": "bf16 + FP32 rescoring (R=4)", "ad_fields": w.recipe.f_a,
             "cross_pairs": int(len(w.pairs)), "k_choices": [100, 500, 1000],
             "filter_fraction": "U[0.01, 1] per request", "request_pool": pool,
-            "max_batch": srv_stats.max_batch, "rates": rows,
-            "mode": ("host-driven pipelines" if args.serve_host_driven else
-                     "device-resident loop (one graph launch; WHILE node running waves)"),
-            "loop_launches": int(srv_stats.loop_launches),
+            "max_batch": max_batch, "rates": rows,
+            "mode": MODE_NAMES[bool(args.serve_host_driven)],
+            "loop_launches": int(loop_launches), "other_mode": other,
             "max_req_per_s": best["req_per_s"],
             "recall": {"checked": len(rec), "min": float(min(rec)) if rec else None,
                        "definition": "|S_gpu & S_oracle| / K against the FP64 oracle, ids "
@@ -734,6 +751,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-host-driven", action="store_true",
                     help="serve with the host-driven pipelines instead of the device-resident loop")
+    ap.add_argument("--no-serve-compare", action="store_true",
+                    help="skip the shorter run of the other serving form")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched BF16, FP8 single and FP8 batched lines")
     ap.add_argument("--extra-steps", type=int, default=10,

@@ -313,43 +313,66 @@ struct BatchSmem {
 __device__ __forceinline__ uint32_t ushift(uint32_t g) { return g >= 2 ? g - 2 : 0; }
 
 // Walk the real slots of window w: f(ad_in_window, key).  `t`/`nt`: this
-// thread's index in the walking group.  Eight units per thread are loaded
-// before any is used, so each thread keeps that many loads in flight.
+// thread's index in the walking group (whole warps).  The window's block
+// range in each of the nine groups is read once (one lane per group) and the
+// groups' work units are walked as one sequence, eight units per thread
+// loaded before any is used, so loads stay in flight across group borders.
 template <typename F>
 __device__ __forceinline__ void walk_window(const BatchArgs &a, uint32_t w, int t, int nt, F f) {
   constexpr int kU = 8;
-#pragma unroll 1
-  for (uint32_t g = 0; g < (uint32_t)kGroups; g++) {
-    const uint32_t lo = __ldg(a.win_ptr[g] + w), hi = __ldg(a.win_ptr[g] + w + 1);
-    const uint32_t us = ushift(g);
-    const uint32_t units = (hi - lo) << us;
-    const uint32_t ns = g >= 2 ? 4u : (g == 1 ? 2u : 1u);
-#pragma unroll 1
-    for (uint32_t u0 = t; u0 < units; u0 += kU * nt) {
-      uint32_t key[kU], word[kU], first[kU];
+  const int lane = threadIdx.x & 31;
+  uint32_t lo_l = 0, n_l = 0;
+  if (lane < kGroups) {
+    const uint32_t lo = __ldg(a.win_ptr[lane] + w), hi = __ldg(a.win_ptr[lane] + w + 1);
+    lo_l = lo;
+    n_l = (hi - lo) << ushift(lane);
+  }
+  uint32_t lo_g[kGroups], end_g[kGroups];  // first block, end of the group's units
+  uint32_t total = 0;
 #pragma unroll
-      for (int e = 0; e < kU; e++) {
-        const uint32_t u = u0 + e * nt;
-        const bool v = u < units;
-        const uint32_t bk = lo + (v ? (u >> us) : 0u), wi = u & ((1u << us) - 1u);
-        key[e] = v ? __ldg(a.wkey[g] + bk) : 0u;
-        if (!v)
-          word[e] = 0u;
-        else if (g >= 2)
-          word[e] = __ldg(reinterpret_cast<const uint32_t *>(a.wvals[g]) + (((uint64_t)bk << us) + wi));
-        else if (g == 1)
-          word[e] = __ldg(reinterpret_cast<const unsigned short *>(a.wvals[1]) + bk);
-        else
-          word[e] = __ldg(a.wvals[0] + bk);
-        first[e] = (v && wi == 0) ? 1u : 0u;
-      }
+  for (int g = 0; g < kGroups; g++) {
+    lo_g[g] = __shfl_sync(0xffffffffu, lo_l, g);
+    total += __shfl_sync(0xffffffffu, n_l, g);
+    end_g[g] = total;
+  }
+#pragma unroll 1
+  for (uint32_t u0 = t; u0 < total; u0 += kU * nt) {
+    uint32_t key[kU], word[kU], gg[kU], first[kU];
 #pragma unroll
-      for (int e = 0; e < kU; e++) {
-        if (u0 + e * nt >= units) break;
-        for (uint32_t s = 0; s < ns; s++) {
-          const uint32_t l = (word[e] >> (8 * s)) & 255u;
-          if ((s == 0 && first[e]) || l != 0) f(l, key[e]);
+    for (int e = 0; e < kU; e++) {
+      const uint32_t U = u0 + e * nt;
+      const bool v = U < total;
+      uint32_t g = 0;
+#pragma unroll
+      for (int i = 0; i < kGroups - 1; i++) g += U >= end_g[i] ? 1u : 0u;
+      uint32_t lo = lo_g[0], beg = 0;
+#pragma unroll
+      for (int i = 1; i < kGroups; i++)
+        if (g == (uint32_t)i) {
+          lo = lo_g[i];
+          beg = end_g[i - 1];
         }
+      const uint32_t us = ushift(g), u = U - beg;
+      const uint32_t bk = lo + (v ? (u >> us) : 0u), wi = u & ((1u << us) - 1u);
+      key[e] = v ? __ldg(a.wkey[g] + bk) : 0u;
+      if (!v)
+        word[e] = 0u;
+      else if (g >= 2)
+        word[e] = __ldg(reinterpret_cast<const uint32_t *>(a.wvals[g]) + (((uint64_t)bk << us) + wi));
+      else if (g == 1)
+        word[e] = __ldg(reinterpret_cast<const unsigned short *>(a.wvals[1]) + bk);
+      else
+        word[e] = __ldg(a.wvals[0] + bk);
+      gg[e] = g;
+      first[e] = (v && wi == 0) ? 1u : 0u;
+    }
+#pragma unroll
+    for (int e = 0; e < kU; e++) {
+      if (u0 + e * nt >= total) break;
+      const uint32_t ns = gg[e] >= 2 ? 4u : (gg[e] == 1 ? 2u : 1u);
+      for (uint32_t s = 0; s < ns; s++) {
+        const uint32_t l = (word[e] >> (8 * s)) & 255u;
+        if ((s == 0 && first[e]) || l != 0) f(l, key[e]);
       }
     }
   }
@@ -1578,7 +1601,9 @@ struct LoopArgs {
   uint32_t *status;            // [R][Bmax]
   uint32_t R, Bmax, desc_bytes;
   unsigned long long poll_ns, idle_exit_ns;
-  cudaGraphConditionalHandle handle;
+  cudaGraphConditionalHandle handle;  // the WHILE node's
+  cudaGraphConditionalHandle sw;      // the SWITCH node's: which user-table width runs
+  uint32_t nsw, bq[3];                // widths (users) of the switch's cases, ascending
 };
 
 __device__ __forceinline__ unsigned long long ld_acquire_sys(const volatile unsigned long long *p) {
@@ -1593,10 +1618,12 @@ __device__ __forceinline__ void st_release_sys(volatile unsigned long long *p,
 
 // First node of the loop body.  Thread 0 waits, for at most poll_ns, for a
 // wave the host posted whose result slot the host has freed, or for stop.
-// A wave: its descriptor is copied into `cur` and its control block and
-// status zeroed.  No wave: cur.B = 0 (every later node of this iteration
-// returns at once), and after idle_exit_ns without a wave, or on stop, the
-// loop's condition is cleared so that this iteration is the last.
+// A wave: its descriptor is copied into `cur`, its control block and status
+// zeroed, and the SWITCH node that follows is told which user-table width
+// (the narrowest that holds the wave's users) to run.  No wave: cur.B = 0
+// (every later node of this iteration returns at once), and after
+// idle_exit_ns without a wave, or on stop, the loop's condition is cleared
+// so that this iteration is the last.
 __global__ void __launch_bounds__(256) k_loop_fetch(LoopArgs a) {
   __shared__ uint32_t s_state, s_slot;
   if (threadIdx.x == 0) {
@@ -1623,6 +1650,13 @@ __global__ void __launch_bounds__(256) k_loop_fetch(LoopArgs a) {
       *a.idle_ns = 0;
     }
     if (st == 2) cudaGraphSetConditional(a.handle, 0u);
+    if (st == 1) {  // the narrowest user table that holds the wave
+      const uint32_t B = reinterpret_cast<const volatile uint32_t *>(
+          a.desc + (size_t)(seq % a.R) * a.desc_bytes)[0];
+      uint32_t c = 0;
+      while (c + 1 < a.nsw && B > a.bq[c]) c++;
+      cudaGraphSetConditional(a.sw, c);
+    }
     s_state = st;
     s_slot = (uint32_t)(seq % a.R);
     *a.slot = s_slot;
@@ -1745,8 +1779,12 @@ int loop_fill(LoopBufs &L, uint64_t wave, const ebr_index *ix, const ebr_cross *
   return EBR_OK;
 }
 
-// Captures the loop body for index ix into a WHILE node and instantiates
-// it.  The batch plan is fixed for Bmax users and K up to L.kmax.
+// Builds the loop graph for index ix: a WHILE node whose body is
+//   fetch -> SWITCH { one case per user-table width 64, 128, 256 (up to the
+//   server's batch): staging, quantiser, expansion, window scan, merge }
+//   -> publish,
+// so a wave of a few users runs on the narrowest table that holds it.  The
+// batch plan (candidate buffers, shared memory) is the same for every width.
 int loop_build(ebr_index *ix, const ebr_cross *cross, uint32_t max_user_vals, BatchWs &w,
                LoopBufs &L, cudaStream_t st) {
   if (L.exec) {
@@ -1759,7 +1797,6 @@ int loop_build(ebr_index *ix, const ebr_cross *cross, uint32_t max_user_vals, Ba
   BatchSizes z;
   batch_sizes(ix, cross, Bmax, kscan_max, (uint64_t)Bmax * max_user_vals, &z);
   const BatchPlan pl = z.pl;
-  const uint32_t Bp = pl.Bq;
   const bool f8 = ix->dtype == EBR_FP8E4M3;
   uint8_t *cur = L.cur;
   const uint32_t *B_dev = (const uint32_t *)cur;
@@ -1767,33 +1804,32 @@ int loop_build(ebr_index *ix, const ebr_cross *cross, uint32_t max_user_vals, Ba
   const ReqSrc *srcs = (const ReqSrc *)(cur + desc_src_off(Bmax));
   uint32_t *d_uptr = (uint32_t *)w.user_ptr.p;
   uint32_t *d_base = d_uptr + (size_t)Bmax * (fu + 1);
-  BatchArgs ba;
-  EBR_TRY(fill_batch_args(ix, Bmax, pl, w, hf, L.ctrl, B_dev, &ba));
   auto kern = f8 ? k_batch_window<true> : k_batch_window<false>;
   EBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)pl.smem));
   EBR_CUDA_TRY(cudaFuncSetAttribute(k_batch_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     8192 * 8));
+  LoopArgs la;
+  memset(&la, 0, sizeof(la));
+  la.nsw = 0;
+  for (uint32_t q = 64; q <= pl.Bq; q <<= 1) la.bq[la.nsw++] = q;
   cudaGraph_t g = nullptr;
   EBR_CUDA_TRY(cudaGraphCreate(&g, 0));
-  cudaGraphConditionalHandle h;
-  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
-  cudaGraphNodeParams np = {};
-  cudaGraphNode_t node;
+  int rc = EBR_OK;
+  const char *what = "conditional graph nodes";
+  cudaError_t e = cudaGraphConditionalHandleCreate(&la.handle, g, 1u, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams wp = {}, sp = {};
+  cudaGraphNode_t wnode, fnode, snode;
   if (e == cudaSuccess) {
-    np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = h;
-    np.conditional.type = cudaGraphCondTypeWhile;
-    np.conditional.size = 1;
-    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = la.handle;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp);
   }
-  if (e != cudaSuccess) {
-    cudaGraphDestroy(g);
-    set_error("serving loop: conditional graph node: %s", cudaGetErrorString(e));
-    return EBR_ECUDA;
-  }
-  cudaGraph_t body = np.conditional.phGraph_out[0];
-  LoopArgs la;
+  cudaGraph_t body = e == cudaSuccess ? wp.conditional.phGraph_out[0] : nullptr;
+  if (e == cudaSuccess)
+    e = cudaGraphConditionalHandleCreate(&la.sw, body, 0u, cudaGraphCondAssignDefault);
   la.sh = L.sh;
   la.desc = L.desc;
   la.flags_out = L.flags_out;
@@ -1809,12 +1845,40 @@ int loop_build(ebr_index *ix, const ebr_cross *cross, uint32_t max_user_vals, Ba
   la.desc_bytes = L.desc_bytes;
   la.poll_ns = L.poll_ns;
   la.idle_exit_ns = L.idle_exit_ns;
-  la.handle = h;
-  e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-  int rc = EBR_OK;
+  // fetch
   if (e == cudaSuccess) {
+    what = "capture of the fetch node";
+    e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      k_loop_fetch<<<1, 256, 0, st>>>(la);
+      cudaGraph_t cap = nullptr;
+      e = cudaStreamEndCapture(st, &cap);
+    }
+    size_t nn = 1;
+    if (e == cudaSuccess) e = cudaGraphGetNodes(body, &fnode, &nn);
+    if (e == cudaSuccess && nn != 1) e = cudaErrorInvalidValue;
+  }
+  // the switch and its cases
+  if (e == cudaSuccess) {
+    what = "switch node";
+    sp.type = cudaGraphNodeTypeConditional;
+    sp.conditional.handle = la.sw;
+    sp.conditional.type = cudaGraphCondTypeSwitch;
+    sp.conditional.size = la.nsw;
+    e = cudaGraphAddNode(&snode, body, &fnode, nullptr, 1, &sp);
+  }
+  for (uint32_t c = 0; e == cudaSuccess && rc == EBR_OK && c < la.nsw; c++) {
+    what = "capture of a wave";
+    BatchPlan pc = pl;
+    pc.Bq = la.bq[c];
+    const uint32_t Bp = pc.Bq;
+    BatchArgs ba;
+    rc = fill_batch_args(ix, Bmax, pc, w, hf, L.ctrl, B_dev, &ba);
+    if (rc != EBR_OK) break;
+    e = cudaStreamBeginCaptureToGraph(st, sp.conditional.phGraph_out[c], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) break;
     const uint32_t ys = (words + kStageWords - 1) / kStageWords;
-    k_loop_fetch<<<1, 256, 0, st>>>(la);
     k_stage_requests<<<dim3(Bp, ys), 256, 0, st>>>(srcs, d, fu, words, Bp / 2,
                                                    (float *)w.users_f32.p,
                                                    (uint32_t *)w.user_vals.p, d_uptr, d_base,
@@ -1826,28 +1890,42 @@ int loop_build(ebr_index *ix, const ebr_cross *cross, uint32_t max_user_vals, Ba
       rc = launch_quantize((const float *)w.users_f32.p, (uint64_t)Bp * d, EBR_BF16,
                            w.users_bf16.p, st);
     if (rc == EBR_OK)
-      rc = expand_transposed(cross, (const uint32_t *)w.user_vals.p, d_uptr, d_base, Bmax, Bp,
-                             (float *)w.wT.p, &L.ctrl->flags, st, B_dev);
+      rc = expand_transposed(cross, (const uint32_t *)w.user_vals.p, d_uptr, d_base,
+                             std::min(Bmax, Bp), Bp, (float *)w.wT.p, &L.ctrl->flags, st, B_dev);
     if (rc == EBR_OK) {
       cudaMemsetAsync((float *)w.wT.p + (size_t)ix->n_keys * Bp, 0, (size_t)Bp * 4, st);
       kern<<<z.grid, kBatchThreads, pl.smem, st>>>(ba);
-      k_batch_merge<<<Bmax, kMergeThreads, 8192 * 8, st>>>(
+      k_batch_merge<<<std::min(Bmax, Bp), kMergeThreads, 8192 * 8, st>>>(
           (const CandEntry *)w.cand.p, (const uint32_t *)w.cand_n.p,
           (const unsigned long long *)w.cand_thr.p, (uint32_t)z.grid, Bmax, pl.cap_u, ks, ko,
           L.kmax, (const float *)ix->emb_f32.p, d, (const float *)w.users_f32.p, Bp / 2,
           (uint64_t *)w.scratch.p, L.out_ids, L.out_scores, L.status, B_dev, L.slot,
           (uint64_t)Bmax * L.kmax, Bmax);
-      k_loop_publish<<<1, 256, 0, st>>>(la);
     }
     cudaGraph_t cap = nullptr;
-    e = cudaStreamEndCapture(st, &cap);
+    const cudaError_t e2 = cudaStreamEndCapture(st, &cap);
+    if (e == cudaSuccess) e = e2;
   }
-  if (e == cudaSuccess && rc == EBR_OK) e = cudaGraphInstantiate(&L.exec, g, 0);
+  // publish, after the switch
+  if (e == cudaSuccess && rc == EBR_OK) {
+    what = "capture of the publish node";
+    e = cudaStreamBeginCaptureToGraph(st, body, &snode, nullptr, 1, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      k_loop_publish<<<1, 256, 0, st>>>(la);
+      cudaGraph_t cap = nullptr;
+      e = cudaStreamEndCapture(st, &cap);
+    }
+  }
+  if (e == cudaSuccess && rc == EBR_OK) {
+    what = "graph instantiation";
+    e = cudaGraphInstantiate(&L.exec, g, 0);
+  }
   cudaGraphDestroy(g);
   if (rc != EBR_OK) return rc;
   if (e != cudaSuccess) {
     L.exec = nullptr;
-    set_error("serving loop: graph capture: %s", cudaGetErrorString(e));
+    cudaGetLastError();
+    set_error("serving loop: %s: %s", what, cudaGetErrorString(e));
     return EBR_ECUDA;
   }
   return EBR_OK;

@@ -125,6 +125,7 @@ struct LoopShared {                     // pinned host memory mapped into the de
 };
 struct LoopBufs {
   uint32_t R = 4, Bmax = 0, kmax = 0, desc_bytes = 0;
+  uint32_t ahead = 2;             // waves posted and not yet taken back, at most (<= R)
   void *host = nullptr;           // pinned, mapped: LoopShared, descriptors [R], flags [R], status [R][Bmax]
   LoopShared *sh = nullptr;
   uint8_t *desc = nullptr;        // [R][desc_bytes] wave descriptors (host-written)

@@ -8,9 +8,10 @@
 //    mapped memory) for the next wave the worker thread posted, stages the
 //    wave's requests from their slots, runs the batched scan and merge into
 //    a ring slot of results and publishes it.  The worker thread only posts
-//    waves (up to max_batch queued requests each, up to four waves ahead)
-//    and takes finished ones back; the loop leaves after a while without
-//    work and is relaunched on demand;
+//    waves (up to max_batch queued requests each; one running and one
+//    waiting, as many as the host-driven form keeps in flight, so that a
+//    request waits behind at most two waves) and takes finished ones back;
+//    the loop leaves after a while without work and is relaunched on demand;
 //  - host-driven pipelines: the worker thread keeps two pipelines (workspace
 //    + stream each) and launches all queued requests (up to max_batch) as
 //    one batched scan whenever one is free, finishing the oldest otherwise.
@@ -461,7 +462,7 @@ void worker_loop_main(ebr_server *s) {
       if (s->swap_req && !inflight) {
         swap_now = true;
       } else if (!s->swap_req && !s->stop && !s->queue.empty() &&
-                 s->loop_posted - s->loop_done < L.R) {
+                 s->loop_posted - s->loop_done < L.ahead) {
         while (!s->queue.empty() && take.size() < s->max_batch) {
           const int i = s->queue.front();
           s->queue.pop_front();
