@@ -848,9 +848,9 @@ __device__ void bitonic_sort_desc(uint64_t *v, uint32_t n_pow2) {
   __syncthreads();
 }
 
-// Selects the best min(k, n) keys among n (global memory), sorts them
-// descending, writes k_out ids/scores (or keys), padded with (0xFFFFFFFF, -inf)
-// (or zero keys).  Dynamic shared memory: 8 * (pow2(min(k, n)) + buf_cap)
+// Selects the best min(k, n) keys among n (global memory) and writes k_out
+// ids/scores sorted descending, padded with (0xFFFFFFFF, -inf), or the keys
+// themselves in no particular order, padded with zero keys.  Dynamic shared memory: 8 * (pow2(min(k, n)) + buf_cap)
 // bytes; when n <= buf_cap the keys are read from global memory once and the
 // radix select runs on the shared copy, otherwise on the global keys.
 // Waits (pdl_wait) for the kernel before it in the stream.
@@ -887,7 +887,11 @@ __global__ void __launch_bounds__(kFinalThreads) k_final_select(
   }
   __syncthreads();
   for (uint32_t i = take + threadIdx.x; i < p2; i += kFinalThreads) s_v[i] = 0ull;
-  bitonic_sort_desc(s_v, p2);
+  if (out_keys) {  // keys for a later stage (FP32 rescoring): any order will do
+    __syncthreads();
+  } else {
+    bitonic_sort_desc(s_v, p2);
+  }
   for (uint32_t i = threadIdx.x; i < k_out; i += kFinalThreads) {
     if (out_keys) {
       out_keys[i] = i < take ? s_v[i] : 0ull;
@@ -902,7 +906,7 @@ __global__ void __launch_bounds__(kFinalThreads) k_final_select(
 }
 
 // Shared-memory keys k_final_select buffers beyond its pow2(k) sort area.
-constexpr uint32_t kFinalBufKeys = 8192;
+constexpr uint32_t kFinalBufKeys = 16384;
 constexpr size_t kFinalMaxSmem = (8192 + kFinalBufKeys) * 8;  // largest k is 8192
 static size_t final_smem(uint32_t p2) { return ((size_t)p2 + kFinalBufKeys) * 8; }
 
