@@ -27,6 +27,7 @@
 // that times out flags the request and drains its copies.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "ebr_device.cuh"
 #include "ebr_internal.cuh"
@@ -61,6 +62,8 @@ struct FusedArgs {
   const uint64_t *filter;
   uint32_t n_ads, n_win, k, cap, stages, slot_bytes, idx_slots;
   uint64_t *cand_out;
+  uint64_t *cand_g;   // if set: the CTAs' candidate buffers (cap entries each) live here, in
+                      // global memory, instead of in shared memory
   Ctrl *ctrl;
   float *all_out;   // score-all mode
   float *wide_out;  // if set: the per-ad wide term is written here (FP32 rescoring needs it)
@@ -187,7 +190,8 @@ struct FusedSmem {
   uint32_t stop_acc, stop_end, team_stop[kTeams];
 };
 
-template <typename Elt, int D, bool ALL>
+// GC: the candidate buffers are in global memory (a.cand_g).
+template <typename Elt, int D, bool ALL, bool GC>
 __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
   using Sh = FusedShape<Elt, D>;
   using Tr = EltTraits<Elt>;
@@ -199,7 +203,8 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
   uint8_t *stage0 = smem;
   uint8_t *slot0 = smem + (size_t)S * kStageBytes;
   float *s_h = reinterpret_cast<float *>(slot0 + (size_t)a.idx_slots * a.slot_bytes);
-  uint64_t *cand = reinterpret_cast<uint64_t *>(s_h + D);
+  uint64_t *cand = GC ? a.cand_g + (size_t)blockIdx.x * a.cap
+                     : reinterpret_cast<uint64_t *>(s_h + D);
 
   // a contiguous, balanced range of windows per CTA: one sequential stream per SM
   const uint32_t w_begin = (uint32_t)(((uint64_t)a.n_win * blockIdx.x) / gridDim.x);
@@ -546,8 +551,15 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
 #pragma unroll
     for (int e = 0; e < Tr::kVec; e++) hreg[i * Tr::kVec + e] = s_h[c * Tr::kVec + e];
   }
-  for (uint32_t j = 0; j < my_wins; j++) {
-    const uint32_t b = j % kAccBufs, apar = (j / kAccBufs) & 1u;
+  // Where the scorers wait for a window's wide terms: before its inner
+  // products, or (FP32 tables) after them, so that the stages are read and
+  // handed back while a decoder team finishes the window and the embedding
+  // stream keeps moving.  Measured on both workloads: the later wait is
+  // faster with FP32 rows (2M ads, d = 64) and slower with FP8 rows, whose
+  // conversions leave no registers for the held products.
+  constexpr bool kDotFirst = std::is_same<Elt, float>::value;
+  // waits (thread 0, bounded) for window j's wide terms; true: stop scoring
+  auto wait_wide = [&](uint32_t b, uint32_t apar) -> bool {
     if (tid == 0) {
       uint32_t stop = *((volatile uint32_t *)&sm.abort);
       if (!stop && !mbar_wait_bounded(&sm.acc_full[b], apar, kWaitTimeoutNs)) stop = 1;
@@ -558,9 +570,14 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       sm.stop_acc = stop;
     }
     gsync();
-    if (sm.stop_acc) break;
+    if (sm.stop_acc) return true;
     mbar_try_wait(&sm.acc_full[b], apar);  // per-thread acquire
+    return false;
+  };
+  for (uint32_t j = 0; j < my_wins; j++) {
+    const uint32_t b = j % kAccBufs, apar = (j / kAccBufs) & 1u;
     const uint32_t w = w_begin + j;
+    if (!kDotFirst && wait_wide(b, apar)) break;
     // per-row side inputs, loaded before the rows arrive so that their
     // latency overlaps the wait for the stage
     float pre_side[Sh::kPasses], pre_scale[Sh::kPasses];
@@ -573,19 +590,24 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       pre_scale[ps] = in && a.scale ? __ldg(a.scale + ad) : 1.f;
       pre_keep[ps] = !(in && a.filter) || ((__ldg(a.filter + (ad >> 6)) >> (ad & 63)) & 1ull);
     }
-    const float *acc = sm.acc[b].fp;  // the window's wide terms, folded by the decoders
+    // the inner products of the window's rows
+    float dotv[Sh::kPasses];
+    bool validv[Sh::kPasses];
 #pragma unroll
     for (int ps = 0; ps < Sh::kPasses; ps++) {
       const uint32_t rw = ps * Sh::kRowsPerPass + prow;  // row within the window
       const uint32_t ad = w * kWin + rw;
       const uint32_t seq = j * Sh::kStagesPerWin + rw / Sh::kRowsPerStage;
-      // Each warp's rows lie in one stage: wait for that stage only, and hand
-      // it back right after reading it, so the producer refills the ring while
-      // the rest of the window is still being scored.
+      // Each warp's rows lie in one stage: wait for that stage only (not at
+      // all once the CTA has given up), and hand it back right after reading
+      // it, so the producer refills the ring while the rest of the window is
+      // still being scored.
       bool staged = true;
-      if (lane == 0) staged = mbar_wait_bounded(&sm.full[seq % S], (seq / S) & 1u, kWaitTimeoutNs);
+      if (lane == 0)
+        staged = (!kDotFirst || !*((volatile uint32_t *)&sm.abort)) &&
+                 mbar_wait_bounded(&sm.full[seq % S], (seq / S) & 1u, kWaitTimeoutNs);
       staged = __shfl_sync(0xffffffffu, staged, 0);
-      if (!staged && lane == 0) {
+      if (!staged && lane == 0 && (!kDotFirst || !*((volatile uint32_t *)&sm.abort))) {
         atomicOr(&a.ctrl->flags, DEVERR_TIMEOUT);
         sm.abort = 1;
       }
@@ -611,11 +633,20 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       float dot = dot2.x + dot2.y;
 #pragma unroll
       for (int o = Sh::kTPR / 2; o >= 1; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-      const bool leader = valid && qd == 0;
+      dotv[ps] = dot;
+      validv[ps] = valid;
+    }
+    if (kDotFirst && wait_wide(b, apar)) break;
+    const float *acc = sm.acc[b].fp;  // the window's wide terms, folded by the decoders
+#pragma unroll
+    for (int ps = 0; ps < Sh::kPasses; ps++) {
+      const uint32_t rw = ps * Sh::kRowsPerPass + prow;
+      const uint32_t ad = w * kWin + rw;
+      const bool leader = validv[ps] && qd == 0;
       float score = 0.f;
       if (leader) {
         const float wide = pre ? pre_side[ps] : acc[rw];
-        score = dot;
+        score = dotv[ps];
         if (a.scale) score *= pre_scale[ps];
         score += wide;
         if (a.wide_out && !pre) a.wide_out[ad] = wide;
@@ -717,7 +748,8 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
   }
 }
 
-// Shared memory the fused scan needs besides its stage ring.
+// Shared memory the fused scan needs besides its stage ring (cap: entries of
+// the candidate buffer held in shared memory, 0 when it is in global memory).
 static size_t fused_fixed_bytes(const ebr_index *ix, uint32_t d, uint32_t cap, uint32_t slots,
                                 uint32_t *slot_bytes) {
   *slot_bytes = (ix->max_win_bytes + 127) / 128 * 128;
@@ -734,16 +766,32 @@ static uint32_t fused_cap(uint32_t k) {
 }
 
 template <typename Elt, int D, bool ALL>
-static int launch_fused_t(const ebr_index *ix, FusedArgs a, int max_grid, cudaStream_t st) {
+static int launch_fused_t(const ebr_index *ix, FusedArgs a, int max_grid, cudaStream_t st,
+                          uint64_t *cta_cand, size_t cta_cand_entries) {
   a.cap = ALL ? 0 : fused_cap(a.k);
+  int grid = ix->num_sms;
+  if (max_grid > 0) grid = std::min(grid, max_grid);
+  grid = std::min<int>(grid, (int)a.n_win);
+  if (grid < 1) grid = 1;
   uint32_t slot_bytes = 0;
   // two index slots per decoder team (the next window's segments arrive while
-  // the team decodes the current one) when that still leaves 8 stages
+  // the team decodes the current one) when that still leaves 8 stages; a
+  // large candidate buffer (big K) moves to global memory to make room for
+  // them, since after the first windows the running threshold lets few
+  // candidates through and the buffer is rarely touched
   uint32_t slots = kMaxIdxSlots;
   size_t fixed = fused_fixed_bytes(ix, D, a.cap, slots, &slot_bytes);
+  a.cand_g = nullptr;
   if (fixed + 8 * (size_t)kStageBytes > kFusedSmemBudget) {
-    slots = kTeams;
-    fixed = fused_fixed_bytes(ix, D, a.cap, slots, &slot_bytes);
+    const size_t fixed_g = fused_fixed_bytes(ix, D, 0, slots, &slot_bytes);
+    if (!ALL && cta_cand && (size_t)grid * a.cap <= cta_cand_entries &&
+        fixed_g + 8 * (size_t)kStageBytes <= kFusedSmemBudget) {
+      a.cand_g = cta_cand;
+      fixed = fixed_g;
+    } else {
+      slots = kTeams;
+      fixed = fused_fixed_bytes(ix, D, a.cap, slots, &slot_bytes);
+    }
   }
   a.idx_slots = slots;
   if (fixed + kMinStages * (size_t)kStageBytes > kFusedSmemBudget) {
@@ -758,7 +806,10 @@ static int launch_fused_t(const ebr_index *ix, FusedArgs a, int max_grid, cudaSt
   a.stages = stages;
   a.slot_bytes = slot_bytes;
   const size_t smem = fixed + (size_t)stages * kStageBytes;
-  auto kern = k_fused_window<Elt, D, ALL>;
+  auto kern = k_fused_window<Elt, D, ALL, false>;
+  if constexpr (!ALL) {
+    if (a.cand_g) kern = k_fused_window<Elt, D, false, true>;
+  }
   EBR_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   EBR_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kFusedThreads, smem));
@@ -767,24 +818,20 @@ static int launch_fused_t(const ebr_index *ix, FusedArgs a, int max_grid, cudaSt
               kFusedThreads, smem);
     return EBR_ECUDA;
   }
-  int grid = ix->num_sms;
-  if (max_grid > 0) grid = std::min(grid, max_grid);
-  grid = std::min<int>(grid, (int)a.n_win);
-  if (grid < 1) grid = 1;
   EBR_CUDA_TRY(launch_pdl(kern, grid, kFusedThreads, smem, st, a));
   return EBR_OK;
 }
 
 template <typename Elt, bool ALL>
 static int launch_fused_d(const ebr_index *ix, const FusedArgs &a, int max_grid,
-                          cudaStream_t st) {
+                          cudaStream_t st, uint64_t *cc, size_t ce) {
   switch (ix->d) {
-    case 4: if constexpr (EltTraits<Elt>::kVec <= 4) return launch_fused_t<Elt, 4, ALL>(ix, a, max_grid, st); break;
-    case 8: if constexpr (EltTraits<Elt>::kVec <= 8) return launch_fused_t<Elt, 8, ALL>(ix, a, max_grid, st); break;
-    case 16: return launch_fused_t<Elt, 16, ALL>(ix, a, max_grid, st);
-    case 32: return launch_fused_t<Elt, 32, ALL>(ix, a, max_grid, st);
-    case 64: return launch_fused_t<Elt, 64, ALL>(ix, a, max_grid, st);
-    case 128: return launch_fused_t<Elt, 128, ALL>(ix, a, max_grid, st);
+    case 4: if constexpr (EltTraits<Elt>::kVec <= 4) return launch_fused_t<Elt, 4, ALL>(ix, a, max_grid, st, cc, ce); break;
+    case 8: if constexpr (EltTraits<Elt>::kVec <= 8) return launch_fused_t<Elt, 8, ALL>(ix, a, max_grid, st, cc, ce); break;
+    case 16: return launch_fused_t<Elt, 16, ALL>(ix, a, max_grid, st, cc, ce);
+    case 32: return launch_fused_t<Elt, 32, ALL>(ix, a, max_grid, st, cc, ce);
+    case 64: return launch_fused_t<Elt, 64, ALL>(ix, a, max_grid, st, cc, ce);
+    case 128: return launch_fused_t<Elt, 128, ALL>(ix, a, max_grid, st, cc, ce);
   }
   set_error("embedding dimension %u unsupported for this dtype", ix->d);
   return EBR_EINVAL;
@@ -835,12 +882,14 @@ bool fused_fits(const ebr_index *ix, uint32_t k) {
 // most) with counters in ctrl.  The window decode reads packed terms from wq
 // with F in ctrl->fx: when `packed` is false they are made here from the
 // dense w_hat first (after max |w^| unless wmax_ready).  *n_launched counts
-// this library's kernels launched.
+// this library's kernels launched.  cta_cand (cta_cand_entries entries), if
+// given, may hold the CTAs' candidate buffers when they do not fit shared
+// memory beside two index slots per decoder team.
 int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat, uint32_t *wq,
                  bool packed, const uint64_t *filter, uint32_t k, uint64_t *cand_out,
                  Ctrl *ctrl, float *all_out, float *wide_out, uint32_t *hist, int max_grid,
                  cudaStream_t st, bool wmax_ready, const float *wide_in, const uint32_t *route,
-                 int *n_launched) {
+                 int *n_launched, uint64_t *cta_cand, size_t cta_cand_entries) {
   FusedArgs a;
   memset(&a, 0, sizeof(a));
   int launched = 0;
@@ -884,14 +933,16 @@ int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat, uint
     launched++;
   }
   int rc;
+  uint64_t *cc = cta_cand;
+  const size_t ce = cta_cand_entries;
   if (all_out) {
-    if (ix->dtype == EBR_F32) rc = launch_fused_d<float, true>(ix, a, max_grid, st);
-    else if (ix->dtype == EBR_BF16) rc = launch_fused_d<Bf16Tag, true>(ix, a, max_grid, st);
-    else rc = launch_fused_d<Fp8Tag, true>(ix, a, max_grid, st);
+    if (ix->dtype == EBR_F32) rc = launch_fused_d<float, true>(ix, a, max_grid, st, cc, ce);
+    else if (ix->dtype == EBR_BF16) rc = launch_fused_d<Bf16Tag, true>(ix, a, max_grid, st, cc, ce);
+    else rc = launch_fused_d<Fp8Tag, true>(ix, a, max_grid, st, cc, ce);
   } else {
-    if (ix->dtype == EBR_F32) rc = launch_fused_d<float, false>(ix, a, max_grid, st);
-    else if (ix->dtype == EBR_BF16) rc = launch_fused_d<Bf16Tag, false>(ix, a, max_grid, st);
-    else rc = launch_fused_d<Fp8Tag, false>(ix, a, max_grid, st);
+    if (ix->dtype == EBR_F32) rc = launch_fused_d<float, false>(ix, a, max_grid, st, cc, ce);
+    else if (ix->dtype == EBR_BF16) rc = launch_fused_d<Bf16Tag, false>(ix, a, max_grid, st, cc, ce);
+    else rc = launch_fused_d<Fp8Tag, false>(ix, a, max_grid, st, cc, ce);
   }
   if (rc == EBR_OK) launched++;
   if (n_launched) *n_launched = launched;

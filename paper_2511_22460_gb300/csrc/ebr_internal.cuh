@@ -220,7 +220,8 @@ int launch_fused(const ebr_index *ix, const float *h_u, const float *w_hat, uint
                  bool packed, const uint64_t *filter, uint32_t k, uint64_t *cand_out,
                  Ctrl *ctrl, float *all_out, float *wide_out, uint32_t *hist, int max_grid,
                  cudaStream_t st, bool wmax_ready = false, const float *wide_in = nullptr,
-                 const uint32_t *route = nullptr, int *n_launched = nullptr);
+                 const uint32_t *route = nullptr, int *n_launched = nullptr,
+                 uint64_t *cta_cand = nullptr, size_t cta_cand_entries = 0);
 bool fused_fits(const ebr_index *ix, uint32_t k);
 constexpr size_t kHistWords = 4096;  // candidate-score histogram of the fused scan (2048 bins + top bin)
 constexpr size_t kCtrlBytes = 256;   // Ctrl block, then the histogram, in one buffer (one memset)

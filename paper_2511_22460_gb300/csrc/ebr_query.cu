@@ -1257,6 +1257,13 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
   pm.mark(1, st);
   const bool fused =
       q_key == nullptr && !(q.flags & EBR_QF_KEY_MAJOR) && fused_fits(ix, kscan);
+  // the fused scan's per-CTA candidate buffers, when they go to global
+  // memory: past the survivors' area (one CTA per SM, kscan each) and
+  // before the tail the rescoring path selects into
+  uint64_t *cta_cand = (uint64_t *)w.cand.p + (size_t)ix->num_sms * kscan;
+  const size_t cand_used = (size_t)ix->num_sms * kscan +
+                           2 * (size_t)pow2_at_least(std::max<uint32_t>(kscan, 1));
+  const size_t cta_entries = w.cand.bytes / 8 > cand_used ? w.cand.bytes / 8 - cand_used : 0;
   // a sparse list with no traversal forced: chosen on the device by its work
   const bool auto_route = q_key != nullptr && n_q > 0 &&
                           !(q.flags & (EBR_QF_KEY_MAJOR | EBR_QF_WINDOW_MAJOR)) &&
@@ -1269,7 +1276,7 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
     EBR_TRY(launch_fused(ix, q.h_u, q_w, (uint32_t *)w.wq.p, packed, q.filter, kscan,
                          (uint64_t *)w.cand.p, ctrl, nullptr, quant ? (float *)w.wide.p : nullptr,
                          ws_hist(w), ix->num_sms * kMaxCtasPerSm, st, wmax_ready,
-                         nullptr, nullptr, &nl));
+                         nullptr, nullptr, &nl, cta_cand, cta_entries));
     ix->launches += nl;  // (k_absmax, k_pack) k_fused_window
   } else {
     float *w_dense = auto_route ? (float *)w.w_dense.p : nullptr;
@@ -1292,7 +1299,7 @@ int query_one(const ebr_index *cix, const ebr_cross *cross, const ebr_query &q, 
                            auto_route && quant ? (float *)w.wide.p : nullptr,
                            ws_hist(w), ix->num_sms * kMaxCtasPerSm, st,
                            !auto_route || planned, (const float *)w.wide.p,
-                           auto_route ? &ctrl->route : nullptr, &nl));
+                           auto_route ? &ctrl->route : nullptr, &nl, cta_cand, cta_entries));
       ix->launches += nl;  // (k_absmax, k_pack) k_fused_window
 
     } else {

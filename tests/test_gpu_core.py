@@ -225,6 +225,26 @@ def test_topk_matches_oracle(name, n, k, flags):
     check_topk(ids.cpu().numpy().view(np.uint32), sc.cpu().numpy(), ref, tol, k)
 
 
+def test_topk_large_k_buffers_in_global_memory_agree_with_shared_memory():
+    """A K too large for the fused scan's shared-memory candidate buffer beside
+    two index slots per decoder team puts the per-CTA buffers in global
+    memory; the scores are formed the same way, so the best 400 of a K = 3000
+    request are exactly the K = 400 request's (which keeps its buffer in
+    shared memory), and both match the FP64 oracle."""
+    w, post, ix, cross = _setup("single_fp32_2m", 300_007, seed=12)
+    ref, tol = ref_scores(w, 0, post)
+    out = {}
+    for k in (400, 3000):
+        ids = torch.empty(k, dtype=torch.int32, device=DEV)
+        sc = torch.empty(k, dtype=torch.float32, device=DEV)
+        ebr.score_topk(ix, cross, [ebr.Query(h_u=dev(w.h_u[0]), k=k,
+                                             user_vals=dev(w.users[0]))], ids, sc)
+        out[k] = (ids.cpu().numpy().view(np.uint32), sc.cpu().numpy())
+        check_topk(out[k][0], out[k][1], ref, tol, k)
+    assert np.array_equal(out[3000][0][:400], out[400][0])
+    assert np.array_equal(out[3000][1][:400], out[400][1])
+
+
 def test_topk_with_filter_dense_q_w_and_batch():
     w, post, ix, cross = _setup("single_fp32_2m", 200_000, seed=3, batch=3)
     filt = make_filters(np.random.default_rng(9), w.n_ads, 3, (0.001, 0.3))
