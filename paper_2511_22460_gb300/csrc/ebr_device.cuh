@@ -395,21 +395,31 @@ template <> struct EltTraits<Bf16Tag> {
   }
 };
 struct Fp8Tag {};
-// E4M3 byte -> float, from the format: bias 7, exponent field 0 subnormal.
-__device__ __forceinline__ float e4m3_to_f32(uint32_t c) {
-  const uint32_t s = (c & 0x80u) << 24, e = (c >> 3) & 15u, m = c & 7u;
-  if (e == 0) return __uint_as_float(s | __float_as_uint((float)m * 0.001953125f));  // m * 2^-9
-  return __uint_as_float(s | ((e + 120u) << 23) | (m << 20));
+// Four E4M3 bytes (byte k of w is element k) -> FP32, with the hardware
+// converters: each pair of bytes to an FP16 pair, then each FP16 to FP32.
+// Both steps are exact: every E4M3 value is an FP16 value.  (The all-ones
+// NaN codes, which the library's quantiser never writes, become NaN.)
+__device__ __forceinline__ void e4m3x4_to_f32(uint32_t w, float *f) {
+  uint32_t h01, h23;
+  asm("{\n .reg .b16 lo, hi;\n mov.b32 {lo, hi}, %2;\n"
+      " cvt.rn.f16x2.e4m3x2 %0, lo;\n cvt.rn.f16x2.e4m3x2 %1, hi;\n}"
+      : "=r"(h01), "=r"(h23)
+      : "r"(w));
+  asm("{\n .reg .f16 x, y;\n mov.b32 {x, y}, %2;\n cvt.f32.f16 %0, x;\n cvt.f32.f16 %1, y;\n}"
+      : "=f"(f[0]), "=f"(f[1])
+      : "r"(h01));
+  asm("{\n .reg .f16 x, y;\n mov.b32 {x, y}, %2;\n cvt.f32.f16 %0, x;\n cvt.f32.f16 %1, y;\n}"
+      : "=f"(f[2]), "=f"(f[3])
+      : "r"(h23));
 }
 template <> struct EltTraits<Fp8Tag> {
   static constexpr int kBytes = 1;
   static constexpr int kVec = 16;
   __device__ static __forceinline__ void load(const uint4 &v, float *f) {
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-      for (int k = 0; k < 4; k++) f[4 * i + k] = e4m3_to_f32((w[i] >> (8 * k)) & 255u);
+    e4m3x4_to_f32(v.x, f);
+    e4m3x4_to_f32(v.y, f + 4);
+    e4m3x4_to_f32(v.z, f + 8);
+    e4m3x4_to_f32(v.w, f + 12);
   }
 };
 
