@@ -381,7 +381,7 @@ int ebr_profile_read(ebr_index *ix, ebr_profile *out);
  * batched scan takes, host_driven = 0) the waves run in a device-resident
  * loop: one graph launch whose WHILE node, on the device, waits with a
  * bounded poll for the next wave a worker thread posted (up to max_batch
- * queued users; one wave running and one waiting), stages it from its slots, runs the
+ * queued users; one wave at a time, the next formed while it runs), stages it from its slots, runs the
  * batched scan and merge and publishes the results; the loop leaves after
  * about 0.2 s without work and is relaunched on demand.  With host_driven =
  * 1 (and for FP32 indexes) the worker launches whatever is queued as one

@@ -125,7 +125,11 @@ struct LoopShared {                     // pinned host memory mapped into the de
 };
 struct LoopBufs {
   uint32_t R = 4, Bmax = 0, kmax = 0, desc_bytes = 0;
-  uint32_t ahead = 2;             // waves posted and not yet taken back, at most (<= R)
+  // waves posted and not yet taken back, at most (<= R): one, so that a
+  // request that arrives while a wave runs waits for that wave only (with two,
+  // p50 at 2 k req/s on 5M BF16 ads was 13.9 ms instead of 8.5 ms, at the
+  // same throughput)
+  uint32_t ahead = 1;
   void *host = nullptr;           // pinned, mapped: LoopShared, descriptors [R], flags [R], status [R][Bmax]
   LoopShared *sh = nullptr;
   uint8_t *desc = nullptr;        // [R][desc_bytes] wave descriptors (host-written)
