@@ -293,12 +293,12 @@ def run_single(args, w, rank, world, local_rank, workload, steps=None, n_req=16,
     step_bytes = kern_bytes
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", "scan_traffic.json")
-    if os.path.exists(tr_path):
+    if os.path.exists(tr_path) and not sparse:
         with open(tr_path) as f:
-            tr = json.load(f)
-        if (tr.get("workload") == workload and tr.get("kernel_rev") == KERNEL_REV and
-                not sparse):
-            traffic = tr.get("bytes_per_launch")
+            records = json.load(f)
+        for tr in records if isinstance(records, list) else [records]:
+            if tr.get("workload") == workload and tr.get("kernel_rev") == KERNEL_REV:
+                traffic = tr.get("bytes_per_launch")
     launches_per_step = launches / max(steps, 1)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
@@ -338,7 +338,7 @@ def run_single(args, w, rank, world, local_rank, workload, steps=None, n_req=16,
     return out
 
 
-KERNEL_REV = "fused-v4"
+KERNEL_REV = "fused-v5"
 
 # FP32 add throughput of the CUDA cores: 152 SMs x 128 FP32 lanes x 2.07 GHz
 ALU_ADD_PEAK_T = 152 * 128 * 2.07e9 / 1e12
