@@ -338,7 +338,7 @@ def run_single(args, w, rank, world, local_rank, workload, steps=None, n_req=16,
     return out
 
 
-KERNEL_REV = "fused-v5"
+KERNEL_REV = "fused-v6"
 
 # FP32 add throughput of the CUDA cores: 152 SMs x 128 FP32 lanes x 2.07 GHz
 ALU_ADD_PEAK_T = 152 * 128 * 2.07e9 / 1e12

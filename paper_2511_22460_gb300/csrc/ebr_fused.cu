@@ -543,11 +543,15 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
   // this thread's row part and its rotated copy of h_u (constant for the kernel)
   const int qd = tid % Sh::kTPR;
   const int prow = tid / Sh::kTPR;              // row within a pass
-  const uint32_t rot = tid / Sh::kRowsPer128;   // 16-byte reads of neighbours hit other banks
+  // 16-byte reads of neighbouring rows hit other banks: at step i a thread
+  // reads chunk i ^ rot of its row part (rot < kCPT; threads with different
+  // rot read different chunks)
+  static_assert((Sh::kCPT & (Sh::kCPT - 1)) == 0, "chunks per thread: a power of two");
+  const uint32_t rot = (tid / Sh::kRowsPer128) % Sh::kCPT;
   float hreg[Sh::kHPT];
 #pragma unroll
   for (int i = 0; i < Sh::kCPT; i++) {
-    const uint32_t c = qd * Sh::kCPT + (i + rot) % Sh::kCPT;
+    const uint32_t c = qd * Sh::kCPT + (i ^ rot);
 #pragma unroll
     for (int e = 0; e < Tr::kVec; e++) hreg[i * Tr::kVec + e] = s_h[c * Tr::kVec + e];
   }
@@ -619,7 +623,7 @@ __global__ void __maxnreg__(96) k_fused_window(FusedArgs a) {
       if (valid) {
 #pragma unroll
         for (int i = 0; i < Sh::kCPT; i++) {
-          const uint32_t c = qd * Sh::kCPT + (i + rot) % Sh::kCPT;
+          const uint32_t c = qd * Sh::kCPT + (i ^ rot);
           const uint4 v = *reinterpret_cast<const uint4 *>(row + c * 16);
           float f[Tr::kVec];
           Tr::load(v, f);
