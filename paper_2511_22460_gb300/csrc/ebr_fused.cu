@@ -5,8 +5,9 @@
 // ad >> 8) -- from the window-major view of the compressed inverted list, in
 // shared memory, and added to the dual-tower inner product (Eq. 1) of the same
 // ads as their embedding rows stream through; the K best survive in a per-CTA
-// buffer.  Neither the wide term nor the score vector is written to global
-// memory.
+// buffer (in shared memory, or in global memory when a large K would crowd
+// out the index slots).  Neither the wide term nor the score vector is
+// written to global memory.
 //
 // One persistent CTA per SM, three warp roles:
 //   producers (2 warps, independent): one stages every window's
@@ -20,9 +21,11 @@
 //       gather w^[key] and add it into one of four fixed-point accumulators
 //       of 256 ads (one 32-bit integer atomic per real ad slot);
 //   scorers (8 warps): one thread per row (two for 128-element rows) forms the
-//       inner product with its rotated copy of h_u held in registers, adds the
-//       window's accumulator (and the FP8 row scale), applies the filter and
-//       appends candidates; a radix select trims the buffer to the K best.
+//       inner product with its permuted copy of h_u held in registers (each
+//       thread reads the row's 16-byte chunks in its own order, so that
+//       neighbouring rows hit other banks), adds the window's accumulator
+//       (and the FP8 row scale), applies the filter and appends candidates;
+//       a radix select trims the buffer to the K best.
 // All hand-offs are mbarrier phases; every wait is bounded (2 s) and a CTA
 // that times out flags the request and drains its copies.
 #include <algorithm>
